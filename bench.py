@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the periodic cubic-spline particle-tracking hot path on GB300.
+
+Workload (one "step"): the spline-coefficient solve of a 512^3 three-component
+FP32 field (random-phase k^-5/3 spectrum, 1 <= |k| <= 170, unit rms), then 10
+Heun RK2 steps (dt = 1e-3) of 16,777,216 FP64 particles (uniform in the box)
+with re-binning into 8^3-cell bricks before every RK2 step.  Inputs are larger
+than L2 (1.6 GB field, 0.4 GB positions), so no L2 flush is added.
+
+Unit: one particle interpolation of (u, v, w) at one position; an RK2 step
+interpolates every particle twice, so value = n_gpus * 2 * 10 * Np / t_step.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s interpolated (u,v,w tricubic) + spline GB/s, % HBM roofline, 1 GB300"
+UNIT = "particles/s"
+N = 512
+KMAX = 170
+NP = 1 << 24
+RK_STEPS = 10
+DT = 1e-3
+BRICK = (8, 8, 8)
+FIELD_SEED = 1001
+POS_SEED = 2001
+WORKLOAD = ("mid: 512^3 FP32 u,v,w (k^-5/3, 1<=|k|<=170, unit rms), 16,777,216 uniform FP64 "
+            "particles; spline solve + 10 Heun RK2 steps (dt 1e-3) with re-binning into 8^3 "
+            "bricks every step")
+# kernels of libps launched per bench step: 3 solve passes + 10 x (5 bin + 1 RK2)
+LAUNCHES_PER_STEP = 3 + RK_STEPS * 6
+DOMINANT = "interp_staged<float,3,RK2> (fused binned Heun step)"
+SOURCE_FOR_TRAFFIC = os.path.join(ROOT, "paper_2005_13193_gb300", "csrc", "interp.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.idx = gpu_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def traffic_for(kernel_key: str):
+    """Per-launch DRAM bytes from a committed ncu summary, or None if absent or
+    taken on a different version of the kernel source."""
+    try:
+        sha = hashlib.sha256(open(SOURCE_FOR_TRAFFIC, "rb").read()).hexdigest()[:12]
+        for line in open(TRAFFIC_FILE):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == sha:
+                return float(parts[2])
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------- our arm ----
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2005_13193_gb300 as ps
+    from paper_2005_13193_gb300 import synth
+
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    field = synth.spectral_field(N, KMAX, seed=FIELD_SEED, device=dev, dtype=torch.float32)
+    pos_host = synth.uniform_particles(NP, seed=POS_SEED)
+    pos0 = torch.from_numpy(pos_host).to(dev)
+    n3 = (N, N, N)
+    coef = torch.empty((3, N + 3, N + 3, N + 3), dtype=torch.float32, device=dev)
+    nb = [-(-N // b) for b in BRICK]
+    nbins = nb[0] * nb[1] * nb[2]
+    offsets = torch.empty(nbins + 1, dtype=torch.int32, device=dev)
+    bin_of = torch.empty(NP, dtype=torch.int32, device=dev)
+    ws_bin = ps.workspace(ps.ps_bin_workspace_size(n3, BRICK, NP), dev)
+    status = torch.zeros(4, dtype=torch.int32, device=dev)
+    vel = torch.empty((3, NP), dtype=torch.float32, device=dev)
+    bufs = [pos0.clone(), torch.empty_like(pos0)]
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(ev_solve=None, ev_rk=None):
+        if ev_solve:
+            ev_solve[0].record(stream)
+        ps.ps_spline_coeffs(field, coef)
+        if ev_solve:
+            ev_solve[1].record(stream)
+        for r in range(RK_STEPS):
+            src, dst = bufs[0], bufs[1]
+            ps.ps_bin_particles(n3, BRICK, src, bin_of, offsets, None, dst, ws_bin, status)
+            if ev_rk:
+                ev_rk[r][0].record(stream)
+            ps.ps_rk2_step(coef, dst, DT, vel_out=vel, brick=BRICK, rebin=False,
+                           bin_offsets=offsets, status=status)
+            if ev_rk:
+                ev_rk[r][1].record(stream)
+            bufs[0], bufs[1] = dst, src
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    st = ps.ps_status_read(status)
+    if st[0] != 0:
+        raise RuntimeError(f"device status after warm-up: {st}")
+
+    K = args.steps
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ev_solve = [(mk(), mk()) for _ in range(K)]
+    ev_rk = [[(mk(), mk()) for _ in range(RK_STEPS)] for _ in range(K)]
+    t0, t1 = mk(), mk()
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    for k in range(K):
+        one_step(ev_solve[k], ev_rk[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    ms = t0.elapsed_time(t1) / K
+    if pg:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+
+    solve_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_solve)
+    rk_ms = [a.elapsed_time(b) for step in ev_rk for a, b in step]
+    rk_avg = statistics.mean(rk_ms)
+    peak, peak_kind = measured_peaks()
+    coef_bytes = 3 * 4 * (N + 3) ** 3
+    rk_alg_bytes = NP * (24 + 24 + 12) + coef_bytes
+    solve_min_bytes = 3 * 4 * N ** 3 + coef_bytes
+    solve_pass_bytes = 3 * 4 * N ** 3 * 5 + coef_bytes
+    achieved = rk_alg_bytes / (rk_avg * 1e-3) / 1e9
+    units = 2 * RK_STEPS * NP
+    value = ws_ * units / (ms * 1e-3)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded spectral field, uniform particles)",
+        "config": {"workload": WORKLOAD, "grid": N, "particles": NP, "rk2_steps": RK_STEPS,
+                   "dt": DT, "brick": list(BRICK), "coef_dtype": "f32",
+                   "positions": "f64", "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{ws_} (independent problems)"},
+        "gpu_launches": LAUNCHES_PER_STEP * K,
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic_for("rk2_staged_f32"),
+                     "alg_bytes_per_launch": rk_alg_bytes, "avg_launch_ms": rk_avg},
+        "breakdown": {"solve_ms": solve_ms,
+                      "solve_gbs_min_bytes": solve_min_bytes / (solve_ms * 1e-3) / 1e9,
+                      "solve_gbs_pass_bytes": solve_pass_bytes / (solve_ms * 1e-3) / 1e9,
+                      "solve_frac_of_peak_min_bytes": solve_min_bytes / (solve_ms * 1e-3) / 1e9
+                      / peak,
+                      "rk2_kernel_ms_avg": rk_avg,
+                      "rk2_kernel_particles_per_s": 2 * NP / (rk_avg * 1e-3),
+                      "bin_and_rest_ms_per_rk_step": (ms - solve_ms) / RK_STEPS - rk_avg},
+    }
+
+    if not args.no_extras and rank == 0:
+        result["interp_sorted_vs_unsorted"] = interp_extras(ps, torch, dev, coef, bufs[0], n3)
+    if not args.no_e2e:
+        result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg)
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(field.cpu().numpy(), pos_host)
+    if rank == 0:
+        print(json.dumps(result))
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
+    """Config-2 comparison: one interpolation of all particles, unsorted (random
+    storage order, direct gathers) vs sorted (bin order, staged halos)."""
+    g = torch.Generator(device="cpu").manual_seed(5)
+    perm = torch.randperm(NP, generator=g).to(dev)
+    pos_rand = pos_sorted_by_bin[:, perm].contiguous()
+    vel = torch.empty((3, NP), dtype=torch.float32, device=dev)
+    bins = ps.bin_particles(n3, BRICK, pos_sorted_by_bin, want_perm=False)
+    sorted_bins = ps.Bins(BRICK, bins.offsets, bins.bin_of, None)
+    # physically sorted copy
+    bins2, pos_sorted = ps.bin_particles(n3, BRICK, pos_sorted_by_bin, want_sorted=True)
+    out = {}
+    for name, fn in (
+            ("unsorted_direct", lambda: ps.ps_interp(coef, pos_rand, vel)),
+            ("sorted_direct", lambda: ps.ps_interp(coef, pos_sorted, vel)),
+            ("sorted_staged", lambda: ps.ps_interp(coef, pos_sorted, vel,
+                                                   bin_offsets=bins2.offsets, brick=BRICK))):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 5
+        out[name] = {"ms": t, "particles_per_s": NP / (t * 1e-3)}
+    del sorted_bins
+    return out
+
+
+def e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg):
+    """The same step through the public API from pinned host buffers: the field
+    and positions are copied in, the result positions and velocities out."""
+    field_h = field.cpu().pin_memory()
+    pos_h = torch.from_numpy(pos_host).pin_memory()
+    pos_out_h = torch.empty_like(pos_h).pin_memory()
+    vel_h = torch.empty((3, NP), dtype=torch.float32).pin_memory()
+    field_d = torch.empty_like(field)
+    pos_d = torch.empty((3, NP), dtype=torch.float64, device=dev)
+    vel_d = torch.empty((3, NP), dtype=torch.float32, device=dev)
+    ids = torch.arange(NP, dtype=torch.int64, device=dev)
+    ws = ps.workspace(ps.ps_rk2_workspace_size(n3, BRICK, NP), dev)
+    nb = [-(-N // b) for b in BRICK]
+    offsets = torch.empty(nb[0] * nb[1] * nb[2] + 1, dtype=torch.int32, device=dev)
+    status = torch.zeros(4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        field_d.copy_(field_h, non_blocking=True)
+        pos_d.copy_(pos_h, non_blocking=True)
+        ps.ps_spline_coeffs(field_d, coef)
+        for _ in range(RK_STEPS):
+            ps.ps_rk2_step(coef, pos_d, DT, ids=ids, vel_out=vel_d, brick=BRICK, rebin=True,
+                           bin_offsets=offsets, ws=ws, status=status)
+        pos_out_h.copy_(pos_d, non_blocking=True)
+        vel_h.copy_(vel_d, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(1, min(K, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    if pg:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    units = 2 * RK_STEPS * NP
+    return {"value": ws_ * units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": field_h.numel() * 4 + pos_h.numel() * 8,
+            "d2h_bytes_per_step": pos_out_h.numel() * 8 + vel_h.numel() * 4,
+            "api": "ps_spline_coeffs + ps_rk2_step(rebin=1, ids)"}
+
+
+# ------------------------------------------------------------- the oracle ----
+
+CPU_SAMPLE = 65536
+
+
+def oracle_step(oracle, field64, pos_sample):
+    """One bounded sample of the workload on the host: the full 512^3 solve and
+    10 RK2 steps of a particle subsample.  Returns (t_solve, t_rk2)."""
+    t = time.perf_counter()
+    coef = oracle.spline_coeffs(field64)
+    t_solve = time.perf_counter() - t
+    p = pos_sample.copy()
+    t = time.perf_counter()
+    for _ in range(RK_STEPS):
+        p, _ = oracle.rk2_step(coef, p, DT)
+    t_rk = time.perf_counter() - t
+    return t_solve, t_rk
+
+
+def extrapolated_rate(t_solve, t_rk):
+    t_full = t_solve + t_rk * (NP / CPU_SAMPLE)
+    return 2 * RK_STEPS * NP / t_full
+
+
+def cpu_baseline(field_np, pos_host):
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.set_num_threads(cores)
+    field64 = field_np.astype(np.float64)
+    t_solve, t_rk = oracle_step(oracle, field64, pos_host[:, :CPU_SAMPLE])
+    return {"value": extrapolated_rate(t_solve, t_rk), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"full 512^3 FP64 solve ({t_solve:.1f} s) + 10 RK2 steps of "
+                      f"{CPU_SAMPLE} particles ({t_rk:.2f} s), particle part scaled to "
+                      f"{NP} particles"}
+
+
+def run_reference(args):
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2005_13193_gb300 import synth
+
+    ws_, rank, _ = dist_env()
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    field = synth.spectral_field(N, KMAX, seed=FIELD_SEED, device=dev, dtype=torch.float32)
+    field64 = field.cpu().numpy().astype(np.float64)
+    del field
+    pos = synth.uniform_particles(NP, seed=POS_SEED)[:, :CPU_SAMPLE].copy()
+    cores = os.cpu_count() or 1
+    oracle.set_num_threads(cores)
+    for _ in range(args.warmup):
+        oracle_step(oracle, field64, pos)
+    rates, solves, rks = [], [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ts, tr = oracle_step(oracle, field64, pos)
+        solves.append(ts)
+        rks.append(tr)
+        rates.append(extrapolated_rate(ts, tr))
+    wall = time.perf_counter() - t0
+    ms = 1e3 * (statistics.mean(solves) + statistics.mean(rks) * NP / CPU_SAMPLE)
+    value = 2 * RK_STEPS * NP / (ms * 1e-3)
+    sample = (f"full 512^3 FP64 solve + 10 RK2 steps of {CPU_SAMPLE} particles per step, "
+              f"particle part scaled to {NP}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded spectral field, uniform particles)",
+        "config": {"workload": WORKLOAD, "grid": N, "particles": NP, "rk2_steps": RK_STEPS,
+                   "dt": DT, "brick": list(BRICK)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * ps.h - periodic cubic-spline particle interpolation on one GPU (C ABI).
+ *
+ * The operations are those of Buaria & Yeung, "A highly scalable particle
+ * tracking algorithm using PGAS programming for extreme-scale turbulence
+ * simulations" (arXiv 2005.13193):
+ *   Sec. 2.2, Operation 1  spline coefficients from the Eulerian field;
+ *   Sec. 2.2, Operation 2  basis functions from particle positions;
+ *   Sec. 2.2, Operation 3  64-term sum of Eq. (spline);
+ *   Sec. 3                 particles handled where their stencil lives
+ *                          (here: bin sort into cell bricks);
+ *   Sec. 2.1 / 4.3         second-order Runge-Kutta particle advance.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns a ps_status.  On failure ps_last_error() returns a
+ *   thread-local message.  No C++ exception crosses this interface.
+ * - Every GPU call is enqueued on `stream` (a cudaStream_t passed as void*;
+ *   NULL = the legacy default stream) and returns before the GPU work ends.
+ *   Argument errors are detected on the host before anything is enqueued.
+ * - All array pointers are device pointers owned by the caller.  The library
+ *   never frees them and, on these calls, allocates no device memory: scratch
+ *   comes from the caller through (ws, ws_bytes), sized by the matching
+ *   *_workspace_size() query.  ws must be 256-byte aligned.
+ * - Device-side anomalies (a non-finite or out-of-range position) never trap:
+ *   they are recorded in an optional caller-owned device word
+ *   `int32_t status[4]` = {code, first index low 32 bits, high 32 bits,
+ *   count} and the affected outputs are NaN.  Read it with ps_status_read().
+ *
+ * Layouts (x is the fastest index everywhere)
+ * -------------------------------------------
+ *   grid       n[0] = nx, n[1] = ny, n[2] = nz nodes on the periodic box
+ *              [0,L[0]) x [0,L[1]) x [0,L[2]); node spacing h_d = L_d / n_d.
+ *              3 <= n_d <= 2048.
+ *   field      [ncomp][nz][ny][nx]                     (F32 or F64)
+ *   coef       [ncomp][nz+3][ny+3][nx+3]               (F32, F64, BF16, F16)
+ *              padded index P in [0, n+2] holds node (P-1) mod n: one periodic
+ *              ghost below and two above, the N+3 coefficients per line of
+ *              Sec. 2.2.  Storage offset of (c, Pz, Py, Px) is
+ *              ((c*(nz+3) + Pz)*(ny+3) + Py)*(nx+3) + Px.
+ *   scale      [ncomp][nz+3][ny+3] F32, only for BF16/F16 coefficients: the
+ *              value of a coefficient is stored * scale of its x-line; scales
+ *              are powers of two, so scaling itself is exact.
+ *   pos        [3][np] FP64, structure of arrays; positions may lie outside
+ *              the box (their periodic shadow image is used, Sec. 2.2).
+ *   vel        [ncomp][np] F32.
+ *   grad       [ncomp][3][np] F32, grad[c][d] = d u_c / d x_d.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PS_OK = 0,
+  PS_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype or layout request   */
+  PS_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed  */
+  PS_ERR_WORKSPACE = 3,     /* ws NULL, misaligned or smaller than needed   */
+  PS_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement  */
+  PS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                */
+  PS_ERR_DEVICE_STATUS = 6  /* ps_status_read found a device-side anomaly   */
+} ps_status;
+
+typedef enum { PS_F32 = 0, PS_BF16 = 1, PS_F16 = 2, PS_F64 = 3 } ps_dtype;
+
+/* device status codes (status[0]) */
+#define PS_DEV_OK 0
+#define PS_DEV_NONFINITE_POS 1 /* position NaN/Inf or |x * n/L| >= 1e15 */
+#define PS_DEV_TIMEOUT 2
+
+typedef struct {
+  int32_t n[3]; /* nodes per axis: x, y, z */
+  double L[3];  /* periodic box lengths (2*pi in the paper) */
+} ps_grid;
+
+/* Thread-local description of the last failure on this host thread. */
+const char* ps_last_error(void);
+/* Library version string. */
+const char* ps_version(void);
+
+/* Zero a device status word (4 x int32) on `stream`. */
+ps_status ps_status_clear(int32_t* status, void* stream);
+/* Copy a device status word to host_out[4], synchronising `stream`.
+ * Returns PS_ERR_DEVICE_STATUS if host_out[0] != PS_DEV_OK. */
+ps_status ps_status_read(const int32_t* status, int32_t* host_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Operation 1 (Sec. 2.2): spline coefficients.                             */
+/* Along every grid line of N nodes solve the periodic tridiagonal system   */
+/* (1/6) c[j-1] + (4/6) c[j] + (1/6) c[j+1] = g[j] (indices mod N), for the */
+/* x, y and z lines of every component, and store the N+3 padded           */
+/* coefficients per axis.  The result is the exact inverse up to rounding;  */
+/* the order of the three directions is immaterial in exact arithmetic.     */
+/*   field_t: PS_F32 or PS_F64.  coef_t: PS_F32, PS_F64, PS_BF16, PS_F16.   */
+/*   Arithmetic is FP64 when coef_t is PS_F64, else FP32.                   */
+/*   scale: required for BF16/F16 (per x-line power-of-two scale), else     */
+/*   ignored.  field and coef must not overlap.  ncomp in [1, 16].          */
+/* ------------------------------------------------------------------------ */
+size_t ps_spline_coeffs_workspace_size(const ps_grid* grid, int ncomp,
+                                       ps_dtype coef_t);
+ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype field_t,
+                           const void* field, ps_dtype coef_t, void* coef,
+                           float* scale, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Bin sort (Sec. 3: each particle is handled where the coefficients of its */
+/* stencil live).  Cell a_d = floor(x_d * n_d/L_d) mod n_d (FP64, one       */
+/* rounded multiply), brick b_d = a_d / brick[d], nb_d = ceil(n_d/brick[d]),*/
+/* bin = (b_z*nb_y + b_y)*nb_x + b_x.  A counting sort gives                */
+/*   bin_of[np]            int32 bin of each particle (required);           */
+/*   bin_offsets[nbins+1]  int32 exclusive prefix sum of bin counts;        */
+/*   perm[np]              int64 sorted slot -> particle index (optional);  */
+/*   pos_sorted[3][np]     positions in sorted order (optional).            */
+/* Within a bin the order is unspecified.  A non-finite position goes to    */
+/* bin 0 and is flagged in `status` (optional).  np < 2^31.                 */
+/* ------------------------------------------------------------------------ */
+size_t ps_bin_workspace_size(const ps_grid* grid, const int32_t brick[3],
+                             int64_t np);
+ps_status ps_bin_particles(const ps_grid* grid, const int32_t brick[3],
+                           int64_t np, const double* pos, int32_t* bin_of,
+                           int32_t* bin_offsets, int64_t* perm,
+                           double* pos_sorted, void* ws, size_t ws_bytes,
+                           int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Operations 2 and 3 (Sec. 2.2, Eq. (spline)):                             */
+/*   u_c(x) = sum_{i,j,k=0..3} b_i(t_x) b_j(t_y) b_k(t_z)                   */
+/*            C_c[a_z+k][a_y+j][a_x+i]                                      */
+/* with the uniform cubic B-spline b(t) = [(1-t)^3, 3t^3-6t^2+4,            */
+/* -3t^3+3t^2+3t+1, t^3]/6 and t_d = x_d n_d/L_d - floor(x_d n_d/L_d).      */
+/* FP64 positions, FP32 basis and accumulation (FP64 for PS_F64 coef).      */
+/* Modes:                                                                   */
+/*   bin_offsets == NULL             direct gather, any particle order;     */
+/*   bin_offsets != NULL, perm NULL  particles stored in bin order (as left */
+/*                                   by ps_bin_particles' pos_sorted or by  */
+/*                                   ps_rk2_step); each brick's coefficient */
+/*                                   halo is staged once in shared memory;  */
+/*   bin_offsets and perm != NULL    same, particle perm[s] at sorted slot s.*/
+/* brick[3] must be the one used for binning when bin_offsets != NULL.      */
+/* Particles whose stencil leaves their brick's halo fall back to a direct  */
+/* gather, so stale bins give correct (slower) results.                     */
+/*   grad: optional [ncomp][3][np] velocity-gradient tensor.                */
+/*   ncomp: 1 or 3.  status: optional.                                      */
+/* ------------------------------------------------------------------------ */
+ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
+                    const void* coef, const float* scale, int64_t np,
+                    const double* pos, const int64_t* perm,
+                    const int32_t* bin_offsets, const int32_t brick[3],
+                    float* vel, float* grad, int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of ps_interp (and of ps_spline_coeffs) for a cotangent g_vel     */
+/* [ncomp][np] F32:                                                         */
+/*   g_pos[d][p]  = sum_c g_vel[c][p] d u_c / d x_d      ([3][np] FP64);    */
+/*   g_field      = d <g_vel, u> / d field   ([ncomp][nz][ny][nx] F32):     */
+/*                  scatter-add of g * basis weights, folded onto the N     */
+/*                  periodic nodes (transpose of the padding), then the     */
+/*                  same periodic solves (the matrix is symmetric).         */
+/* Either output may be NULL.  g_field is overwritten (not accumulated).    */
+/* Quantised (BF16/F16) coefficients are differentiated as if exact.        */
+/* No workspace is needed (ws may be NULL with ws_bytes 0).                 */
+/* ------------------------------------------------------------------------ */
+ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype coef_t,
+                             const void* coef, const float* scale, int64_t np,
+                             const double* pos, const float* g_vel,
+                             double* g_pos, float* g_field, void* ws,
+                             size_t ws_bytes, int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* One second-order Runge-Kutta step (Sec. 2.1; Sec. 4.3), Heun's form:     */
+/*   u1 = u(x^n; coef_n);  x* = x^n + dt u1;  u2 = u(x*; coef_np1);         */
+/*   x^{n+1} = x^n + (dt/2)(u1 + u2)                                        */
+/* in FP64 for positions (velocities from the FP32 interpolation).          */
+/* coef_np1 == NULL: frozen field (coef_n for both stages).  ncomp = 3.     */
+/*   brick == NULL   particles keep their order; direct gathers.            */
+/*   brick, rebin=1  particles are first bin-sorted by x^n and physically   */
+/*                   reordered (pos, and ids if given), the analogue of the */
+/*                   paper's particle migration (Sec. 4.3); bin_offsets     */
+/*                   (optional, [nbins+1]) receives the new bin bounds;     */
+/*                   stage 1 reads the staged brick halo in shared memory.  */
+/*   brick, rebin=0  particles are taken to be in bin order already with    */
+/*                   the given bin_offsets (required).                      */
+/*   vel_out: optional [3][np], receives u1 in the final particle order.    */
+/*   ids: optional int64 [np] particle labels, permuted with the particles. */
+/* ------------------------------------------------------------------------ */
+size_t ps_rk2_workspace_size(const ps_grid* grid, const int32_t brick[3],
+                             int64_t np);
+ps_status ps_rk2_step(const ps_grid* grid, ps_dtype coef_t, const void* coef_n,
+                      const void* coef_np1, const float* scale_n,
+                      const float* scale_np1, int64_t np, double* pos,
+                      int64_t* ids, float* vel_out, double dt,
+                      const int32_t brick[3], int rebin, int32_t* bin_offsets,
+                      void* ws, size_t ws_bytes, int32_t* status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_H */

@@ -1,0 +1,391 @@
+"""Periodic cubic-spline particle interpolation on one GB300.
+
+Python binding of the C ABI in include/ps.h (Buaria & Yeung, arXiv
+2005.13193, Sec. 2.2 Eq. (spline), Sec. 3, Sec. 4.3).  The ``ps_*``
+functions carry the C names and only marshal torch tensors into pointers and
+sizes; every step of the computation runs in the CUDA library libps.so.  If
+that library cannot be loaded the calls raise: there is no CPU path.
+
+Higher-level helpers (`SplineField`, `Tracker`, `InterpFn`) allocate with
+torch and call the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import (PS_BF16, PS_F16, PS_F32, PS_F64, PS_OK, PsGrid)
+
+TWO_PI = 2.0 * math.pi
+DEFAULT_L = (TWO_PI, TWO_PI, TWO_PI)
+
+_DT = {torch.float32: PS_F32, torch.float64: PS_F64, torch.bfloat16: PS_BF16,
+       torch.float16: PS_F16}
+
+
+class PSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libps error {code}: {msg}")
+        self.code = code
+
+
+def _lib():
+    return _abi.load()
+
+
+def _check(rc: int):
+    if rc != PS_OK:
+        raise PSError(rc, _lib().ps_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t: Optional[torch.Tensor], name: str, dtype=None, numel=None):
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_grid(n: Sequence[int], L: Sequence[float] = DEFAULT_L) -> PsGrid:
+    """n = (nx, ny, nz) nodes; L = box lengths."""
+    g = PsGrid()
+    for d in range(3):
+        g.n[d] = int(n[d])
+        g.L[d] = float(L[d])
+    return g
+
+
+def _brick_arr(brick):
+    if brick is None:
+        return None
+    if isinstance(brick, int):
+        brick = (brick, brick, brick)
+    return (ctypes.c_int32 * 3)(*[int(b) for b in brick])
+
+
+def grid_of_coef(coef: torch.Tensor):
+    """(nx, ny, nz) of a padded coefficient array [ncomp][nz+3][ny+3][nx+3]."""
+    return (coef.shape[3] - 3, coef.shape[2] - 3, coef.shape[1] - 3)
+
+
+def grid_of_field(field: torch.Tensor):
+    return (field.shape[3], field.shape[2], field.shape[1])
+
+
+# ------------------------------------------------------------- C entry points ----
+
+def ps_last_error() -> str:
+    return _lib().ps_last_error().decode()
+
+
+def ps_version() -> str:
+    return _lib().ps_version().decode()
+
+
+def ps_status_clear(status: torch.Tensor, stream=None):
+    _dev(status, "status", torch.int32, 4)
+    _check(_lib().ps_status_clear(_ptr(status), _stream(stream)))
+
+
+def ps_status_read(status: torch.Tensor, stream=None, raise_on_error: bool = False):
+    """Returns [code, index_lo, index_hi, count]."""
+    _dev(status, "status", torch.int32, 4)
+    out = (ctypes.c_int32 * 4)()
+    rc = _lib().ps_status_read(_ptr(status), ctypes.cast(out, ctypes.c_void_p), _stream(stream))
+    if rc not in (PS_OK, _abi.PS_ERR_DEVICE_STATUS) or (raise_on_error and rc != PS_OK):
+        _check(rc)
+    return list(out)
+
+
+def ps_spline_coeffs_workspace_size(n, ncomp: int, coef_dtype: torch.dtype,
+                                    L=DEFAULT_L) -> int:
+    g = make_grid(n, L)
+    return int(_lib().ps_spline_coeffs_workspace_size(ctypes.byref(g), ncomp, _DT[coef_dtype]))
+
+
+def ps_spline_coeffs(field: torch.Tensor, coef: torch.Tensor, scale: Optional[torch.Tensor] = None,
+                     ws: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
+    """Operation 1 (Sec. 2.2): field [ncomp][nz][ny][nx] -> coef [ncomp][nz+3][ny+3][nx+3]."""
+    n = grid_of_field(field)
+    ncomp = field.shape[0]
+    _dev(field, "field")
+    _dev(coef, "coef", numel=ncomp * (n[0] + 3) * (n[1] + 3) * (n[2] + 3))
+    _dev(scale, "scale", torch.float32)
+    _dev(ws, "ws")
+    g = make_grid(n, L)
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_lib().ps_spline_coeffs(ctypes.byref(g), ncomp, _DT[field.dtype], _ptr(field),
+                                   _DT[coef.dtype], _ptr(coef), _ptr(scale), _ptr(ws), ws_bytes,
+                                   _stream(stream)))
+
+
+def ps_bin_workspace_size(n, brick, np_: int, L=DEFAULT_L) -> int:
+    g = make_grid(n, L)
+    return int(_lib().ps_bin_workspace_size(ctypes.byref(g), _brick_arr(brick), int(np_)))
+
+
+def ps_bin_particles(n, brick, pos: torch.Tensor, bin_of: torch.Tensor, bin_offsets: torch.Tensor,
+                     perm: Optional[torch.Tensor] = None, pos_sorted: Optional[torch.Tensor] = None,
+                     ws: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                     L=DEFAULT_L, stream=None):
+    """Sec. 3 dynamic mapping read as a bin sort into bricks of `brick` cells."""
+    np_ = pos.shape[1]
+    _dev(pos, "pos", torch.float64)
+    _dev(bin_of, "bin_of", torch.int32, np_)
+    _dev(bin_offsets, "bin_offsets", torch.int32)
+    _dev(perm, "perm", torch.int64, np_)
+    _dev(pos_sorted, "pos_sorted", torch.float64, 3 * np_)
+    _dev(ws, "ws")
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_lib().ps_bin_particles(ctypes.byref(g), _brick_arr(brick), np_, _ptr(pos),
+                                   _ptr(bin_of), _ptr(bin_offsets), _ptr(perm), _ptr(pos_sorted),
+                                   _ptr(ws), ws_bytes, _ptr(status), _stream(stream)))
+
+
+def ps_interp(coef: torch.Tensor, pos: torch.Tensor, vel: torch.Tensor,
+              scale: Optional[torch.Tensor] = None, perm: Optional[torch.Tensor] = None,
+              bin_offsets: Optional[torch.Tensor] = None, brick=None,
+              grad: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+              L=DEFAULT_L, stream=None):
+    """Operations 2-3 (Sec. 2.2, Eq. (spline)) at positions pos [3][np] -> vel [ncomp][np]."""
+    n = grid_of_coef(coef)
+    ncomp = coef.shape[0]
+    np_ = pos.shape[1]
+    _dev(coef, "coef")
+    _dev(pos, "pos", torch.float64)
+    _dev(vel, "vel", torch.float32, ncomp * np_)
+    _dev(scale, "scale", torch.float32)
+    _dev(perm, "perm", torch.int64, np_)
+    _dev(bin_offsets, "bin_offsets", torch.int32)
+    _dev(grad, "grad", torch.float32, ncomp * 3 * np_)
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    _check(_lib().ps_interp(ctypes.byref(g), ncomp, _DT[coef.dtype], _ptr(coef), _ptr(scale), np_,
+                            _ptr(pos), _ptr(perm), _ptr(bin_offsets), _brick_arr(brick),
+                            _ptr(vel), _ptr(grad), _ptr(status), _stream(stream)))
+
+
+def ps_interp_backward(coef: torch.Tensor, pos: torch.Tensor, g_vel: torch.Tensor,
+                       g_pos: Optional[torch.Tensor] = None, g_field: Optional[torch.Tensor] = None,
+                       scale: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                       L=DEFAULT_L, stream=None):
+    """Adjoint of ps_interp and of the coefficient solve."""
+    n = grid_of_coef(coef)
+    ncomp = coef.shape[0]
+    np_ = pos.shape[1]
+    _dev(coef, "coef")
+    _dev(pos, "pos", torch.float64)
+    _dev(g_vel, "g_vel", torch.float32, ncomp * np_)
+    _dev(g_pos, "g_pos", torch.float64, 3 * np_)
+    _dev(g_field, "g_field", torch.float32, ncomp * n[0] * n[1] * n[2])
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    _check(_lib().ps_interp_backward(ctypes.byref(g), ncomp, _DT[coef.dtype], _ptr(coef),
+                                     _ptr(scale), np_, _ptr(pos), _ptr(g_vel), _ptr(g_pos),
+                                     _ptr(g_field), None, 0, _ptr(status), _stream(stream)))
+
+
+def ps_rk2_workspace_size(n, brick, np_: int, L=DEFAULT_L) -> int:
+    g = make_grid(n, L)
+    return int(_lib().ps_rk2_workspace_size(ctypes.byref(g), _brick_arr(brick), int(np_)))
+
+
+def ps_rk2_step(coef_n: torch.Tensor, pos: torch.Tensor, dt: float,
+                coef_np1: Optional[torch.Tensor] = None, scale_n: Optional[torch.Tensor] = None,
+                scale_np1: Optional[torch.Tensor] = None, ids: Optional[torch.Tensor] = None,
+                vel_out: Optional[torch.Tensor] = None, brick=None, rebin: bool = True,
+                bin_offsets: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
+                status: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
+    """One Heun RK2 step (Sec. 2.1 / 4.3) of positions pos [3][np] in place."""
+    n = grid_of_coef(coef_n)
+    np_ = pos.shape[1]
+    _dev(coef_n, "coef_n")
+    _dev(coef_np1, "coef_np1", coef_n.dtype)
+    _dev(pos, "pos", torch.float64)
+    _dev(ids, "ids", torch.int64, np_)
+    _dev(vel_out, "vel_out", torch.float32, 3 * np_)
+    _dev(bin_offsets, "bin_offsets", torch.int32)
+    _dev(ws, "ws")
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_lib().ps_rk2_step(ctypes.byref(g), _DT[coef_n.dtype], _ptr(coef_n), _ptr(coef_np1),
+                              _ptr(scale_n), _ptr(scale_np1), np_, _ptr(pos), _ptr(ids),
+                              _ptr(vel_out), float(dt), _brick_arr(brick), 1 if rebin else 0,
+                              _ptr(bin_offsets), _ptr(ws), ws_bytes, _ptr(status),
+                              _stream(stream)))
+
+
+# ------------------------------------------------------------------ helpers ----
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """A 256-byte-aligned byte buffer (torch's caching allocator aligns to 512)."""
+    t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+class SplineField:
+    """Padded spline coefficients of a periodic field (Sec. 2.2 Operation 1)."""
+
+    def __init__(self, coef: torch.Tensor, scale: Optional[torch.Tensor], L=DEFAULT_L):
+        self.coef = coef
+        self.scale = scale
+        self.L = tuple(float(v) for v in L)
+        self.n = grid_of_coef(coef)
+        self.ncomp = coef.shape[0]
+
+    @classmethod
+    def from_field(cls, field: torch.Tensor, coef_dtype=torch.float32, L=DEFAULT_L,
+                   out: Optional["SplineField"] = None, ws: Optional[torch.Tensor] = None,
+                   stream=None) -> "SplineField":
+        n = grid_of_field(field)
+        ncomp = field.shape[0]
+        if out is None:
+            coef = torch.empty((ncomp, n[2] + 3, n[1] + 3, n[0] + 3), dtype=coef_dtype,
+                               device=field.device)
+            scale = None
+            if coef_dtype in (torch.bfloat16, torch.float16):
+                scale = torch.empty((ncomp, n[2] + 3, n[1] + 3), dtype=torch.float32,
+                                    device=field.device)
+            out = cls(coef, scale, L)
+        need = ps_spline_coeffs_workspace_size(n, ncomp, out.coef.dtype, L)
+        if need and (ws is None or ws.numel() < need):
+            ws = workspace(need, field.device)
+        ps_spline_coeffs(field, out.coef, out.scale, ws if need else None, L=L, stream=stream)
+        return out
+
+    def interp(self, pos: torch.Tensor, grad: bool = False, bins: Optional["Bins"] = None,
+               status: Optional[torch.Tensor] = None, stream=None):
+        np_ = pos.shape[1]
+        vel = torch.empty((self.ncomp, np_), dtype=torch.float32, device=pos.device)
+        g = (torch.empty((self.ncomp, 3, np_), dtype=torch.float32, device=pos.device)
+             if grad else None)
+        ps_interp(self.coef, pos, vel, scale=self.scale,
+                  perm=bins.perm if bins is not None else None,
+                  bin_offsets=bins.offsets if bins is not None else None,
+                  brick=bins.brick if bins is not None else None, grad=g, status=status,
+                  L=self.L, stream=stream)
+        return (vel, g) if grad else vel
+
+
+class Bins:
+    """Result of a bin sort: offsets per brick and (optionally) a permutation."""
+
+    def __init__(self, brick, offsets, bin_of, perm=None):
+        self.brick = brick
+        self.offsets = offsets
+        self.bin_of = bin_of
+        self.perm = perm
+
+
+def bin_particles(n, brick, pos: torch.Tensor, L=DEFAULT_L, want_perm=True,
+                  want_sorted=False, status=None, stream=None):
+    if isinstance(brick, int):
+        brick = (brick, brick, brick)
+    np_ = pos.shape[1]
+    nb = [-(-int(n[d]) // int(brick[d])) for d in range(3)]
+    dev = pos.device
+    bin_of = torch.empty(np_, dtype=torch.int32, device=dev)
+    offsets = torch.empty(nb[0] * nb[1] * nb[2] + 1, dtype=torch.int32, device=dev)
+    perm = torch.empty(np_, dtype=torch.int64, device=dev) if want_perm else None
+    pos_sorted = torch.empty_like(pos) if want_sorted else None
+    ws = workspace(ps_bin_workspace_size(n, brick, np_, L), dev)
+    ps_bin_particles(n, brick, pos, bin_of, offsets, perm, pos_sorted, ws, status, L, stream)
+    b = Bins(tuple(brick), offsets, bin_of, perm)
+    return (b, pos_sorted) if want_sorted else b
+
+
+class Tracker:
+    """Particles advanced by Heun RK2 through a (frozen or time-dependent)
+    spline field, bin-sorted into bricks every step."""
+
+    def __init__(self, field: SplineField, pos: torch.Tensor, brick=(8, 8, 8),
+                 ids: Optional[torch.Tensor] = None, keep_velocity: bool = True):
+        self.field = field
+        self.pos = pos
+        self.brick = brick if brick is None or not isinstance(brick, int) else (brick,) * 3
+        np_ = pos.shape[1]
+        self.ids = ids if ids is not None else torch.arange(np_, dtype=torch.int64,
+                                                            device=pos.device)
+        self.vel = (torch.empty((3, np_), dtype=torch.float32, device=pos.device)
+                    if keep_velocity else None)
+        self.status = torch.zeros(4, dtype=torch.int32, device=pos.device)
+        self.ws = None
+        self.offsets = None
+        if self.brick is not None:
+            nb = [-(-field.n[d] // self.brick[d]) for d in range(3)]
+            self.offsets = torch.empty(nb[0] * nb[1] * nb[2] + 1, dtype=torch.int32,
+                                       device=pos.device)
+            self.ws = workspace(ps_rk2_workspace_size(field.n, self.brick, np_, field.L),
+                                pos.device)
+
+    def step(self, dt: float, field_np1: Optional[SplineField] = None, rebin: bool = True,
+             stream=None):
+        f1 = field_np1
+        ps_rk2_step(self.field.coef, self.pos, dt,
+                    coef_np1=f1.coef if f1 is not None else None, scale_n=self.field.scale,
+                    scale_np1=f1.scale if f1 is not None else None, ids=self.ids,
+                    vel_out=self.vel, brick=self.brick, rebin=rebin, bin_offsets=self.offsets,
+                    ws=self.ws, status=self.status, L=self.field.L, stream=stream)
+
+
+class InterpFn(torch.autograd.Function):
+    """u = I(pos; spline(field)) with the hand-written adjoint:
+    d/dpos via the spline derivative, d/dfield via scatter-add + the transposed
+    (= same, symmetric) periodic solves."""
+
+    @staticmethod
+    def forward(ctx, pos: torch.Tensor, field: torch.Tensor, L=DEFAULT_L):
+        sf = SplineField.from_field(field.detach().float(), torch.float32, L)
+        vel = sf.interp(pos.detach())
+        ctx.save_for_backward(pos)
+        ctx.sf = sf
+        ctx.field_dtype = field.dtype
+        return vel
+
+    @staticmethod
+    def backward(ctx, g_vel):
+        (pos,) = ctx.saved_tensors
+        sf = ctx.sf
+        g_vel = g_vel.contiguous().float()
+        want_pos = ctx.needs_input_grad[0]
+        want_field = ctx.needs_input_grad[1]
+        g_pos = torch.empty_like(pos) if want_pos else None
+        g_field = (torch.empty((sf.ncomp, sf.n[2], sf.n[1], sf.n[0]), dtype=torch.float32,
+                               device=pos.device) if want_field else None)
+        if want_pos or want_field:
+            ps_interp_backward(sf.coef, pos.detach(), g_vel, g_pos, g_field, scale=sf.scale,
+                               L=sf.L)
+        if g_field is not None:
+            g_field = g_field.to(ctx.field_dtype)
+        return g_pos, g_field, None
+
+
+def interp_autograd(pos: torch.Tensor, field: torch.Tensor, L=DEFAULT_L) -> torch.Tensor:
+    return InterpFn.apply(pos, field, L)

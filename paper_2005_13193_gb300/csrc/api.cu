@@ -1,0 +1,114 @@
+// Host-side plumbing of the C ABI: error strings, status words, validation.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "ps_internal.cuh"
+
+namespace ps {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+ps_status fail(ps_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+ps_status check_cuda(cudaError_t err, const char* what) {
+  if (err == cudaSuccess) return PS_OK;
+  return fail(PS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+ps_status check_launch(const char* what) {
+  return check_cuda(cudaGetLastError(), what);
+}
+
+ps_status validate_grid(const ps_grid* g) {
+  if (!g) return fail(PS_ERR_INVALID_ARG, "grid is NULL");
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 3 || g->n[d] > 2048)
+      return fail(PS_ERR_INVALID_ARG, "grid n[%d]=%d outside [3, 2048]", d, g->n[d]);
+    if (!(g->L[d] > 0.0) || !std::isfinite(g->L[d]))
+      return fail(PS_ERR_INVALID_ARG, "grid L[%d] must be finite and > 0", d);
+  }
+  return PS_OK;
+}
+
+size_t dtype_size(ps_dtype t) {
+  switch (t) {
+    case PS_F32: return 4;
+    case PS_F64: return 8;
+    case PS_BF16: return 2;
+    case PS_F16: return 2;
+  }
+  return 0;
+}
+
+GridArgs make_grid_args(const ps_grid* g) {
+  GridArgs a;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g->n[d];
+    a.m[d] = g->n[d] + 3;
+    a.inv_h[d] = (double)g->n[d] / g->L[d];
+    a.inv_hf[d] = (float)a.inv_h[d];
+  }
+  return a;
+}
+
+ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* out) {
+  if (!brick) return fail(PS_ERR_INVALID_ARG, "brick is NULL");
+  int64_t nbins = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (brick[d] < 1 || brick[d] > 64)
+      return fail(PS_ERR_INVALID_ARG, "brick[%d]=%d outside [1, 64]", d, brick[d]);
+    out->B[d] = brick[d];
+    out->nb[d] = (g->n[d] + brick[d] - 1) / brick[d];
+    nbins *= out->nb[d];
+  }
+  if (nbins >= (int64_t)1 << 31) return fail(PS_ERR_INVALID_ARG, "too many bins");
+  out->nbins = nbins;
+  return PS_OK;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" const char* ps_last_error(void) { return g_err; }
+
+extern "C" const char* ps_version(void) { return "ps 0.1 (sm_103a)"; }
+
+extern "C" ps_status ps_status_clear(int32_t* status, void* stream) {
+  if (!status) return fail(PS_ERR_INVALID_ARG, "status is NULL");
+  return check_cuda(cudaMemsetAsync(status, 0, 4 * sizeof(int32_t), as_stream(stream)),
+                    "ps_status_clear");
+}
+
+extern "C" ps_status ps_status_read(const int32_t* status, int32_t* host_out,
+                                    void* stream) {
+  if (!status || !host_out) return fail(PS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = as_stream(stream);
+  ps_status rc = check_cuda(cudaMemcpyAsync(host_out, status, 4 * sizeof(int32_t),
+                                            cudaMemcpyDeviceToHost, st),
+                            "ps_status_read copy");
+  if (rc) return rc;
+  rc = check_cuda(cudaStreamSynchronize(st), "ps_status_read sync");
+  if (rc) return rc;
+  if (host_out[0] != PS_DEV_OK)
+    return fail(PS_ERR_DEVICE_STATUS, "device status %d at index %lld (%d events)",
+                host_out[0],
+                (long long)(((uint64_t)(uint32_t)host_out[2] << 32) | (uint32_t)host_out[1]),
+                host_out[3]);
+  return PS_OK;
+}

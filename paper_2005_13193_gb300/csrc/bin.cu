@@ -1,0 +1,258 @@
+// Bin sort of particles into cell bricks: the one-device reading of the
+// paper's dynamic particle-to-process mapping by instantaneous position
+// (Sec. 3) and of its per-step particle migration (Sec. 4.3).
+//
+// count:   bin of every particle; a warp-aggregated atomicAdd on the bin's
+//          counter returns the particle's rank inside its bin.
+// scan:    exclusive prefix sum of the counters -> bin_offsets (3 phases).
+// scatter: slot = bin_offsets[bin] + rank; writes perm / sorted copies.
+#include "ps_internal.cuh"
+
+namespace ps {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int bin_of_position(const GridArgs& g, const BrickArgs& b,
+                                               double x, double y, double z, bool& ok) {
+  int cx, cy, cz;
+  double t;
+  ok = locate(x, g.inv_h[0], g.n[0], cx, t);
+  ok &= locate(y, g.inv_h[1], g.n[1], cy, t);
+  ok &= locate(z, g.inv_h[2], g.n[2], cz, t);
+  if (!ok) return 0;
+  const int bx = cx / b.B[0], by = cy / b.B[1], bz = cz / b.B[2];
+  return (bz * b.nb[1] + by) * b.nb[0] + bx;
+}
+
+__global__ void bin_count_kernel(GridArgs g, BrickArgs b, int64_t np,
+                                 const double* __restrict__ pos, int32_t* __restrict__ bin_of,
+                                 int32_t* __restrict__ rank, int32_t* __restrict__ counts,
+                                 int32_t* status) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // uniform trip count per warp so that every lane reaches the warp intrinsics
+  const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t warp_start = start - lane;
+  for (int64_t base = warp_start; base < np; base += stride) {
+    const int64_t p = base + lane;
+    const bool valid = p < np;
+    int key = -1 - lane;  // unique per lane when invalid
+    if (valid) {
+      bool ok;
+      key = bin_of_position(g, b, pos[p], pos[np + p], pos[2 * np + p], ok);
+      if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+    }
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int leader = __ffs(peers) - 1;
+    const int within = __popc(peers & ((1u << lane) - 1));
+    int basev = 0;
+    if (valid && lane == leader) basev = atomicAdd(&counts[key], __popc(peers));
+    basev = __shfl_sync(peers, basev, leader);
+    if (valid) {
+      bin_of[p] = key;
+      rank[p] = basev + within;
+    }
+  }
+}
+
+// Phase 1: per-tile sums.
+__global__ void scan_tile_sums(const int32_t* __restrict__ in, int64_t n,
+                               int32_t* __restrict__ tile_sums) {
+  __shared__ int32_t red[kScanThreads / 32];
+  const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
+  int32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t idx = tile0 + (int64_t)i * kScanThreads + threadIdx.x;
+    if (idx < n) s += in[idx];
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
+    tile_sums[blockIdx.x] = t;
+  }
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int32_t block_exclusive_scan(int32_t v, int32_t& excl) {
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  int32_t woff = 0, total = 0;
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    const int32_t t = warp_tot[w];
+    if (w < warp) woff += t;
+    total += t;
+  }
+  __syncthreads();
+  excl = woff + incl - v;
+  return total;
+}
+
+// Phase 2: one block scans the tile sums in place (any count, running carry).
+__global__ void scan_tile_offsets(int32_t* tile_sums, int64_t ntiles) {
+  int32_t carry = 0;
+  for (int64_t base = 0; base < ntiles; base += kScanThreads) {
+    const int64_t idx = base + threadIdx.x;
+    const int32_t v = idx < ntiles ? tile_sums[idx] : 0;
+    int32_t excl;
+    const int32_t tot = block_exclusive_scan(v, excl);
+    if (idx < ntiles) tile_sums[idx] = carry + excl;
+    carry += tot;
+  }
+}
+
+// Phase 3: scan inside each tile, add the tile offset; out has n+1 entries.
+__global__ void scan_tiles(const int32_t* __restrict__ in, int64_t n,
+                           const int32_t* __restrict__ tile_off, int32_t* __restrict__ out) {
+  const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
+  // each thread takes kScanItems consecutive elements
+  int32_t v[kScanItems];
+  int32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t idx = tile0 + (int64_t)threadIdx.x * kScanItems + i;
+    v[i] = idx < n ? in[idx] : 0;
+    s += v[i];
+  }
+  int32_t excl;
+  const int32_t tot = block_exclusive_scan(s, excl);
+  int32_t run = tile_off[blockIdx.x] + excl;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t idx = tile0 + (int64_t)threadIdx.x * kScanItems + i;
+    if (idx < n) out[idx] = run;
+    run += v[i];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = tile_off[blockIdx.x] + tot;
+}
+
+__global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
+                                   const int32_t* __restrict__ bin_of,
+                                   const int32_t* __restrict__ rank,
+                                   const int32_t* __restrict__ offsets,
+                                   int64_t* __restrict__ perm,
+                                   double* __restrict__ pos_sorted,
+                                   const int64_t* __restrict__ ids,
+                                   int64_t* __restrict__ ids_sorted) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
+    const int64_t slot = (int64_t)offsets[bin_of[p]] + rank[p];
+    if (perm) perm[slot] = p;
+    if (pos_sorted) {
+      pos_sorted[slot] = pos[p];
+      pos_sorted[np + slot] = pos[np + p];
+      pos_sorted[2 * np + slot] = pos[2 * np + p];
+    }
+    if (ids_sorted) ids_sorted[slot] = ids[p];
+  }
+}
+
+int persistent_blocks(int64_t work, int threads) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 132;
+  }
+  int64_t need = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sms * (2048 / threads);
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+}  // namespace
+
+size_t scan_tmp_elems(int64_t nbins) { return (size_t)((nbins + kScanTile - 1) / kScanTile); }
+
+size_t bin_ws_bytes(const BrickArgs& b, int64_t np, bool need_offsets, bool need_bin_of,
+                    bool need_pos_sorted, bool need_ids) {
+  // carve order: counts, tile sums, rank, [offsets], [bin_of], [pos_sorted], [ids]
+  Carver c(nullptr);
+  c.take<int32_t>(b.nbins + 1);                  // counts
+  c.take<int32_t>(scan_tmp_elems(b.nbins) + 1);  // tile sums
+  c.take<int32_t>(np);                           // rank
+  if (need_offsets) c.take<int32_t>(b.nbins + 1);
+  if (need_bin_of) c.take<int32_t>(np);
+  if (need_pos_sorted) c.take<double>(3 * np);
+  if (need_ids) c.take<int64_t>(np);
+  return align_up(c.used, 256) + 256;
+}
+
+ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np, const double* pos,
+                  int32_t* bin_of, int32_t* bin_offsets, int64_t* perm, double* pos_sorted,
+                  const int64_t* ids, int64_t* ids_sorted, int32_t* counts, int32_t* rank,
+                  int32_t* scan_tmp, int32_t* status, cudaStream_t st) {
+  ps_status rc = check_cuda(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (ba.nbins + 1), st),
+                            "bin counts memset");
+  if (rc) return rc;
+  if (np > 0) {
+    bin_count_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(ga, ba, np, pos, bin_of,
+                                                                 rank, counts, status);
+    if ((rc = check_launch("bin_count"))) return rc;
+  }
+  const int64_t ntiles = (int64_t)scan_tmp_elems(ba.nbins);
+  scan_tile_sums<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, ba.nbins, scan_tmp);
+  if ((rc = check_launch("scan_tile_sums"))) return rc;
+  scan_tile_offsets<<<1, kScanThreads, 0, st>>>(scan_tmp, ntiles);
+  if ((rc = check_launch("scan_tile_offsets"))) return rc;
+  scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, ba.nbins, scan_tmp,
+                                                        bin_offsets);
+  if ((rc = check_launch("scan_tiles"))) return rc;
+  if (np > 0 && (perm || pos_sorted || ids_sorted)) {
+    bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
+        np, pos, bin_of, rank, bin_offsets, perm, pos_sorted, ids, ids_sorted);
+    if ((rc = check_launch("bin_scatter"))) return rc;
+  }
+  return PS_OK;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" size_t ps_bin_workspace_size(const ps_grid* grid, const int32_t brick[3],
+                                        int64_t np) {
+  BrickArgs ba;
+  if (validate_grid(grid) || make_brick_args(grid, brick, &ba) || np < 0) return 0;
+  return bin_ws_bytes(ba, np, false, false, false, false);
+}
+
+extern "C" ps_status ps_bin_particles(const ps_grid* grid, const int32_t brick[3],
+                                      int64_t np, const double* pos, int32_t* bin_of,
+                                      int32_t* bin_offsets, int64_t* perm,
+                                      double* pos_sorted, void* ws, size_t ws_bytes,
+                                      int32_t* status, void* stream) {
+  ps_status rc = validate_grid(grid);
+  if (rc) return rc;
+  BrickArgs ba;
+  if ((rc = make_brick_args(grid, brick, &ba))) return rc;
+  if (np < 0 || np >= ((int64_t)1 << 31)) return fail(PS_ERR_INVALID_ARG, "np out of range");
+  if (!bin_offsets || (np > 0 && (!pos || !bin_of)))
+    return fail(PS_ERR_INVALID_ARG, "pos, bin_of and bin_offsets are required");
+  const size_t need = bin_ws_bytes(ba, np, false, false, false, false);
+  if (!ws || ws_bytes < need - 256 || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(PS_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need - 256);
+  Carver c(ws);
+  int32_t* counts = c.take<int32_t>(ba.nbins + 1);
+  int32_t* scan_tmp = c.take<int32_t>(scan_tmp_elems(ba.nbins) + 1);
+  int32_t* rank = c.take<int32_t>(np);
+  GridArgs ga = make_grid_args(grid);
+  return bin_run(ga, ba, np, pos, bin_of, bin_offsets, perm, pos_sorted, nullptr, nullptr,
+                 counts, rank, scan_tmp, status, as_stream(stream));
+}

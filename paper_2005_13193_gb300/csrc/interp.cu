@@ -1,0 +1,717 @@
+// Operations 2 and 3 of Sec. 2.2 (basis functions and the 64-term sum of
+// Eq. (spline)), their adjoint, and the second-order Runge-Kutta particle
+// advance of Sec. 2.1 / Sec. 4.3.
+//
+// Two gather strategies:
+//  * direct: a quad of lanes per particle, lane q owning stencil column
+//    x = a_x + q; every (j,k) row is one 16-byte segment per quad.  Works for
+//    any particle order (the "unsorted" path).
+//  * staged: particles stored in brick order (Sec. 3's dynamic mapping read as
+//    a bin sort); one CTA per brick stages the brick's coefficient halo once
+//    in shared memory as float4 (u, v, w, 0) and 8 lanes per particle read it
+//    with conflict-free 128-bit loads.  This is the GPU form of the paper's
+//    "fetch only the coefficients a particle needs": the halo is the union of
+//    the stencils of the brick's particles.
+#include <cmath>
+
+#include "ps_internal.cuh"
+
+namespace ps {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T pick4(const T b[4], int q) {
+  return q == 0 ? b[0] : (q == 1 ? b[1] : (q == 2 ? b[2] : b[3]));
+}
+
+template <typename T>
+__device__ __forceinline__ T quad_sum(T v) {
+  v += __shfl_xor_sync(FULL, v, 1);
+  v += __shfl_xor_sync(FULL, v, 2);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T oct_sum(T v) {
+  v += __shfl_xor_sync(FULL, v, 1);
+  v += __shfl_xor_sync(FULL, v, 2);
+  v += __shfl_xor_sync(FULL, v, 4);
+  return v;
+}
+
+template <typename Tc>
+__device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
+                                                              const float* scale,
+                                                              const GridArgs& g, int c,
+                                                              int Pz, int Py, int Px) {
+  const int64_t m0 = g.m[0], m1 = g.m[1], m2 = g.m[2];
+  const int64_t row = ((int64_t)c * m2 + Pz) * m1 + Py;
+  typename AccOf<Tc>::type v = CoefLoad<Tc>::ld(coef + row * m0 + Px);
+  if (IsQuant<Tc>::value) v *= __ldg(scale + row);
+  return v;
+}
+
+// Locate a particle: cell indices and FP64 fractions -> basis (type A).
+template <typename A, bool GRAD>
+struct Basis {
+  int a[3];
+  A b[3][4];
+  A db[3][4];
+  __device__ __forceinline__ bool setup(const GridArgs& g, const double x[3]) {
+    bool ok = true;
+    double t[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ok &= locate(x[d], g.inv_h[d], g.n[d], a[d], t[d]);
+    if (!ok)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        a[d] = 0;
+        t[d] = 0.0;
+      }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      bspline<A>((A)t[d], b[d]);
+      if (GRAD) dbspline<A>((A)t[d], db[d]);
+    }
+    return ok;
+  }
+};
+
+// Direct gather by a quad: lane q accumulates its column over the 16 rows.
+template <typename Tc, int NC, bool GRAD, typename A>
+__device__ __forceinline__ void quad_rows(const GridArgs& g, const Tc* __restrict__ coef,
+                                          const float* __restrict__ scale,
+                                          const Basis<A, GRAD>& B, int q, A acc[NC],
+                                          A accy[NC], A accz[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = A(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const A w = B.b[1][j] * B.b[2][k];
+      A wy = A(0), wz = A(0);
+      if (GRAD) {
+        wy = B.db[1][j] * B.b[2][k];
+        wz = B.b[1][j] * B.db[2][k];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const A v = load_coef<Tc>(coef, scale, g, c, B.a[2] + k, B.a[1] + j, B.a[0] + q);
+        acc[c] += w * v;
+        if (GRAD) {
+          accy[c] += wy * v;
+          accz[c] += wz * v;
+        }
+      }
+    }
+}
+
+// MODE 0: vel; 1: vel + grad; 2: g_pos = sum_c g_vel[c] grad[c][.]
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256) interp_direct(GridArgs g, const Tc* __restrict__ coef,
+                                                     const float* __restrict__ scale,
+                                                     int64_t np,
+                                                     const double* __restrict__ pos,
+                                                     const int64_t* __restrict__ perm,
+                                                     float* __restrict__ vel,
+                                                     float* __restrict__ grad,
+                                                     const float* __restrict__ gvel,
+                                                     double* __restrict__ gpos,
+                                                     int32_t* status) {
+  using A = typename AccOf<Tc>::type;
+  constexpr bool GRAD = MODE >= 1;
+  const int q = threadIdx.x & 3;
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const bool valid = s < np;
+  const int64_t p = valid ? (perm ? perm[s] : s) : 0;
+  double x[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    x[0] = pos[p];
+    x[1] = pos[np + p];
+    x[2] = pos[2 * np + p];
+  }
+  Basis<A, GRAD> B;
+  const bool ok = B.setup(g, x);
+  A acc[NC], accy[NC], accz[NC];
+  quad_rows<Tc, NC, GRAD, A>(g, coef, scale, B, q, acc, accy, accz);
+  const A bq = pick4(B.b[0], q);
+  A u[NC], gx[NC], gy[NC], gz[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    u[c] = quad_sum(bq * acc[c]);
+    if (GRAD) {
+      const A dbq = pick4(B.db[0], q);
+      gx[c] = quad_sum(dbq * acc[c]) * (A)g.inv_h[0];
+      gy[c] = quad_sum(bq * accy[c]) * (A)g.inv_h[1];
+      gz[c] = quad_sum(bq * accz[c]) * (A)g.inv_h[2];
+    }
+  }
+  if (!valid || q != 0) return;
+  if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+  const float nanf_ = __int_as_float(0x7fc00000);
+  if (MODE <= 1) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) vel[(int64_t)c * np + p] = ok ? (float)u[c] : nanf_;
+    if (MODE == 1 && grad) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        grad[((int64_t)c * 3 + 0) * np + p] = ok ? (float)gx[c] : nanf_;
+        grad[((int64_t)c * 3 + 1) * np + p] = ok ? (float)gy[c] : nanf_;
+        grad[((int64_t)c * 3 + 2) * np + p] = ok ? (float)gz[c] : nanf_;
+      }
+    }
+  } else {
+    A sx = A(0), sy = A(0), sz = A(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const A w = (A)gvel[(int64_t)c * np + p];
+      sx += w * gx[c];
+      sy += w * gy[c];
+      sz += w * gz[c];
+    }
+    const double nand = __longlong_as_double(0x7ff8000000000000ll);
+    gpos[p] = ok ? (double)sx : nand;
+    gpos[np + p] = ok ? (double)sy : nand;
+    gpos[2 * np + p] = ok ? (double)sz : nand;
+  }
+}
+
+// Scatter-add of g_vel * basis weights onto the periodic nodes: the adjoint
+// of the 64-term sum followed by the adjoint of the periodic padding (fold).
+template <int NC>
+__global__ void __launch_bounds__(256) scatter_field(GridArgs g, int64_t np,
+                                                    const double* __restrict__ pos,
+                                                    const float* __restrict__ gvel,
+                                                    float* __restrict__ gfield,
+                                                    int32_t* status) {
+  const int q = threadIdx.x & 3;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  if (p >= np) return;  // no shuffles below
+  const double x[3] = {pos[p], pos[np + p], pos[2 * np + p]};
+  Basis<float, false> B;
+  if (!B.setup(g, x)) {
+    if (q == 0) flag_status(status, PS_DEV_NONFINITE_POS, p);
+    return;
+  }
+  float gc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) gc[c] = gvel[(int64_t)c * np + p] * pick4(B.b[0], q);
+  const int64_t vol = (int64_t)g.n[0] * g.n[1] * g.n[2];
+  const int nodex = padded_to_node(B.a[0] + q, g.n[0]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int nodez = padded_to_node(B.a[2] + k, g.n[2]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nodey = padded_to_node(B.a[1] + j, g.n[1]);
+      const float w = B.b[1][j] * B.b[2][k];
+      const int64_t off = ((int64_t)nodez * g.n[1] + nodey) * g.n[0] + nodex;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) atomicAdd(gfield + c * vol + off, w * gc[c]);
+    }
+  }
+}
+
+// Fused Heun step with direct gathers (any particle order).
+template <typename Tc>
+__global__ void __launch_bounds__(256) rk2_direct(GridArgs g, const Tc* __restrict__ c0,
+                                                  const float* __restrict__ s0,
+                                                  const Tc* __restrict__ c1,
+                                                  const float* __restrict__ s1, int64_t np,
+                                                  double* pos, float* __restrict__ vel_out,
+                                                  double dt, int32_t* status) {
+  using A = typename AccOf<Tc>::type;
+  const int q = threadIdx.x & 3;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const bool valid = p < np;
+  double x[3] = {0.0, 0.0, 0.0};
+  if (valid) {
+    x[0] = pos[p];
+    x[1] = pos[np + p];
+    x[2] = pos[2 * np + p];
+  }
+  A acc[3], ay[3], az[3];
+  Basis<A, false> B;
+  bool ok = B.setup(g, x);
+  quad_rows<Tc, 3, false, A>(g, c0, s0, B, q, acc, ay, az);
+  A bq = pick4(B.b[0], q);
+  double u1[3], xs[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u1[c] = (double)quad_sum(bq * acc[c]);
+    xs[c] = x[c] + dt * u1[c];
+  }
+  ok &= B.setup(g, xs);
+  quad_rows<Tc, 3, false, A>(g, c1, s1, B, q, acc, ay, az);
+  bq = pick4(B.b[0], q);
+  double u2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u2[c] = (double)quad_sum(bq * acc[c]);
+  if (!valid || q != 0) return;
+  if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+  const double half_dt = dt * 0.5;
+  const double nand = __longlong_as_double(0x7ff8000000000000ll);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    pos[(int64_t)c * np + p] = ok ? x[c] + half_dt * (u1[c] + u2[c]) : nand;
+    if (vel_out) vel_out[(int64_t)c * np + p] = ok ? (float)u1[c] : __int_as_float(0x7fc00000);
+  }
+}
+
+// ------------------------------------------------------------- staged ----
+
+struct StagedArgs {
+  GridArgs g;
+  BrickArgs b;
+  int E;        // extra halo cells on each side (stage-2 reach of the RK2 step)
+  int S[3];     // staged extent per axis: B + 3 + 2E
+  int PS;       // plane stride in float4 units: >= S[0]*S[1], = 4 (mod 8)
+  const void* coef;
+  const float* scale;
+  const void* coef2;  // second-stage field of an RK2 step; NULL = same as coef
+  const float* scale2;
+  int64_t np;
+  const double* pos_in;
+  double* pos_out;
+  const int64_t* perm;
+  const int32_t* offs;
+  float* vel;
+  float* grad;
+  const int64_t* ids_in;
+  int64_t* ids_out;
+  double dt;
+  int32_t* status;
+};
+
+// Stencil-local index of a cell inside the staged box starting at padded
+// index P0 (periodic), or -1 if the 4-wide stencil does not fit.
+__device__ __forceinline__ int local_index(int a, int P0, int n, int S) {
+  int la = a - P0;
+  if (la < 0) la += n;
+  else if (la >= n) la -= n;
+  return (la >= 0 && la <= S - 4) ? la : -1;
+}
+
+// 8 lanes per particle: q = x column, kh = parity of the z row; each lane
+// covers rows (j = 0..3) x (k = kh, kh+2).  Accumulators per lane.
+template <int NC, bool GRAD>
+__device__ __forceinline__ void oct_rows_smem(const float4* __restrict__ halo, int PS,
+                                              int Sx, const int l[3],
+                                              const Basis<float, GRAD>& B, int q, int kh,
+                                              float acc[NC], float accy[NC],
+                                              float accz[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
+  const float4* hp = halo + (l[2] + kh) * PS + l[1] * Sx + l[0] + q;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const float bzk = kh ? B.b[2][1 + 2 * kk] : B.b[2][2 * kk];
+    const float dbzk = GRAD ? (kh ? B.db[2][1 + 2 * kk] : B.db[2][2 * kk]) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = hp[2 * kk * PS + j * Sx];
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+      const float w = B.b[1][j] * bzk;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += w * vv[c];
+      if (GRAD) {
+        const float wy = B.db[1][j] * bzk, wz = B.b[1][j] * dbzk;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          accy[c] += wy * vv[c];
+          accz[c] += wz * vv[c];
+        }
+      }
+    }
+  }
+}
+
+template <typename Tc, int NC, bool GRAD>
+__device__ __forceinline__ void oct_rows_global(const GridArgs& g, const Tc* __restrict__ coef,
+                                                const float* __restrict__ scale,
+                                                const Basis<float, GRAD>& B, int q, int kh,
+                                                float acc[NC], float accy[NC],
+                                                float accz[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int k = kh + 2 * kk;
+    const float bzk = kh ? B.b[2][1 + 2 * kk] : B.b[2][2 * kk];
+    const float dbzk = GRAD ? (kh ? B.db[2][1 + 2 * kk] : B.db[2][2 * kk]) : 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float w = B.b[1][j] * bzk;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float v = load_coef<Tc>(coef, scale, g, c, B.a[2] + k, B.a[1] + j, B.a[0] + q);
+        acc[c] += w * v;
+        if (GRAD) {
+          accy[c] += B.db[1][j] * bzk * v;
+          accz[c] += B.b[1][j] * dbzk * v;
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T sel3(const T v[3], int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
+// MODE 0: vel; 1: vel + grad; 2: fused Heun step.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256) interp_staged(StagedArgs a) {
+  extern __shared__ float4 halo[];
+  constexpr bool GRAD = MODE == 1;
+  const int64_t bin = blockIdx.x;
+  const int beg = a.offs[bin], end = a.offs[bin + 1];
+  if (beg >= end) return;
+  const GridArgs& g = a.g;
+  const int nbx = a.b.nb[0], nby = a.b.nb[1];
+  const int bxi = (int)(bin % nbx);
+  const int byi = (int)((bin / nbx) % nby);
+  const int bzi = (int)(bin / ((int64_t)nbx * nby));
+  const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
+  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  const int64_t m0 = g.m[0], m1 = g.m[1], m2 = g.m[2];
+  const int64_t cs = m0 * m1 * m2;
+
+  // stage the brick halo: (u, v, w, 0) per padded point
+  const int tot = Sx * Sy * Sz;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int lx = idx % Sx;
+    const int r = idx / Sx;
+    const int ly = r % Sy, lz = r / Sy;
+    const int Px = wrap_interior(P0[0] + lx, g.n[0]);
+    const int Py = wrap_interior(P0[1] + ly, g.n[1]);
+    const int Pz = wrap_interior(P0[2] + lz, g.n[2]);
+    const int64_t off = ((int64_t)Pz * m1 + Py) * m0 + Px;
+    float vv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float v = (float)CoefLoad<Tc>::ld(coef + c * cs + off);
+      if (IsQuant<Tc>::value) v *= __ldg(a.scale + ((int64_t)c * m2 + Pz) * m1 + Py);
+      vv[c] = v;
+    }
+    halo[lz * a.PS + ly * Sx + lx] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, q = lane & 3, kh = (lane >> 2) & 1, grp = lane >> 3;
+  const int sub = lane & 7;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float nanf_ = __int_as_float(0x7fc00000);
+  const double nand = __longlong_as_double(0x7ff8000000000000ll);
+  for (int s0 = beg + warp * 4; s0 < end; s0 += nw * 4) {
+    const int s = s0 + grp;
+    const bool valid = s < end;
+    const int64_t slot = valid ? s : beg;
+    const int64_t p = a.perm ? a.perm[slot] : slot;
+    const int64_t np = a.np;
+    const double x[3] = {a.pos_in[p], a.pos_in[np + p], a.pos_in[2 * np + p]};
+    Basis<float, GRAD> B;
+    bool ok = B.setup(g, x);
+    int l[3];
+    bool inh = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      l[d] = local_index(B.a[d], P0[d], g.n[d], a.S[d]);
+      inh &= l[d] >= 0;
+    }
+    float acc[NC], accy[NC], accz[NC];
+    if (inh)
+      oct_rows_smem<NC, GRAD>(halo, a.PS, Sx, l, B, q, kh, acc, accy, accz);
+    else
+      oct_rows_global<Tc, NC, GRAD>(g, coef, a.scale, B, q, kh, acc, accy, accz);
+    const float bq = pick4(B.b[0], q);
+    float u[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) u[c] = oct_sum(bq * acc[c]);
+
+    if constexpr (MODE <= 1) {
+      float gx[NC], gy[NC], gz[NC];
+      if (GRAD) {
+        const float dbq = pick4(B.db[0], q);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          gx[c] = oct_sum(dbq * acc[c]) * g.inv_hf[0];
+          gy[c] = oct_sum(bq * accy[c]) * g.inv_hf[1];
+          gz[c] = oct_sum(bq * accz[c]) * g.inv_hf[2];
+        }
+      }
+      if (valid) {
+        if (!ok && sub == 0) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (sub == c) a.vel[(int64_t)c * np + p] = ok ? u[c] : nanf_;
+        if (GRAD && a.grad) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (sub == 0) a.grad[((int64_t)c * 3 + 0) * np + p] = ok ? gx[c] : nanf_;
+            if (sub == 1) a.grad[((int64_t)c * 3 + 1) * np + p] = ok ? gy[c] : nanf_;
+            if (sub == 2) a.grad[((int64_t)c * 3 + 2) * np + p] = ok ? gz[c] : nanf_;
+          }
+        }
+      }
+    } else {
+      // fused Heun step: second stage at x* = x + dt u1
+      double xs[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) xs[d] = x[d] + a.dt * (double)u[d];
+      ok &= B.setup(g, xs);
+      bool inh2 = a.coef2 == nullptr;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        l[d] = local_index(B.a[d], P0[d], g.n[d], a.S[d]);
+        inh2 &= l[d] >= 0;
+      }
+      const Tc* c2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
+      const float* sc2 = a.coef2 ? a.scale2 : a.scale;
+      if (inh2)
+        oct_rows_smem<NC, false>(halo, a.PS, Sx, l, B, q, kh, acc, accy, accz);
+      else
+        oct_rows_global<Tc, NC, false>(g, c2, sc2, B, q, kh, acc, accy, accz);
+      const float bq2 = pick4(B.b[0], q);
+      double xn[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float u2 = oct_sum(bq2 * acc[d]);
+        xn[d] = ok ? x[d] + (a.dt * 0.5) * ((double)u[d] + (double)u2) : nand;
+      }
+      if (valid) {
+        if (!ok && sub == 0) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+        if (sub < 3) a.pos_out[(int64_t)sub * np + p] = sel3(xn, sub);
+        if (a.vel && sub >= 3 && sub < 6) {
+          const int c = sub - 3;
+          a.vel[(int64_t)c * np + p] = ok ? sel3(u, c) : nanf_;
+        }
+        if (a.ids_out && sub == 6) a.ids_out[p] = a.ids_in[p];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host ----
+
+template <typename F>
+ps_status with_coef_type(ps_dtype t, F&& f) {
+  switch (t) {
+    case PS_F32: return f(float{});
+    case PS_F64: return f(double{});
+    case PS_BF16: return f(__nv_bfloat16{});
+    case PS_F16: return f(__half{});
+  }
+  return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype %d", (int)t);
+}
+
+ps_status check_coef(ps_dtype coef_t, const void* coef, const float* scale) {
+  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16)
+    return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype %d", (int)coef_t);
+  if (!coef) return fail(PS_ERR_INVALID_ARG, "coef is NULL");
+  if ((coef_t == PS_BF16 || coef_t == PS_F16) && !scale)
+    return fail(PS_ERR_INVALID_ARG, "scale required for BF16/F16 coefficients");
+  return PS_OK;
+}
+
+unsigned quad_blocks(int64_t np) { return (unsigned)((np * 4 + 255) / 256); }
+
+int plane_stride(int sx, int sy) {
+  int ps = sx * sy;
+  while ((ps & 7) != 4) ++ps;
+  return ps;
+}
+
+ps_status fill_staged(const ps_grid* grid, const int32_t brick[3], int E, StagedArgs* a,
+                      size_t* smem) {
+  ps_status rc = make_brick_args(grid, brick, &a->b);
+  if (rc) return rc;
+  a->g = make_grid_args(grid);
+  a->E = E;
+  for (int d = 0; d < 3; ++d) a->S[d] = a->b.B[d] + 3 + 2 * E;
+  a->PS = plane_stride(a->S[0], a->S[1]);
+  *smem = (size_t)a->S[2] * a->PS * sizeof(float4);
+  if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
+  return PS_OK;
+}
+
+template <typename Tc, int NC, int MODE>
+ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
+  auto kern = interp_staged<Tc, NC, MODE>;
+  if (smem > 48 * 1024) {
+    ps_status rc = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "staged smem attribute");
+    if (rc) return rc;
+  }
+  if (a.b.nbins > 0x7fffffff) return fail(PS_ERR_UNSUPPORTED, "too many bins");
+  kern<<<(unsigned)a.b.nbins, 256, smem, st>>>(a);
+  return check_launch("interp_staged");
+}
+
+}  // namespace
+
+// RK2 kernels used by ps_rk2_step (rk2.cu).
+ps_status rk2_launch_direct(const ps_grid* grid, ps_dtype coef_t, const void* c0,
+                            const float* s0, const void* c1, const float* s1, int64_t np,
+                            double* pos, float* vel_out, double dt, int32_t* status,
+                            cudaStream_t st) {
+  GridArgs g = make_grid_args(grid);
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    rk2_direct<Tc><<<quad_blocks(np), 256, 0, st>>>(g, static_cast<const Tc*>(c0), s0,
+                                                    static_cast<const Tc*>(c1), s1, np, pos,
+                                                    vel_out, dt, status);
+    return check_launch("rk2_direct");
+  });
+}
+
+ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
+                            ps_dtype coef_t, const void* c0, const float* s0,
+                            const void* c1, const float* s1, int64_t np,
+                            const double* pos_in, double* pos_out, const int32_t* offs,
+                            float* vel_out, const int64_t* ids_in, int64_t* ids_out,
+                            double dt, int32_t* status, cudaStream_t st) {
+  if (coef_t == PS_F64)
+    return fail(PS_ERR_UNSUPPORTED, "staged RK2 needs F32/BF16/F16 coefficients");
+  StagedArgs a{};
+  size_t smem;
+  ps_status rc = fill_staged(grid, brick, E, &a, &smem);
+  if (rc) return rc;
+  a.coef = c0;
+  a.scale = s0;
+  a.coef2 = c1;
+  a.scale2 = s1;
+  a.np = np;
+  a.pos_in = pos_in;
+  a.pos_out = pos_out;
+  a.offs = offs;
+  a.vel = vel_out;
+  a.ids_in = ids_in;
+  a.ids_out = ids_out;
+  a.dt = dt;
+  a.status = status;
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    if constexpr (sizeof(Tc) == 8) return PS_ERR_UNSUPPORTED;
+    else return launch_staged<Tc, 3, 2>(a, smem, st);
+  });
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
+                               const void* coef, const float* scale, int64_t np,
+                               const double* pos, const int64_t* perm,
+                               const int32_t* bin_offsets, const int32_t brick[3],
+                               float* vel, float* grad, int32_t* status, void* stream) {
+  ps_status rc = validate_grid(grid);
+  if (rc) return rc;
+  if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
+  if ((rc = check_coef(coef_t, coef, scale))) return rc;
+  if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
+  if (np == 0) return PS_OK;
+  if (!pos || !vel) return fail(PS_ERR_INVALID_ARG, "pos and vel are required");
+  if (perm && !bin_offsets) return fail(PS_ERR_INVALID_ARG, "perm needs bin_offsets");
+  if (bin_offsets && !brick) return fail(PS_ERR_INVALID_ARG, "bin_offsets needs brick");
+  cudaStream_t st = as_stream(stream);
+  GridArgs g = make_grid_args(grid);
+  const bool staged = bin_offsets && coef_t != PS_F64;
+  if (!staged) {
+    return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+      using Tc = decltype(tag);
+      const Tc* c = static_cast<const Tc*>(coef);
+      if (ncomp == 3) {
+        if (grad)
+          interp_direct<Tc, 3, 1><<<quad_blocks(np), 256, 0, st>>>(
+              g, c, scale, np, pos, perm, vel, grad, nullptr, nullptr, status);
+        else
+          interp_direct<Tc, 3, 0><<<quad_blocks(np), 256, 0, st>>>(
+              g, c, scale, np, pos, perm, vel, nullptr, nullptr, nullptr, status);
+      } else {
+        if (grad)
+          interp_direct<Tc, 1, 1><<<quad_blocks(np), 256, 0, st>>>(
+              g, c, scale, np, pos, perm, vel, grad, nullptr, nullptr, status);
+        else
+          interp_direct<Tc, 1, 0><<<quad_blocks(np), 256, 0, st>>>(
+              g, c, scale, np, pos, perm, vel, nullptr, nullptr, nullptr, status);
+      }
+      return check_launch("interp_direct");
+    });
+  }
+  StagedArgs a{};
+  size_t smem;
+  if ((rc = fill_staged(grid, brick, 0, &a, &smem))) return rc;
+  a.coef = coef;
+  a.scale = scale;
+  a.np = np;
+  a.pos_in = pos;
+  a.perm = perm;
+  a.offs = bin_offsets;
+  a.vel = vel;
+  a.grad = grad;
+  a.status = status;
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    if constexpr (sizeof(Tc) == 8) {
+      return PS_ERR_UNSUPPORTED;
+    } else {
+      if (ncomp == 3)
+        return grad ? launch_staged<Tc, 3, 1>(a, smem, st) : launch_staged<Tc, 3, 0>(a, smem, st);
+      return grad ? launch_staged<Tc, 1, 1>(a, smem, st) : launch_staged<Tc, 1, 0>(a, smem, st);
+    }
+  });
+}
+
+extern "C" ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype coef_t,
+                                        const void* coef, const float* scale, int64_t np,
+                                        const double* pos, const float* g_vel,
+                                        double* g_pos, float* g_field, void* ws,
+                                        size_t ws_bytes, int32_t* status, void* stream) {
+  (void)ws;
+  (void)ws_bytes;
+  ps_status rc = validate_grid(grid);
+  if (rc) return rc;
+  if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
+  if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
+  if (np > 0 && (!pos || !g_vel)) return fail(PS_ERR_INVALID_ARG, "pos and g_vel required");
+  cudaStream_t st = as_stream(stream);
+  GridArgs g = make_grid_args(grid);
+  if (g_pos && np > 0) {
+    if ((rc = check_coef(coef_t, coef, scale))) return rc;
+    rc = with_coef_type(coef_t, [&](auto tag) -> ps_status {
+      using Tc = decltype(tag);
+      const Tc* c = static_cast<const Tc*>(coef);
+      if (ncomp == 3)
+        interp_direct<Tc, 3, 2><<<quad_blocks(np), 256, 0, st>>>(
+            g, c, scale, np, pos, nullptr, nullptr, nullptr, g_vel, g_pos, status);
+      else
+        interp_direct<Tc, 1, 2><<<quad_blocks(np), 256, 0, st>>>(
+            g, c, scale, np, pos, nullptr, nullptr, nullptr, g_vel, g_pos, status);
+      return check_launch("interp_backward_pos");
+    });
+    if (rc) return rc;
+  }
+  if (g_field) {
+    const int64_t vol = grid_volume(grid);
+    rc = check_cuda(cudaMemsetAsync(g_field, 0, sizeof(float) * vol * ncomp, st),
+                    "g_field memset");
+    if (rc) return rc;
+    if (np > 0) {
+      if (ncomp == 3)
+        scatter_field<3><<<quad_blocks(np), 256, 0, st>>>(g, np, pos, g_vel, g_field, status);
+      else
+        scatter_field<1><<<quad_blocks(np), 256, 0, st>>>(g, np, pos, g_vel, g_field, status);
+      if ((rc = check_launch("scatter_field"))) return rc;
+    }
+    rc = solve_unpadded_inplace_f32(grid, ncomp, g_field, st);
+    if (rc) return rc;
+  }
+  return PS_OK;
+}

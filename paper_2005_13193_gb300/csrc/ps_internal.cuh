@@ -1,0 +1,183 @@
+// Internal helpers shared by the CUDA translation units of libps.
+// Nothing here is part of the public C ABI (include/ps.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ps.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------- host ----
+
+void set_error(const char* fmt, ...);
+ps_status fail(ps_status code, const char* fmt, ...);
+ps_status check_cuda(cudaError_t err, const char* what);
+// cudaGetLastError after a launch
+ps_status check_launch(const char* what);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Carves 256-byte-aligned pieces out of a caller workspace.
+struct Carver {
+  char* base;
+  size_t used = 0;
+  explicit Carver(void* p) : base(static_cast<char*>(p)) {}
+  template <typename T>
+  T* take(size_t count) {
+    used = align_up(used, 256);
+    T* out = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += count * sizeof(T);
+    return out;
+  }
+};
+
+ps_status validate_grid(const ps_grid* g);
+inline int64_t grid_volume(const ps_grid* g) {
+  return (int64_t)g->n[0] * g->n[1] * g->n[2];
+}
+inline int64_t padded_volume(const ps_grid* g) {
+  return (int64_t)(g->n[0] + 3) * (g->n[1] + 3) * (g->n[2] + 3);
+}
+size_t dtype_size(ps_dtype t);
+
+// Per-launch geometry passed by value to kernels.
+struct GridArgs {
+  int n[3];        // nodes per axis
+  int m[3];        // padded extents n+3
+  double inv_h[3]; // n/L, computed on the host in FP64
+  float inv_hf[3]; // the same, rounded to FP32 (derivative scaling)
+};
+GridArgs make_grid_args(const ps_grid* g);
+
+struct BrickArgs {
+  int B[3];   // brick edge in cells per axis
+  int nb[3];  // bricks per axis
+  int64_t nbins;
+};
+ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* out);
+
+// ------------------------------------------------------- cross-file API ----
+
+// Periodic solves in place on an unpadded F32 array [ncomp][nz][ny][nx]
+// (the transposed solve of the backward pass; the matrix is symmetric).
+ps_status solve_unpadded_inplace_f32(const ps_grid* g, int ncomp, float* a,
+                                     cudaStream_t st);
+
+// Binning pieces (bin.cu).
+size_t bin_ws_bytes(const BrickArgs& b, int64_t np, bool need_offsets,
+                    bool need_bin_of, bool need_pos_sorted, bool need_ids);
+ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np,
+                  const double* pos, int32_t* bin_of, int32_t* bin_offsets,
+                  int64_t* perm, double* pos_sorted, const int64_t* ids,
+                  int64_t* ids_sorted, int32_t* counts, int32_t* rank,
+                  int32_t* scan_tmp, int32_t* status, cudaStream_t st);
+size_t scan_tmp_elems(int64_t nbins);
+
+// -------------------------------------------------------------- device ----
+
+#ifdef __CUDACC__
+
+// Record a device-side anomaly: first code and index win, count accumulates.
+__device__ __forceinline__ void flag_status(int32_t* st, int code, int64_t idx) {
+  if (!st) return;
+  if (atomicCAS(&st[0], 0, code) == 0) {
+    st[1] = (int32_t)(uint32_t)(idx & 0xffffffffll);
+    st[2] = (int32_t)(idx >> 32);
+  }
+  atomicAdd(&st[3], 1);
+}
+
+// Operation 2, index part (Sec. 2.2): s = x * (n/L) as one rounded FP64
+// multiply, a = floor(s), t = s - a, cell = a mod n in [0, n).
+// Returns false for a non-finite position or |s| >= 1e15.
+__device__ __forceinline__ bool locate(double x, double inv_h, int n, int& cell,
+                                       double& t) {
+  double s = __dmul_rn(x, inv_h);
+  if (!(fabs(s) < 1.0e15)) {
+    cell = 0;
+    t = 0.0;
+    return false;
+  }
+  double a = floor(s);
+  t = __dsub_rn(s, a);
+  long long ai = (long long)a;
+  long long m = ai % n;
+  if (m < 0) m += n;
+  cell = (int)m;
+  return true;
+}
+
+// Uniform cubic B-spline on nodes a-1, a, a+1, a+2 at local coordinate t.
+template <typename T>
+__device__ __forceinline__ void bspline(T t, T b[4]) {
+  const T s = T(1) - t;
+  const T t2 = t * t, t3 = t2 * t;
+  const T sixth = T(1) / T(6);
+  b[0] = s * s * s * sixth;
+  b[1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+  b[2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
+  b[3] = t3 * sixth;
+}
+
+template <typename T>
+__device__ __forceinline__ void dbspline(T t, T d[4]) {
+  const T s = T(1) - t;
+  const T half = T(1) / T(2);
+  d[0] = -s * s * half;
+  d[1] = (T(3) * t * t - T(4) * t) * half;
+  d[2] = (T(-3) * t * t + T(2) * t + T(1)) * half;
+  d[3] = t * t * half;
+}
+
+// Coefficient element -> arithmetic type.
+template <typename Tc> struct CoefLoad;
+template <> struct CoefLoad<float> {
+  static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+};
+template <> struct CoefLoad<double> {
+  static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+};
+template <> struct CoefLoad<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+};
+template <> struct CoefLoad<__half> {
+  static __device__ __forceinline__ float ld(const __half* p) {
+    return __half2float(__ldg(p));
+  }
+};
+
+template <typename Tc> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+template <typename Tc> struct IsQuant { static constexpr bool value = false; };
+template <> struct IsQuant<__nv_bfloat16> { static constexpr bool value = true; };
+template <> struct IsQuant<__half> { static constexpr bool value = true; };
+
+// Padded index (possibly outside [0, n+2]) -> interior padded index holding
+// the same periodic node: node (P-1) mod n lives at P' = node + 1.
+__device__ __forceinline__ int wrap_interior(int P, int n) {
+  int m = (P - 1) % n;
+  if (m < 0) m += n;
+  return m + 1;
+}
+
+// Padded index in [0, n+2] -> periodic node (P-1) mod n.
+__device__ __forceinline__ int padded_to_node(int P, int n) {
+  int m = P - 1;
+  if (m < 0) m += n;
+  else if (m >= n) m -= n;
+  return m;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace ps

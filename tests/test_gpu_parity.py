@@ -1,0 +1,315 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (derived from the arithmetic):
+  * coefficients (FP32): each pencil pass is a pair of first-order recursions
+    with |z| = 0.268 and gain 1.61; rounding grows by a few ulp per pass, so
+    |c_gpu - c_ora| <= 2e-6 * max|field| (about 30 ulp of the largest value).
+  * interpolation (FP32): max |u_gpu - u_ora| <= 1e-5 * rms(u_ora) -- the bar
+    the method is held to.  64 non-negative weights summing to 1 bound the
+    accumulation error by ~64 ulp of max|c|.
+  * gradients: the derivative weights sum in absolute value to < 3 per axis,
+    times n/L: |g_gpu - g_ora| <= 1e-5 * 3 * (n/L) * max|c|.
+  * cell indices, bins, offsets, permutations: bit-exact / set-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2005_13193_gb300 as ps
+from paper_2005_13193_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+TWO_PI = 2 * math.pi
+
+
+def rel_err(gpu, ref):
+    ref = np.asarray(ref)
+    rms = np.sqrt((ref ** 2).mean())
+    return np.abs(np.asarray(gpu, dtype=np.float64) - ref).max() / rms
+
+
+def coef_tol(field):
+    return 2e-6 * float(np.abs(field).max())
+
+
+# ------------------------------------------------------------------ solve ----
+
+@pytest.mark.parametrize("n", [(3, 3, 3), (4, 5, 6), (12, 10, 9), (32, 32, 32), (37, 33, 40),
+                               (100, 7, 65)])
+def test_spline_coeffs_f32(n):
+    field = synth.random_field(n, ncomp=3, seed=sum(n))
+    ref = oracle.spline_coeffs(field)
+    f = torch.from_numpy(field.astype(np.float32)).to(DEV)
+    sf = ps.SplineField.from_field(f, torch.float32)
+    ref32 = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
+    got = sf.coef.cpu().numpy()
+    assert got.shape == ref.shape
+    assert np.abs(got - ref32).max() <= coef_tol(field)
+
+
+def test_spline_coeffs_f64_field_and_coef():
+    n = (24, 20, 18)
+    field = synth.random_field(n, ncomp=3, seed=5)
+    ref = oracle.spline_coeffs(field)
+    f = torch.from_numpy(field).to(DEV)
+    c64 = ps.SplineField.from_field(f, torch.float64).coef.cpu().numpy()
+    assert np.abs(c64 - ref).max() <= 1e-13 * np.abs(field).max()
+    c32 = ps.SplineField.from_field(f, torch.float32).coef.cpu().numpy()
+    assert np.abs(c32 - ref).max() <= coef_tol(field)
+
+
+@pytest.mark.parametrize("n", [64, 200, 512, 700, 1100, 1536])
+def test_spline_coeffs_long_pencils(n):
+    # pencil lengths that select every chunking configuration of the passes
+    dims = (n, 5, 4) if n > 600 else (n, 9, 7)
+    for perm in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        shape = tuple(dims[p] for p in perm)
+        field = synth.random_field(shape, ncomp=1, seed=n + perm[0])
+        f = torch.from_numpy(field.astype(np.float32)).to(DEV)
+        got = ps.SplineField.from_field(f, torch.float32).coef.cpu().numpy()
+        ref = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
+        assert np.abs(got - ref).max() <= coef_tol(field), shape
+
+
+# ---------------------------------------------------------------- binning ----
+
+@pytest.mark.parametrize("n,brick", [((32, 32, 32), (8, 8, 8)), ((37, 20, 9), (8, 4, 5)),
+                                     ((16, 16, 16), (1, 1, 1)), ((64, 48, 40), (16, 16, 16)),
+                                     ((10, 10, 10), (3, 7, 10))])
+def test_binning_bit_exact(n, brick):
+    L = (TWO_PI, 3.5, 1.25)
+    pos = synth.uniform_particles(5000, seed=7)
+    pos = pos / TWO_PI * np.array(L)[:, None] * 2.2 - np.array(L)[:, None] * 0.6
+    b_ora, off_ora, perm_ora = oracle.bin_particles(n, brick, pos, L=L)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins, sorted_pos = ps.bin_particles(n, brick, pg, L=L, want_sorted=True)
+    np.testing.assert_array_equal(bins.bin_of.cpu().numpy(), b_ora)
+    off = bins.offsets.cpu().numpy()
+    np.testing.assert_array_equal(off, off_ora)
+    perm = bins.perm.cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(5000))
+    for b in range(len(off) - 1):
+        assert set(perm[off[b]:off[b + 1]]) == set(perm_ora[off[b]:off[b + 1]])
+    np.testing.assert_array_equal(sorted_pos.cpu().numpy(), pos[:, perm])
+
+
+def test_binning_empty_and_single():
+    n, brick = (16, 16, 16), (8, 8, 8)
+    pg = torch.empty((3, 0), dtype=torch.float64, device=DEV)
+    bins = ps.bin_particles(n, brick, pg)
+    assert bins.offsets.cpu().tolist() == [0] * 9
+    pos = np.array([[1.0], [2.0], [6.0]])
+    bins = ps.bin_particles(n, brick, torch.from_numpy(pos).to(DEV))
+    _, off_ora, _ = oracle.bin_particles(n, brick, pos)
+    np.testing.assert_array_equal(bins.offsets.cpu().numpy(), off_ora)
+
+
+# ----------------------------------------------------------------- interp ----
+
+def _case(n, np_, seed, L=(TWO_PI,) * 3, ncomp=3, spread=1.0):
+    field = synth.random_field(n, ncomp=ncomp, seed=seed).astype(np.float32)
+    pos = synth.uniform_particles(np_, seed=seed + 1)
+    pos = pos / TWO_PI * np.array(L)[:, None] * spread
+    coef_ref = oracle.spline_coeffs(field.astype(np.float64))
+    return field, pos, coef_ref
+
+
+@pytest.mark.parametrize("n,np_", [((32, 32, 32), 4096), ((37, 21, 10), 3001), ((3, 4, 5), 257),
+                                   ((64, 64, 64), 1)])
+def test_interp_direct(n, np_):
+    L = (TWO_PI, 4.0, 2.5)
+    field, pos, cref = _case(n, np_, seed=11, L=L, spread=1.7)
+    ref = oracle.interp(cref, pos, L=L)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32, L=L)
+    vel = sf.interp(torch.from_numpy(pos).to(DEV)).cpu().numpy()
+    assert rel_err(vel, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("brick", [(8, 8, 8), (4, 4, 4), (16, 8, 4), (5, 7, 3), (1, 1, 1)])
+def test_interp_staged_sorted_and_perm(brick):
+    n = (40, 36, 33)
+    field, pos, cref = _case(n, 20000, seed=21, spread=2.0)
+    ref = oracle.interp(cref, pos)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins, sorted_pos = ps.bin_particles(n, brick, pg, want_sorted=True)
+    # via the permutation, outputs in the original order
+    vel = sf.interp(pg, bins=bins).cpu().numpy()
+    assert rel_err(vel, ref) <= 1e-5
+    # physically sorted storage
+    bins_sorted = ps.Bins(bins.brick, bins.offsets, bins.bin_of, None)
+    vel_s = sf.interp(sorted_pos, bins=bins_sorted).cpu().numpy()
+    perm = bins.perm.cpu().numpy()
+    assert rel_err(vel_s, ref[:, perm]) <= 1e-5
+
+
+def test_interp_stale_bins_fall_back_correctly():
+    # bins computed for other positions: every particle takes the global path
+    n = (32, 32, 32)
+    field, pos, cref = _case(n, 3000, seed=31)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins = ps.bin_particles(n, (8, 8, 8), pg)
+    moved = (pos + 1.3) % TWO_PI
+    vel = sf.interp(torch.from_numpy(moved).to(DEV), bins=bins).cpu().numpy()
+    assert rel_err(vel, oracle.interp(cref, moved)) <= 1e-5
+
+
+def test_interp_scalar_component():
+    n = (20, 24, 28)
+    field, pos, cref = _case(n, 2000, seed=41, ncomp=1)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    pg = torch.from_numpy(pos).to(DEV)
+    ref = oracle.interp(cref, pos)
+    assert rel_err(sf.interp(pg).cpu().numpy(), ref) <= 1e-5
+    bins = ps.bin_particles(n, 8, pg)
+    assert rel_err(sf.interp(pg, bins=bins).cpu().numpy(), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("staged", [False, True])
+def test_gradient_tensor(staged):
+    n = (32, 28, 24)
+    L = (TWO_PI, 5.0, 3.0)
+    field, pos, cref = _case(n, 4096, seed=51, L=L)
+    ref_v, ref_g = oracle.interp(cref, pos, L=L, grad=True)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32, L=L)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins = ps.bin_particles(n, 8, pg, L=L) if staged else None
+    vel, grad = sf.interp(pg, grad=True, bins=bins)
+    assert rel_err(vel.cpu().numpy(), ref_v) <= 1e-5
+    cmax = np.abs(cref).max()
+    for d in range(3):
+        tol = 1e-5 * 3 * (n[d] / L[d]) * cmax
+        assert np.abs(grad[:, d].cpu().numpy() - ref_g[:, d]).max() <= tol
+
+
+def test_f64_coefficients_tight():
+    n = (16, 18, 20)
+    field = synth.random_field(n, ncomp=3, seed=61)
+    pos = synth.uniform_particles(1000, seed=62) * 1.3
+    ref = oracle.interp(oracle.spline_coeffs(field), pos)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float64)
+    vel = sf.interp(torch.from_numpy(pos).to(DEV)).cpu().numpy()
+    # FP64 coefficients, FP64 accumulation, FP32 output rounding only
+    assert rel_err(vel, ref) <= 5e-7
+
+
+@pytest.mark.parametrize("dtype,bound", [(torch.bfloat16, 1e-2), (torch.float16, 1e-3)])
+def test_low_precision_coefficients(dtype, bound):
+    n = (48, 48, 48)
+    field = synth.spectral_field(48, kmax=16, seed=71, device="cpu", dtype=torch.float64).numpy()
+    field32 = field.astype(np.float32)
+    pos = synth.uniform_particles(8192, seed=72)
+    ref = oracle.interp(oracle.spline_coeffs(field32.astype(np.float64)), pos)
+    sf = ps.SplineField.from_field(torch.from_numpy(field32).to(DEV), dtype)
+    assert sf.scale is not None
+    sc = sf.scale.cpu().numpy()
+    assert np.all(np.log2(sc) == np.round(np.log2(sc)))  # powers of two
+    pg = torch.from_numpy(pos).to(DEV)
+    err = rel_err(sf.interp(pg).cpu().numpy(), ref)
+    assert err <= bound, err
+    bins = ps.bin_particles(n, 8, pg)
+    assert rel_err(sf.interp(pg, bins=bins).cpu().numpy(), ref) <= bound
+
+
+def test_nonfinite_position_flagged():
+    n = (16, 16, 16)
+    field, pos, cref = _case(n, 100, seed=81)
+    pos[0, 7] = np.nan
+    pos[2, 40] = np.inf
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    st = torch.zeros(4, dtype=torch.int32, device=DEV)
+    pg = torch.from_numpy(pos).to(DEV)
+    vel = sf.interp(pg, status=st).cpu().numpy()
+    code, lo, hi, count = ps.ps_status_read(st)
+    assert code == ps._abi.PS_DEV_NONFINITE_POS and count == 2 and lo in (7, 40)
+    assert np.isnan(vel[:, [7, 40]]).all()
+    good = np.ones(100, bool)
+    good[[7, 40]] = False
+    ref = oracle.interp(cref, pos[:, good])
+    assert rel_err(vel[:, good], ref) <= 1e-5
+    # binning puts them in bin 0 and flags them too
+    st.zero_()
+    bins = ps.bin_particles(n, 8, pg, status=st)
+    assert ps.ps_status_read(st)[0] == ps._abi.PS_DEV_NONFINITE_POS
+    assert set(bins.bin_of.cpu().numpy()[[7, 40]]) == {0}
+
+
+# --------------------------------------------------------------- backward ----
+
+def test_backward_positions_and_field():
+    n = (20, 18, 16)
+    field, pos, cref = _case(n, 3000, seed=91)
+    w = np.random.default_rng(92).standard_normal((3, 3000)).astype(np.float32)
+    gp_ref, gf_ref = oracle.interp_backward(cref, pos, w.astype(np.float64))
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    pg = torch.from_numpy(pos).to(DEV)
+    g_pos = torch.empty_like(pg)
+    g_field = torch.empty((3,) + tuple(reversed(n)), dtype=torch.float32, device=DEV)
+    ps.ps_interp_backward(sf.coef, pg, torch.from_numpy(w).to(DEV), g_pos, g_field)
+    gp = g_pos.cpu().numpy()
+    scale_p = 3 * (n[0] / TWO_PI) * np.abs(cref).max() * np.abs(w).max() * 3
+    assert np.abs(gp - gp_ref).max() <= 1e-5 * scale_p
+    gf = g_field.cpu().numpy()
+    # scatter of 3000 * 64 weights with FP32 atomics, then three FP32 passes
+    assert np.abs(gf - gf_ref).max() <= 1e-5 * np.abs(gf_ref).max() + 1e-6
+
+
+def test_autograd_matches_oracle_and_fd():
+    n = (16, 16, 16)
+    field, pos, cref = _case(n, 512, seed=93)
+    w = np.random.default_rng(94).standard_normal((3, 512))
+    f = torch.from_numpy(field).to(DEV).requires_grad_(True)
+    p = torch.from_numpy(pos).to(DEV).requires_grad_(True)
+    vel = ps.interp_autograd(p, f)
+    loss = (vel.double() * torch.from_numpy(w).to(DEV)).sum()
+    loss.backward()
+    gp_ref, gf_ref = oracle.interp_backward(cref, pos, w)
+    assert np.abs(p.grad.cpu().numpy() - gp_ref).max() <= 1e-4 * np.abs(gp_ref).max()
+    assert np.abs(f.grad.cpu().numpy() - gf_ref).max() <= 1e-5 * np.abs(gf_ref).max() + 1e-6
+
+
+# -------------------------------------------------------------------- RK2 ----
+
+@pytest.mark.parametrize("brick", [None, (8, 8, 8), (4, 4, 4)])
+def test_rk2_step(brick):
+    n = (32, 32, 32)
+    field, pos, cref = _case(n, 8000, seed=101)
+    dt = 1e-2  # large enough that x* leaves the brick halo for some particles
+    new_ref, u1_ref = oracle.rk2_step(cref, pos, dt)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick)
+    tr.step(dt)
+    ids = tr.ids.cpu().numpy()
+    assert np.array_equal(np.sort(ids), np.arange(8000))
+    rms = np.sqrt((u1_ref ** 2).mean())
+    got = tr.pos.cpu().numpy()
+    assert np.abs(got - new_ref[:, ids]).max() <= dt * 1e-5 * rms + 1e-14
+    assert rel_err(tr.vel.cpu().numpy(), u1_ref[:, ids]) <= 1e-5
+    if brick is not None:
+        # the new storage order is the bin order of x^n
+        b_ora, off_ora, _ = oracle.bin_particles(n, brick, pos)
+        np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
+        assert np.all(np.diff(b_ora[ids]) >= 0)
+
+
+def test_rk2_multi_step_and_time_dependent():
+    n = (24, 24, 24)
+    field, pos, cref = _case(n, 4000, seed=111)
+    field2 = synth.random_field(n, ncomp=3, seed=112).astype(np.float32)
+    cref2 = oracle.spline_coeffs(field2.astype(np.float64))
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    sf2 = ps.SplineField.from_field(torch.from_numpy(field2).to(DEV), torch.float32)
+    tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=(8, 8, 8))
+    ref = pos.copy()
+    dt = 5e-3
+    for step in range(4):
+        two = step % 2 == 1
+        tr.step(dt, field_np1=sf2 if two else None)
+        ref, _ = oracle.rk2_step(cref, ref, dt, coef_np1=cref2 if two else None)
+    ids = tr.ids.cpu().numpy()
+    assert np.abs(tr.pos.cpu().numpy() - ref[:, ids]).max() <= 4 * dt * 3e-5 * 3 + 1e-13
