@@ -56,7 +56,21 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    return ap.parse_args()
+    # smaller cases of the same workload (profiling captures); defaults = mid
+    ap.add_argument("--grid", type=int, default=None)
+    ap.add_argument("--particles", type=int, default=None)
+    ap.add_argument("--rk-steps", type=int, default=None)
+    args = ap.parse_args()
+    global N, NP, RK_STEPS, KMAX, LAUNCHES_PER_STEP, WORKLOAD
+    if args.grid or args.particles or args.rk_steps:
+        N = args.grid or N
+        NP = args.particles or NP
+        RK_STEPS = args.rk_steps or RK_STEPS
+        KMAX = N // 3
+        LAUNCHES_PER_STEP = 3 + RK_STEPS * 6
+        WORKLOAD = (f"reduced case: {N}^3 FP32 u,v,w (k^-5/3, 1<=|k|<={KMAX}), {NP} particles, "
+                    f"solve + {RK_STEPS} RK2 steps, 8^3 bricks")
+    return args
 
 
 def measured_peaks():

@@ -43,8 +43,9 @@
 #define ORA_ERR_NONFINITE 2
 #define ORA_ERR_NOMEM 3
 
-/* |x * N/L| beyond this is rejected: the cell index must fit in int64 exactly. */
-#define ORA_MAX_ABS_S 1.0e15
+/* |x * N/L| >= 2^50 is rejected (an implementation limit the paper does not
+ * set): the cell index and the fraction are then exact in FP64 arithmetic. */
+#define ORA_MAX_ABS_S 1125899906842624.0
 
 int ora_num_threads(void) {
 #ifdef _OPENMP

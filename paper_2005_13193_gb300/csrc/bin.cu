@@ -18,7 +18,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 __device__ __forceinline__ int bin_of_position(const GridArgs& g, const BrickArgs& b,
                                                double x, double y, double z, bool& ok) {
   int cx, cy, cz;
-  double t;
+  float t;
   ok = locate(x, g.inv_h[0], g.n[0], cx, t);
   ok &= locate(y, g.inv_h[1], g.n[1], cy, t);
   ok &= locate(z, g.inv_h[2], g.n[2], cz, t);

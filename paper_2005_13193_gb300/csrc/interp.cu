@@ -7,12 +7,18 @@
 //    x = a_x + q; every (j,k) row is one 16-byte segment per quad.  Works for
 //    any particle order (the "unsorted" path).
 //  * staged: particles stored in brick order (Sec. 3's dynamic mapping read as
-//    a bin sort); one CTA per brick stages the brick's coefficient halo once
-//    in shared memory as float4 (u, v, w, 0) and 8 lanes per particle read it
-//    with conflict-free 128-bit loads.  This is the GPU form of the paper's
-//    "fetch only the coefficients a particle needs": the halo is the union of
-//    the stencils of the brick's particles.
+//    a bin sort); one CTA per brick copies the brick's coefficient halo once
+//    into shared memory as float4 (u, v, w, 0), and 8 lanes per particle read
+//    it with conflict-free 128-bit loads.  This is the GPU form
+//    of the paper's "fetch only the coefficients a particle needs": the halo
+//    is the union of the stencils of the brick's particles.
+//
+// FP64 work per particle is one multiply per axis (done by three lanes in
+// parallel); floor and fraction come from the bits of the product, the RK2
+// predictor position is located in FP32 relative to the stage-1 cell, and the
+// position update is one FMA per axis.
 #include <cmath>
+#include <type_traits>
 
 #include "ps_internal.cuh"
 
@@ -25,18 +31,15 @@ template <typename T>
 __device__ __forceinline__ T pick4(const T b[4], int q) {
   return q == 0 ? b[0] : (q == 1 ? b[1] : (q == 2 ? b[2] : b[3]));
 }
-
 template <typename T>
-__device__ __forceinline__ T quad_sum(T v) {
-  v += __shfl_xor_sync(FULL, v, 1);
-  v += __shfl_xor_sync(FULL, v, 2);
-  return v;
+__device__ __forceinline__ T sel3(const T v[3], int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
 }
-template <typename T>
-__device__ __forceinline__ T oct_sum(T v) {
-  v += __shfl_xor_sync(FULL, v, 1);
-  v += __shfl_xor_sync(FULL, v, 2);
-  v += __shfl_xor_sync(FULL, v, 4);
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1) v += __shfl_xor_sync(FULL, v, d);
   return v;
 }
 
@@ -52,31 +55,68 @@ __device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
   return v;
 }
 
-// Locate a particle: cell indices and FP64 fractions -> basis (type A).
+// The first three lanes of each group of G lanes locate one axis each; the
+// cell indices and fractions are broadcast to the whole group.  xd returns
+// the FP64 coordinate of the lane's own axis (lanes 0..2 of the group).
+template <int G, typename A>
+__device__ __forceinline__ bool locate_group(const GridArgs& g, const double* pos, int64_t np,
+                                             int64_t p, int lane, int cell[3], A t[3],
+                                             double& xd) {
+  const int sub = lane & (G - 1), base = lane & ~(G - 1);
+  int cd = 0;
+  A td = A(0);
+  xd = 0.0;
+  if (sub < 3) {
+    xd = pos[sub * np + p];
+    bool okd;
+    if constexpr (std::is_same<A, double>::value)
+      okd = locate_f64(xd, g.inv_h[sub], g.n[sub], cd, td);
+    else
+      okd = locate(xd, g.inv_h[sub], g.n[sub], cd, td);
+    if (!okd) cd = -1;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    cell[d] = __shfl_sync(FULL, cd, base + d);
+    t[d] = __shfl_sync(FULL, td, base + d);
+    ok &= cell[d] >= 0;
+    cell[d] = max(cell[d], 0);
+  }
+  return ok;
+}
+
 template <typename A, bool GRAD>
 struct Basis {
   int a[3];
   A b[3][4];
   A db[3][4];
-  __device__ __forceinline__ bool setup(const GridArgs& g, const double x[3]) {
-    bool ok = true;
-    double t[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) ok &= locate(x[d], g.inv_h[d], g.n[d], a[d], t[d]);
-    if (!ok)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        a[d] = 0;
-        t[d] = 0.0;
-      }
+  __device__ __forceinline__ void set(const int cell[3], const A t[3]) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      bspline<A>((A)t[d], b[d]);
-      if (GRAD) dbspline<A>((A)t[d], db[d]);
+      a[d] = cell[d];
+      bspline<A>(t[d], b[d]);
+      if (GRAD) dbspline<A>(t[d], db[d]);
     }
-    return ok;
   }
 };
+
+// Predictor position of a Heun step located in FP32 relative to the stage-1
+// cell: t* = t + u dt n/L, cell* = cell + floor(t*) (mod n).
+__device__ __forceinline__ void advance_cell(int n, int cell, float t, float du, int& c2,
+                                             float& t2) {
+  float tt = t + du;
+  float fl = floorf(tt);
+  if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;  // non-finite velocity: keep the cell
+  tt -= fl;
+  int c = cell + (int)fl;
+  if (c < 0 || c >= n) {
+    c %= n;
+    if (c < 0) c += n;
+  }
+  c2 = c;
+  t2 = fminf(fmaxf(tt, 0.f), 1.f);
+}
 
 // Direct gather by a quad: lane q accumulates its column over the 16 rows.
 template <typename Tc, int NC, bool GRAD, typename A>
@@ -122,30 +162,28 @@ __global__ void __launch_bounds__(256) interp_direct(GridArgs g, const Tc* __res
                                                      int32_t* status) {
   using A = typename AccOf<Tc>::type;
   constexpr bool GRAD = MODE >= 1;
-  const int q = threadIdx.x & 3;
+  const int lane = threadIdx.x & 31, q = lane & 3;
   const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   const bool valid = s < np;
   const int64_t p = valid ? (perm ? perm[s] : s) : 0;
-  double x[3] = {0.0, 0.0, 0.0};
-  if (valid) {
-    x[0] = pos[p];
-    x[1] = pos[np + p];
-    x[2] = pos[2 * np + p];
-  }
+  int cell[3];
+  A t[3];
+  double xd;
+  const bool ok = locate_group<4, A>(g, pos, valid ? np : 0, p, lane, cell, t, xd) || !valid;
   Basis<A, GRAD> B;
-  const bool ok = B.setup(g, x);
+  B.set(cell, t);
   A acc[NC], accy[NC], accz[NC];
   quad_rows<Tc, NC, GRAD, A>(g, coef, scale, B, q, acc, accy, accz);
   const A bq = pick4(B.b[0], q);
   A u[NC], gx[NC], gy[NC], gz[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    u[c] = quad_sum(bq * acc[c]);
+    u[c] = group_sum<4>(bq * acc[c]);
     if (GRAD) {
       const A dbq = pick4(B.db[0], q);
-      gx[c] = quad_sum(dbq * acc[c]) * (A)g.inv_h[0];
-      gy[c] = quad_sum(bq * accy[c]) * (A)g.inv_h[1];
-      gz[c] = quad_sum(bq * accz[c]) * (A)g.inv_h[2];
+      gx[c] = group_sum<4>(dbq * acc[c]) * (A)g.inv_h[0];
+      gy[c] = group_sum<4>(bq * accy[c]) * (A)g.inv_h[1];
+      gz[c] = group_sum<4>(bq * accz[c]) * (A)g.inv_h[2];
     }
   }
   if (!valid || q != 0) return;
@@ -186,15 +224,21 @@ __global__ void __launch_bounds__(256) scatter_field(GridArgs g, int64_t np,
                                                     const float* __restrict__ gvel,
                                                     float* __restrict__ gfield,
                                                     int32_t* status) {
-  const int q = threadIdx.x & 3;
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-  if (p >= np) return;  // no shuffles below
-  const double x[3] = {pos[p], pos[np + p], pos[2 * np + p]};
-  Basis<float, false> B;
-  if (!B.setup(g, x)) {
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const bool valid = p0 < np;
+  const int64_t p = valid ? p0 : 0;
+  int cell[3];
+  float t[3];
+  double xd;
+  const bool ok = locate_group<4, float>(g, pos, valid ? np : 0, p, lane, cell, t, xd);
+  if (!valid) return;  // no shuffles below
+  if (!ok) {
     if (q == 0) flag_status(status, PS_DEV_NONFINITE_POS, p);
     return;
   }
+  Basis<float, false> B;
+  B.set(cell, t);
   float gc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) gc[c] = gvel[(int64_t)c * np + p] * pick4(B.b[0], q);
@@ -221,42 +265,55 @@ __global__ void __launch_bounds__(256) rk2_direct(GridArgs g, const Tc* __restri
                                                   const Tc* __restrict__ c1,
                                                   const float* __restrict__ s1, int64_t np,
                                                   double* pos, float* __restrict__ vel_out,
-                                                  double dt, int32_t* status) {
+                                                  double dt, float3 dtih, int32_t* status) {
   using A = typename AccOf<Tc>::type;
-  const int q = threadIdx.x & 3;
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-  const bool valid = p < np;
-  double x[3] = {0.0, 0.0, 0.0};
-  if (valid) {
-    x[0] = pos[p];
-    x[1] = pos[np + p];
-    x[2] = pos[2 * np + p];
-  }
-  A acc[3], ay[3], az[3];
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const bool valid = p0 < np;
+  const int64_t p = valid ? p0 : 0;
+  int cell[3];
+  A t[3];
+  double xd;
+  bool ok = locate_group<4, A>(g, pos, valid ? np : 0, p, lane, cell, t, xd);
   Basis<A, false> B;
-  bool ok = B.setup(g, x);
+  B.set(cell, t);
+  A acc[3], ay[3], az[3];
   quad_rows<Tc, 3, false, A>(g, c0, s0, B, q, acc, ay, az);
   A bq = pick4(B.b[0], q);
-  double u1[3], xs[3];
+  A u1[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    u1[c] = (double)quad_sum(bq * acc[c]);
-    xs[c] = x[c] + dt * u1[c];
+  for (int c = 0; c < 3; ++c) u1[c] = group_sum<4>(bq * acc[c]);
+  const float dti[3] = {dtih.x, dtih.y, dtih.z};
+  int c2[3];
+  A t2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if constexpr (std::is_same<A, double>::value) {
+      // FP64 coefficients: locate the predictor exactly as x + dt u1
+      double xs = __shfl_sync(FULL, xd, (lane & ~3) + d) + dt * u1[d];
+      double tt;
+      ok &= locate_f64(xs, g.inv_h[d], g.n[d], c2[d], tt);
+      t2[d] = tt;
+    } else {
+      float tt;
+      advance_cell(g.n[d], cell[d], t[d], ok ? (float)u1[d] * dti[d] : 0.f, c2[d], tt);
+      t2[d] = tt;
+    }
   }
-  ok &= B.setup(g, xs);
+  B.set(c2, t2);
   quad_rows<Tc, 3, false, A>(g, c1, s1, B, q, acc, ay, az);
   bq = pick4(B.b[0], q);
-  double u2[3];
+  A u2[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) u2[c] = (double)quad_sum(bq * acc[c]);
-  if (!valid || q != 0) return;
-  if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
-  const double half_dt = dt * 0.5;
-  const double nand = __longlong_as_double(0x7ff8000000000000ll);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    pos[(int64_t)c * np + p] = ok ? x[c] + half_dt * (u1[c] + u2[c]) : nand;
-    if (vel_out) vel_out[(int64_t)c * np + p] = ok ? (float)u1[c] : __int_as_float(0x7fc00000);
+  for (int c = 0; c < 3; ++c) u2[c] = group_sum<4>(bq * acc[c]);
+  if (!valid) return;
+  if (!ok && q == 0) flag_status(status, PS_DEV_NONFINITE_POS, p);
+  if (q < 3) {
+    const double nand = __longlong_as_double(0x7ff8000000000000ll);
+    const double w = (double)(sel3(u1, q) + sel3(u2, q));
+    pos[(int64_t)q * np + p] = ok ? fma(dt * 0.5, w, xd) : nand;
+    if (vel_out)
+      vel_out[(int64_t)q * np + p] = ok ? (float)sel3(u1, q) : __int_as_float(0x7fc00000);
   }
 }
 
@@ -265,7 +322,7 @@ __global__ void __launch_bounds__(256) rk2_direct(GridArgs g, const Tc* __restri
 struct StagedArgs {
   GridArgs g;
   BrickArgs b;
-  int E;        // extra halo cells on each side (stage-2 reach of the RK2 step)
+  int E;        // extra halo cells on each side
   int S[3];     // staged extent per axis: B + 3 + 2E
   int PS;       // plane stride in float4 units: >= S[0]*S[1], = 4 (mod 8)
   const void* coef;
@@ -282,16 +339,78 @@ struct StagedArgs {
   const int64_t* ids_in;
   int64_t* ids_out;
   double dt;
+  float dtih[3];  // dt * n/L per axis
   int32_t* status;
 };
 
 // Stencil-local index of a cell inside the staged box starting at padded
-// index P0 (periodic), or -1 if the 4-wide stencil does not fit.
-__device__ __forceinline__ int local_index(int a, int P0, int n, int S) {
-  int la = a - P0;
-  if (la < 0) la += n;
-  else if (la >= n) la -= n;
-  return (la >= 0 && la <= S - 4) ? la : -1;
+// index P0, or -1 if the 4-wide stencil does not fit.  Particles of the brick
+// itself always fit; anything else (a stale bin, a predictor that left the
+// brick) is served from global memory instead.
+__device__ __forceinline__ int local_index(int a, int P0, int S) {
+  const int la = a - P0;
+  return (unsigned)la <= (unsigned)(S - 4) ? la : -1;
+}
+
+// Padded index (any integer) -> interior padded index of the same node.
+__device__ __forceinline__ int wrap_row(int P, int n) {
+  while (P < 1) P += n;
+  while (P > n) P -= n;
+  return P;
+}
+
+// Copy the brick halo (S[0] x S[1] x S[2] padded points) into shared memory
+// as float4 (u, v, w, 0) per point.  16 (or 32) lanes walk x within a row,
+// the block covers 16 (or 8) rows at a time; each thread loads four rows
+// before storing them so that the loads overlap.
+template <typename Tc, int NC>
+__device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __restrict__ coef,
+                                           const int P0[3], float4* halo) {
+  const GridArgs& g = a.g;
+  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
+  const bool narrow = Sx <= 16;
+  const int tx = narrow ? (threadIdx.x & 15) : (threadIdx.x & 31);
+  const int ty = narrow ? (threadIdx.x >> 4) : (threadIdx.x >> 5);
+  const int RS = narrow ? 16 : 8;  // rows covered by the block per step
+  const bool xact = tx < Sx;
+  const int Px = wrap_row(P0[0] + tx, g.n[0]);
+  const int64_t m0 = g.m[0], m1 = g.m[1], m2 = g.m[2];
+  const int64_t cs = m0 * m1 * m2;
+  const int nrows = Sy * Sz;
+  int ly = ty % Sy, lz = ty / Sy;
+  for (int r = ty; r < nrows; r += 4 * RS) {
+    float v[4][NC];
+    int dst[4];
+    bool act[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      act[u] = xact && (r + u * RS) < nrows;
+      const int Py = wrap_row(P0[1] + ly, g.n[1]);
+      const int Pz = wrap_row(P0[2] + lz, g.n[2]);
+      const int64_t row = (int64_t)Pz * m1 + Py;
+      dst[u] = lz * a.PS + ly * Sx + tx;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float x = 0.f;
+        if (act[u]) {
+          x = (float)CoefLoad<Tc>::ld(coef + c * cs + row * m0 + Px);
+          if (IsQuant<Tc>::value) x *= __ldg(a.scale + c * m2 * m1 + row);
+        }
+        v[u][c] = x;
+      }
+      ly += RS;
+      while (ly >= Sy) {
+        ly -= Sy;
+        ++lz;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (act[u])
+        halo[dst[u]] = make_float4(v[u][0], NC > 1 ? v[u][NC > 1 ? 1 : 0] : 0.f,
+                                   NC > 2 ? v[u][NC > 2 ? 2 : 0] : 0.f, 0.f);
+  }
+  __syncthreads();
 }
 
 // 8 lanes per particle: q = x column, kh = parity of the z row; each lane
@@ -357,14 +476,9 @@ __device__ __forceinline__ void oct_rows_global(const GridArgs& g, const Tc* __r
   }
 }
 
-template <typename T>
-__device__ __forceinline__ T sel3(const T v[3], int i) {
-  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
-}
-
 // MODE 0: vel; 1: vel + grad; 2: fused Heun step.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256) interp_staged(StagedArgs a) {
+__global__ void __launch_bounds__(256, 4) interp_staged(StagedArgs a) {
   extern __shared__ float4 halo[];
   constexpr bool GRAD = MODE == 1;
   const int64_t bin = blockIdx.x;
@@ -376,51 +490,31 @@ __global__ void __launch_bounds__(256) interp_staged(StagedArgs a) {
   const int byi = (int)((bin / nbx) % nby);
   const int bzi = (int)(bin / ((int64_t)nbx * nby));
   const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
-  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
   const Tc* coef = static_cast<const Tc*>(a.coef);
-  const int64_t m0 = g.m[0], m1 = g.m[1], m2 = g.m[2];
-  const int64_t cs = m0 * m1 * m2;
+  stage_halo<Tc, NC>(a, coef, P0, halo);
 
-  // stage the brick halo: (u, v, w, 0) per padded point
-  const int tot = Sx * Sy * Sz;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int lx = idx % Sx;
-    const int r = idx / Sx;
-    const int ly = r % Sy, lz = r / Sy;
-    const int Px = wrap_interior(P0[0] + lx, g.n[0]);
-    const int Py = wrap_interior(P0[1] + ly, g.n[1]);
-    const int Pz = wrap_interior(P0[2] + lz, g.n[2]);
-    const int64_t off = ((int64_t)Pz * m1 + Py) * m0 + Px;
-    float vv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float v = (float)CoefLoad<Tc>::ld(coef + c * cs + off);
-      if (IsQuant<Tc>::value) v *= __ldg(a.scale + ((int64_t)c * m2 + Pz) * m1 + Py);
-      vv[c] = v;
-    }
-    halo[lz * a.PS + ly * Sx + lx] = make_float4(vv[0], vv[1], vv[2], vv[3]);
-  }
-  __syncthreads();
-
-  const int lane = threadIdx.x & 31, q = lane & 3, kh = (lane >> 2) & 1, grp = lane >> 3;
+  const int Sx = a.S[0];
+  const int lane = threadIdx.x & 31, q = lane & 3, kh = (lane >> 2) & 1;
   const int sub = lane & 7;
   const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float nanf_ = __int_as_float(0x7fc00000);
-  const double nand = __longlong_as_double(0x7ff8000000000000ll);
+  const int64_t np = a.np;
   for (int s0 = beg + warp * 4; s0 < end; s0 += nw * 4) {
-    const int s = s0 + grp;
+    const int s = s0 + (lane >> 3);
     const bool valid = s < end;
     const int64_t slot = valid ? s : beg;
     const int64_t p = a.perm ? a.perm[slot] : slot;
-    const int64_t np = a.np;
-    const double x[3] = {a.pos_in[p], a.pos_in[np + p], a.pos_in[2 * np + p]};
+    int cell[3];
+    float t[3];
+    double xd;
+    bool ok = locate_group<8, float>(g, a.pos_in, np, p, lane, cell, t, xd);
     Basis<float, GRAD> B;
-    bool ok = B.setup(g, x);
+    B.set(cell, t);
     int l[3];
     bool inh = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      l[d] = local_index(B.a[d], P0[d], g.n[d], a.S[d]);
+      l[d] = local_index(cell[d], P0[d], a.S[d]);
       inh &= l[d] >= 0;
     }
     float acc[NC], accy[NC], accz[NC];
@@ -431,7 +525,7 @@ __global__ void __launch_bounds__(256) interp_staged(StagedArgs a) {
     const float bq = pick4(B.b[0], q);
     float u[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) u[c] = oct_sum(bq * acc[c]);
+    for (int c = 0; c < NC; ++c) u[c] = group_sum<8>(bq * acc[c]);
 
     if constexpr (MODE <= 1) {
       float gx[NC], gy[NC], gz[NC];
@@ -439,9 +533,9 @@ __global__ void __launch_bounds__(256) interp_staged(StagedArgs a) {
         const float dbq = pick4(B.db[0], q);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          gx[c] = oct_sum(dbq * acc[c]) * g.inv_hf[0];
-          gy[c] = oct_sum(bq * accy[c]) * g.inv_hf[1];
-          gz[c] = oct_sum(bq * accz[c]) * g.inv_hf[2];
+          gx[c] = group_sum<8>(dbq * acc[c]) * g.inv_hf[0];
+          gy[c] = group_sum<8>(bq * accy[c]) * g.inv_hf[1];
+          gz[c] = group_sum<8>(bq * accz[c]) * g.inv_hf[2];
         }
       }
       if (valid) {
@@ -459,38 +553,53 @@ __global__ void __launch_bounds__(256) interp_staged(StagedArgs a) {
         }
       }
     } else {
-      // fused Heun step: second stage at x* = x + dt u1
-      double xs[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) xs[d] = x[d] + a.dt * (double)u[d];
-      ok &= B.setup(g, xs);
+      // fused Heun step: predictor located in FP32 from the stage-1 cell
+      int c2[3];
+      float t2[3];
       bool inh2 = a.coef2 == nullptr;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        l[d] = local_index(B.a[d], P0[d], g.n[d], a.S[d]);
+        float tt = t[d] + (ok ? u[d] * a.dtih[d] : 0.f);
+        float fl = floorf(tt);
+        if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
+        const int di = (int)fl;
+        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
+        c2[d] = cell[d] + di;
+        l[d] = local_index(c2[d], P0[d], a.S[d]);
         inh2 &= l[d] >= 0;
       }
-      const Tc* c2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
+      if (!inh2)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          int c = c2[d];
+          if (c < 0 || c >= g.n[d]) {
+            c %= g.n[d];
+            if (c < 0) c += g.n[d];
+          }
+          c2[d] = c;
+        }
+      B.set(c2, t2);
+      const Tc* cf2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
       const float* sc2 = a.coef2 ? a.scale2 : a.scale;
       if (inh2)
         oct_rows_smem<NC, false>(halo, a.PS, Sx, l, B, q, kh, acc, accy, accz);
       else
-        oct_rows_global<Tc, NC, false>(g, c2, sc2, B, q, kh, acc, accy, accz);
+        oct_rows_global<Tc, NC, false>(g, cf2, sc2, B, q, kh, acc, accy, accz);
       const float bq2 = pick4(B.b[0], q);
-      double xn[3];
+      float u2[NC];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float u2 = oct_sum(bq2 * acc[d]);
-        xn[d] = ok ? x[d] + (a.dt * 0.5) * ((double)u[d] + (double)u2) : nand;
-      }
+      for (int c = 0; c < NC; ++c) u2[c] = group_sum<8>(bq2 * acc[c]);
       if (valid) {
         if (!ok && sub == 0) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
-        if (sub < 3) a.pos_out[(int64_t)sub * np + p] = sel3(xn, sub);
-        if (a.vel && sub >= 3 && sub < 6) {
-          const int c = sub - 3;
-          a.vel[(int64_t)c * np + p] = ok ? sel3(u, c) : nanf_;
+        if (sub < 3) {
+          const double w = (double)(sel3(u, sub) + sel3(u2, sub));
+          a.pos_out[(int64_t)sub * np + p] =
+              ok ? fma(a.dt * 0.5, w, xd) : __longlong_as_double(0x7ff8000000000000ll);
+        } else if (sub < 6) {
+          if (a.vel) a.vel[(int64_t)(sub - 3) * np + p] = ok ? sel3(u, sub - 3) : nanf_;
+        } else if (sub == 6 && a.ids_out) {
+          a.ids_out[p] = a.ids_in[p];
         }
-        if (a.ids_out && sub == 6) a.ids_out[p] = a.ids_in[p];
       }
     }
   }
@@ -533,6 +642,7 @@ ps_status fill_staged(const ps_grid* grid, const int32_t brick[3], int E, Staged
   a->g = make_grid_args(grid);
   a->E = E;
   for (int d = 0; d < 3; ++d) a->S[d] = a->b.B[d] + 3 + 2 * E;
+  if (a->S[0] > 32) return fail(PS_ERR_UNSUPPORTED, "brick x extent above 29 cells");
   a->PS = plane_stride(a->S[0], a->S[1]);
   *smem = (size_t)a->S[2] * a->PS * sizeof(float4);
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
@@ -553,6 +663,11 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
   return check_launch("interp_staged");
 }
 
+float3 dt_over_h(const GridArgs& g, double dt) {
+  return make_float3((float)(dt * g.inv_h[0]), (float)(dt * g.inv_h[1]),
+                     (float)(dt * g.inv_h[2]));
+}
+
 }  // namespace
 
 // RK2 kernels used by ps_rk2_step (rk2.cu).
@@ -561,11 +676,12 @@ ps_status rk2_launch_direct(const ps_grid* grid, ps_dtype coef_t, const void* c0
                             double* pos, float* vel_out, double dt, int32_t* status,
                             cudaStream_t st) {
   GridArgs g = make_grid_args(grid);
+  const float3 dtih = dt_over_h(g, dt);
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
     rk2_direct<Tc><<<quad_blocks(np), 256, 0, st>>>(g, static_cast<const Tc*>(c0), s0,
                                                     static_cast<const Tc*>(c1), s1, np, pos,
-                                                    vel_out, dt, status);
+                                                    vel_out, dt, dtih, status);
     return check_launch("rk2_direct");
   });
 }
@@ -594,6 +710,10 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
   a.ids_in = ids_in;
   a.ids_out = ids_out;
   a.dt = dt;
+  const float3 d = dt_over_h(a.g, dt);
+  a.dtih[0] = d.x;
+  a.dtih[1] = d.y;
+  a.dtih[2] = d.z;
   a.status = status;
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);

@@ -95,21 +95,61 @@ __device__ __forceinline__ void flag_status(int32_t* st, int code, int64_t idx) 
   atomicAdd(&st[3], 1);
 }
 
-// Operation 2, index part (Sec. 2.2): s = x * (n/L) as one rounded FP64
-// multiply, a = floor(s), t = s - a, cell = a mod n in [0, n).
-// Returns false for a non-finite position or |s| >= 1e15.
-__device__ __forceinline__ bool locate(double x, double inv_h, int n, int& cell,
-                                       double& t) {
-  double s = __dmul_rn(x, inv_h);
-  if (!(fabs(s) < 1.0e15)) {
-    cell = 0;
-    t = 0.0;
-    return false;
+// Operation 2, index part (Sec. 2.2).  s = x * (n/L) is one rounded FP64
+// multiply; a = floor(s) and the fraction t = s - a are then read exactly
+// from the bits of s with integer arithmetic (FP64 issue slots are scarce on
+// this GPU), and cell = a mod n.  t is returned rounded toward zero to 24
+// bits (within one FP32 ulp of s - a); the cell index is exact.
+// Returns false for a non-finite position or |s| >= 2^50.
+__device__ __forceinline__ bool locate(double x, double inv_h, int n, int& cell, float& t) {
+  const double s = __dmul_rn(x, inv_h);
+  const long long bits = __double_as_longlong(s);
+  const int bexp = (int)((bits >> 52) & 0x7ff);
+  cell = 0;
+  t = 0.f;
+  if (bexp >= 1023 + 50) return false;  // |s| >= 2^50, Inf or NaN
+  const bool neg = bits < 0;
+  const unsigned long long M = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  long long a;
+  unsigned int hi;  // top 24 fraction bits of |s|
+  bool frac_zero;
+  if (bexp < 1023) {  // |s| < 1
+    if (bexp == 0 && M == 0) return true;  // +-0
+    const unsigned long long MM = bexp == 0 ? M : (M | (1ull << 52));
+    const int sh = 1075 - (bexp == 0 ? 1 : bexp);  // > 52 fraction bits
+    hi = sh - 24 >= 64 ? 0u : (unsigned int)(MM >> (sh - 24));
+    frac_zero = false;
+    a = neg ? -1 : 0;
+  } else {
+    const int sh = 1075 - bexp;  // 3..52 fraction bits
+    const unsigned long long MM = M | (1ull << 52);
+    const unsigned long long ip = MM >> sh;
+    const unsigned long long fr = MM & ((1ull << sh) - 1);
+    hi = sh > 24 ? (unsigned int)(fr >> (sh - 24)) : (unsigned int)(fr << (24 - sh));
+    frac_zero = fr == 0;
+    a = neg ? (frac_zero ? -(long long)ip : -(long long)ip - 1) : (long long)ip;
   }
-  double a = floor(s);
+  const float two_m24 = __int_as_float(0x33800000);  // 2^-24
+  t = neg ? (frac_zero ? 0.f : (float)((1u << 24) - hi) * two_m24) : (float)hi * two_m24;
+  long long m = a;
+  if (m < 0 || m >= n) {
+    m %= n;
+    if (m < 0) m += n;
+  }
+  cell = (int)m;
+  return true;
+}
+
+// FP64 variant for FP64 coefficients: t = s - floor(s) in FP64.
+__device__ __forceinline__ bool locate_f64(double x, double inv_h, int n, int& cell,
+                                           double& t) {
+  const double s = __dmul_rn(x, inv_h);
+  cell = 0;
+  t = 0.0;
+  if (!(fabs(s) < 1125899906842624.0)) return false;  // 2^50
+  const double a = floor(s);
   t = __dsub_rn(s, a);
-  long long ai = (long long)a;
-  long long m = ai % n;
+  long long m = ((long long)a) % n;
   if (m < 0) m += n;
   cell = (int)m;
   return true;

@@ -149,6 +149,13 @@ __device__ __forceinline__ float pow2_at_least(float mx) {
   return f == 0.5f ? ldexpf(1.f, e - 1) : ldexpf(1.f, e);
 }
 
+// e + floor(e / L) for e < 32 (L + 1): (e + 1/2) / L is at least 1/(2L) away
+// from an integer, far more than the FP32 rounding of the product, so the
+// truncation is exact (checked exhaustively for L <= 128).
+__device__ __forceinline__ int skew(int e, float inv_L) {
+  return e + (int)(((float)e + 0.5f) * inv_L);
+}
+
 // x pass: one warp per x-line.  The line is staged in shared memory with a
 // skew (element e at e + e/L) so that lane l reads its chunk [l L, l L + L)
 // without bank conflicts; chunk carries move between lanes by shuffles.
@@ -173,8 +180,9 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
   const unsigned FULL = 0xffffffffu;
   const T thr = Thr<T>::v;
 
+  const float inv_L = 1.f / (float)L;
   const T* sp = src + sv.off + c * sv.sc + zz * sv.sz + yy * sv.sy;
-  for (int e = lane; e < nx; e += 32) buf[e + e / L] = sp[e];
+  for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
   __syncwarp();
   const int s0 = lane * L;
   int len = nx - s0;
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
 
   if (!padded) {
     Tout* orow = dst + dv.off + c * dv.sc + zz * dv.sz + yy * dv.sy;
-    for (int e = lane; e < nx; e += 32) orow[e] = (Tout)buf[e + e / L];
+    for (int e = lane; e < nx; e += 32) orow[e] = (Tout)buf[skew(e, inv_L)];
     return;
   }
   int pys[2], pzs[2];
@@ -281,11 +289,11 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
       const int Pz = pzs[iz], Py = pys[iy];
       Tout* orow = dst + dv.off + c * dv.sc + Pz * dv.sz + Py * dv.sy;
       for (int P = lane; P < nx + 3; P += 32) {
-        const int e = padded_to_node(P, nx);
+        const int e = skew(padded_to_node(P, nx), inv_L);
         if constexpr (sizeof(T) == 8)
-          orow[P] = cvt_out_d<Tout>((double)buf[e + e / L]);
+          orow[P] = cvt_out_d<Tout>((double)buf[e]);
         else
-          orow[P] = cvt_out<Tout>((float)buf[e + e / L]);
+          orow[P] = cvt_out<Tout>((float)buf[e]);
       }
       if (QUANT && lane == 0) scale[((int64_t)c * (nz + 3) + Pz) * (ny + 3) + Py] = sc;
     }

@@ -97,6 +97,30 @@ def test_binning_bit_exact(n, brick):
     np.testing.assert_array_equal(sorted_pos.cpu().numpy(), pos[:, perm])
 
 
+def test_binning_adversarial_positions():
+    # exact nodes, signed zeros, fractions that round to 1, far shadow images,
+    # values just below/above faces: the integer floor must match FP64 floor.
+    n, brick = (64, 48, 40), (8, 8, 8)
+    L = (TWO_PI, 3.0, 1.0)
+    rng = np.random.default_rng(3)
+    cols = []
+    for d in range(3):
+        h = L[d] / n[d]
+        nodes = np.arange(-3 * n[d], 4 * n[d]) * h
+        v = np.concatenate([nodes, nodes + 1e-17, nodes - 1e-17, np.nextafter(nodes, np.inf),
+                            np.nextafter(nodes, -np.inf), [0.0, -0.0, -1e-300, 1e-300, -5e-324],
+                            rng.uniform(-1e6, 1e6, 2000), rng.uniform(-1e-9, 1e-9, 500)])
+        cols.append(v)
+    m = max(len(c) for c in cols)
+    pos = np.stack([np.resize(c, m) for c in cols])
+    for d in range(3):
+        rng.shuffle(pos[d])
+    b_ora, off_ora, _ = oracle.bin_particles(n, brick, pos, L=L)
+    bins = ps.bin_particles(n, brick, torch.from_numpy(pos).to(DEV), L=L)
+    np.testing.assert_array_equal(bins.bin_of.cpu().numpy(), b_ora)
+    np.testing.assert_array_equal(bins.offsets.cpu().numpy(), off_ora)
+
+
 def test_binning_empty_and_single():
     n, brick = (16, 16, 16), (8, 8, 8)
     pg = torch.empty((3, 0), dtype=torch.float64, device=DEV)
