@@ -173,7 +173,8 @@ def run_ours(args):
     pos_host = synth.uniform_particles(NP, seed=POS_SEED)
     pos0 = torch.from_numpy(pos_host).to(dev)
     n3 = (N, N, N)
-    coef = torch.empty((3, N + 3, N + 3, N + 3), dtype=torch.float32, device=dev)
+    coef = torch.empty(ps.coef_shape((N, N, N), 3, torch.float32), dtype=torch.float32,
+                       device=dev)
     nb = [-(-N // b) for b in BRICK]
     nbins = nb[0] * nb[1] * nb[2]
     offsets = torch.empty(nbins + 1, dtype=torch.int32, device=dev)
@@ -195,7 +196,7 @@ def run_ours(args):
             ps.ps_bin_particles(n3, BRICK, src, bin_of, offsets, None, dst, ws_bin, status)
             if ev_rk:
                 ev_rk[r][0].record(stream)
-            ps.ps_rk2_step(coef, dst, DT, vel_out=vel, brick=BRICK, rebin=False,
+            ps.ps_rk2_step(coef, n3, dst, DT, vel_out=vel, brick=BRICK, rebin=False,
                            bin_offsets=offsets, status=status)
             if ev_rk:
                 ev_rk[r][1].record(stream)
@@ -290,15 +291,13 @@ def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
     perm = torch.randperm(NP, generator=g).to(dev)
     pos_rand = pos_sorted_by_bin[:, perm].contiguous()
     vel = torch.empty((3, NP), dtype=torch.float32, device=dev)
-    bins = ps.bin_particles(n3, BRICK, pos_sorted_by_bin, want_perm=False)
-    sorted_bins = ps.Bins(BRICK, bins.offsets, bins.bin_of, None)
     # physically sorted copy
     bins2, pos_sorted = ps.bin_particles(n3, BRICK, pos_sorted_by_bin, want_sorted=True)
     out = {}
     for name, fn in (
-            ("unsorted_direct", lambda: ps.ps_interp(coef, pos_rand, vel)),
-            ("sorted_direct", lambda: ps.ps_interp(coef, pos_sorted, vel)),
-            ("sorted_staged", lambda: ps.ps_interp(coef, pos_sorted, vel,
+            ("unsorted_direct", lambda: ps.ps_interp(coef, n3, pos_rand, vel)),
+            ("sorted_direct", lambda: ps.ps_interp(coef, n3, pos_sorted, vel)),
+            ("sorted_staged", lambda: ps.ps_interp(coef, n3, pos_sorted, vel,
                                                    bin_offsets=bins2.offsets, brick=BRICK))):
         for _ in range(3):
             fn()
@@ -310,7 +309,6 @@ def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 5
         out[name] = {"ms": t, "particles_per_s": NP / (t * 1e-3)}
-    del sorted_bins
     return out
 
 
@@ -336,7 +334,7 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg):
         pos_d.copy_(pos_h, non_blocking=True)
         ps.ps_spline_coeffs(field_d, coef)
         for _ in range(RK_STEPS):
-            ps.ps_rk2_step(coef, pos_d, DT, ids=ids, vel_out=vel_d, brick=BRICK, rebin=True,
+            ps.ps_rk2_step(coef, n3, pos_d, DT, ids=ids, vel_out=vel_d, brick=BRICK, rebin=True,
                            bin_offsets=offsets, ws=ws, status=status)
         pos_out_h.copy_(pos_d, non_blocking=True)
         vel_h.copy_(vel_d, non_blocking=True)

@@ -33,11 +33,13 @@
  *              [0,L[0]) x [0,L[1]) x [0,L[2]); node spacing h_d = L_d / n_d.
  *              3 <= n_d <= 2048.
  *   field      [ncomp][nz][ny][nx]                     (F32 or F64)
- *   coef       [ncomp][nz+3][ny+3][nx+3]               (F32, F64, BF16, F16)
+ *   coef       [ncomp][nz+3][ny+3][rx]                 (F32, F64, BF16, F16)
  *              padded index P in [0, n+2] holds node (P-1) mod n: one periodic
  *              ghost below and two above, the N+3 coefficients per line of
- *              Sec. 2.2.  Storage offset of (c, Pz, Py, Px) is
- *              ((c*(nz+3) + Pz)*(ny+3) + Py)*(nx+3) + Px.
+ *              Sec. 2.2.  Rows are padded to rx = ps_coef_row_pitch(nx, dtype)
+ *              elements (nx+3 rounded up to 16 bytes; the tail is written as
+ *              zero) so that every row starts on a 16-byte boundary.  Storage
+ *              offset of (c, Pz, Py, Px) is ((c*(nz+3) + Pz)*(ny+3) + Py)*rx + Px.
  *   scale      [ncomp][nz+3][ny+3] F32, only for BF16/F16 coefficients: the
  *              value of a coefficient is stored * scale of its x-line; scales
  *              are powers of two, so scaling itself is exact.
@@ -70,7 +72,7 @@ typedef enum { PS_F32 = 0, PS_BF16 = 1, PS_F16 = 2, PS_F64 = 3 } ps_dtype;
 
 /* device status codes (status[0]) */
 #define PS_DEV_OK 0
-#define PS_DEV_NONFINITE_POS 1 /* position NaN/Inf or |x * n/L| >= 1e15 */
+#define PS_DEV_NONFINITE_POS 1 /* position NaN/Inf or |x * n/L| >= 2^50 */
 #define PS_DEV_TIMEOUT 2
 
 typedef struct {
@@ -82,6 +84,10 @@ typedef struct {
 const char* ps_last_error(void);
 /* Library version string. */
 const char* ps_version(void);
+/* Row pitch rx (elements) of a padded coefficient array for nx nodes along x:
+ * nx+3 rounded up to a multiple of 16 bytes.  0 for a bad argument.  Part of
+ * the storage layout, not of the method (the paper stores N+3 per line). */
+int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
 
 /* Zero a device status word (4 x int32) on `stream`. */
 ps_status ps_status_clear(int32_t* status, void* stream);

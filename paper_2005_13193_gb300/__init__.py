@@ -86,9 +86,21 @@ def _brick_arr(brick):
     return (ctypes.c_int32 * 3)(*[int(b) for b in brick])
 
 
-def grid_of_coef(coef: torch.Tensor):
-    """(nx, ny, nz) of a padded coefficient array [ncomp][nz+3][ny+3][nx+3]."""
-    return (coef.shape[3] - 3, coef.shape[2] - 3, coef.shape[1] - 3)
+def coef_row_pitch(nx: int, dtype: torch.dtype) -> int:
+    """Row pitch (elements) of a padded coefficient array: nx+3 rounded up to
+    16 bytes (ps_coef_row_pitch)."""
+    return int(_lib().ps_coef_row_pitch(int(nx), _DT[dtype]))
+
+
+def coef_shape(n, ncomp: int, dtype: torch.dtype):
+    """Storage shape [ncomp][nz+3][ny+3][pitch] of padded coefficients."""
+    return (ncomp, n[2] + 3, n[1] + 3, coef_row_pitch(n[0], dtype))
+
+
+def _check_coef_shape(coef: torch.Tensor, n):
+    want = coef_shape(n, coef.shape[0], coef.dtype)
+    if tuple(coef.shape) != want:
+        raise ValueError(f"coef has shape {tuple(coef.shape)}, grid {tuple(n)} needs {want}")
 
 
 def grid_of_field(field: torch.Tensor):
@@ -132,7 +144,8 @@ def ps_spline_coeffs(field: torch.Tensor, coef: torch.Tensor, scale: Optional[to
     n = grid_of_field(field)
     ncomp = field.shape[0]
     _dev(field, "field")
-    _dev(coef, "coef", numel=ncomp * (n[0] + 3) * (n[1] + 3) * (n[2] + 3))
+    _check_coef_shape(coef, n)
+    _dev(coef, "coef")
     _dev(scale, "scale", torch.float32)
     _dev(ws, "ws")
     g = make_grid(n, L)
@@ -167,13 +180,14 @@ def ps_bin_particles(n, brick, pos: torch.Tensor, bin_of: torch.Tensor, bin_offs
                                    _ptr(ws), ws_bytes, _ptr(status), _stream(stream)))
 
 
-def ps_interp(coef: torch.Tensor, pos: torch.Tensor, vel: torch.Tensor,
+def ps_interp(coef: torch.Tensor, n, pos: torch.Tensor, vel: torch.Tensor,
               scale: Optional[torch.Tensor] = None, perm: Optional[torch.Tensor] = None,
               bin_offsets: Optional[torch.Tensor] = None, brick=None,
               grad: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
               L=DEFAULT_L, stream=None):
-    """Operations 2-3 (Sec. 2.2, Eq. (spline)) at positions pos [3][np] -> vel [ncomp][np]."""
-    n = grid_of_coef(coef)
+    """Operations 2-3 (Sec. 2.2, Eq. (spline)) at positions pos [3][np] -> vel [ncomp][np].
+    n = (nx, ny, nz) of the grid the coefficients belong to."""
+    _check_coef_shape(coef, n)
     ncomp = coef.shape[0]
     np_ = pos.shape[1]
     _dev(coef, "coef")
@@ -190,12 +204,12 @@ def ps_interp(coef: torch.Tensor, pos: torch.Tensor, vel: torch.Tensor,
                             _ptr(vel), _ptr(grad), _ptr(status), _stream(stream)))
 
 
-def ps_interp_backward(coef: torch.Tensor, pos: torch.Tensor, g_vel: torch.Tensor,
+def ps_interp_backward(coef: torch.Tensor, n, pos: torch.Tensor, g_vel: torch.Tensor,
                        g_pos: Optional[torch.Tensor] = None, g_field: Optional[torch.Tensor] = None,
                        scale: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
                        L=DEFAULT_L, stream=None):
     """Adjoint of ps_interp and of the coefficient solve."""
-    n = grid_of_coef(coef)
+    _check_coef_shape(coef, n)
     ncomp = coef.shape[0]
     np_ = pos.shape[1]
     _dev(coef, "coef")
@@ -215,14 +229,14 @@ def ps_rk2_workspace_size(n, brick, np_: int, L=DEFAULT_L) -> int:
     return int(_lib().ps_rk2_workspace_size(ctypes.byref(g), _brick_arr(brick), int(np_)))
 
 
-def ps_rk2_step(coef_n: torch.Tensor, pos: torch.Tensor, dt: float,
+def ps_rk2_step(coef_n: torch.Tensor, n, pos: torch.Tensor, dt: float,
                 coef_np1: Optional[torch.Tensor] = None, scale_n: Optional[torch.Tensor] = None,
                 scale_np1: Optional[torch.Tensor] = None, ids: Optional[torch.Tensor] = None,
                 vel_out: Optional[torch.Tensor] = None, brick=None, rebin: bool = True,
                 bin_offsets: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
                 status: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
     """One Heun RK2 step (Sec. 2.1 / 4.3) of positions pos [3][np] in place."""
-    n = grid_of_coef(coef_n)
+    _check_coef_shape(coef_n, n)
     np_ = pos.shape[1]
     _dev(coef_n, "coef_n")
     _dev(coef_np1, "coef_np1", coef_n.dtype)
@@ -253,12 +267,17 @@ def workspace(nbytes: int, device="cuda") -> torch.Tensor:
 class SplineField:
     """Padded spline coefficients of a periodic field (Sec. 2.2 Operation 1)."""
 
-    def __init__(self, coef: torch.Tensor, scale: Optional[torch.Tensor], L=DEFAULT_L):
+    def __init__(self, coef: torch.Tensor, scale: Optional[torch.Tensor], n, L=DEFAULT_L):
         self.coef = coef
         self.scale = scale
         self.L = tuple(float(v) for v in L)
-        self.n = grid_of_coef(coef)
+        self.n = tuple(int(v) for v in n)
         self.ncomp = coef.shape[0]
+        _check_coef_shape(coef, self.n)
+
+    def padded(self) -> torch.Tensor:
+        """[ncomp][nz+3][ny+3][nx+3] view (the row pitch tail dropped)."""
+        return self.coef[..., : self.n[0] + 3]
 
     @classmethod
     def from_field(cls, field: torch.Tensor, coef_dtype=torch.float32, L=DEFAULT_L,
@@ -267,13 +286,13 @@ class SplineField:
         n = grid_of_field(field)
         ncomp = field.shape[0]
         if out is None:
-            coef = torch.empty((ncomp, n[2] + 3, n[1] + 3, n[0] + 3), dtype=coef_dtype,
+            coef = torch.empty(coef_shape(n, ncomp, coef_dtype), dtype=coef_dtype,
                                device=field.device)
             scale = None
             if coef_dtype in (torch.bfloat16, torch.float16):
                 scale = torch.empty((ncomp, n[2] + 3, n[1] + 3), dtype=torch.float32,
                                     device=field.device)
-            out = cls(coef, scale, L)
+            out = cls(coef, scale, n, L)
         need = ps_spline_coeffs_workspace_size(n, ncomp, out.coef.dtype, L)
         if need and (ws is None or ws.numel() < need):
             ws = workspace(need, field.device)
@@ -286,7 +305,7 @@ class SplineField:
         vel = torch.empty((self.ncomp, np_), dtype=torch.float32, device=pos.device)
         g = (torch.empty((self.ncomp, 3, np_), dtype=torch.float32, device=pos.device)
              if grad else None)
-        ps_interp(self.coef, pos, vel, scale=self.scale,
+        ps_interp(self.coef, self.n, pos, vel, scale=self.scale,
                   perm=bins.perm if bins is not None else None,
                   bin_offsets=bins.offsets if bins is not None else None,
                   brick=bins.brick if bins is not None else None, grad=g, status=status,
@@ -348,7 +367,7 @@ class Tracker:
     def step(self, dt: float, field_np1: Optional[SplineField] = None, rebin: bool = True,
              stream=None):
         f1 = field_np1
-        ps_rk2_step(self.field.coef, self.pos, dt,
+        ps_rk2_step(self.field.coef, self.field.n, self.pos, dt,
                     coef_np1=f1.coef if f1 is not None else None, scale_n=self.field.scale,
                     scale_np1=f1.scale if f1 is not None else None, ids=self.ids,
                     vel_out=self.vel, brick=self.brick, rebin=rebin, bin_offsets=self.offsets,
@@ -380,8 +399,8 @@ class InterpFn(torch.autograd.Function):
         g_field = (torch.empty((sf.ncomp, sf.n[2], sf.n[1], sf.n[0]), dtype=torch.float32,
                                device=pos.device) if want_field else None)
         if want_pos or want_field:
-            ps_interp_backward(sf.coef, pos.detach(), g_vel, g_pos, g_field, scale=sf.scale,
-                               L=sf.L)
+            ps_interp_backward(sf.coef, sf.n, pos.detach(), g_vel, g_pos, g_field,
+                               scale=sf.scale, L=sf.L)
         if g_field is not None:
             g_field = g_field.to(ctx.field_dtype)
         return g_pos, g_field, None

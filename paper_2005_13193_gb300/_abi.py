@@ -38,6 +38,7 @@ _GP = ctypes.POINTER(PsGrid)
 SIGNATURES = {
     "ps_last_error": (ctypes.c_char_p, []),
     "ps_version": (ctypes.c_char_p, []),
+    "ps_coef_row_pitch": (_I64, [_I, _I]),
     "ps_status_clear": (_I, [_P, _P]),
     "ps_status_read": (_I, [_P, _P, _P]),
     "ps_spline_coeffs_workspace_size": (_SZ, [_GP, _I, _I]),

@@ -55,7 +55,12 @@ size_t dtype_size(ps_dtype t) {
   return 0;
 }
 
-GridArgs make_grid_args(const ps_grid* g) {
+int64_t coef_pitch(int nx, ps_dtype t) {
+  const int64_t v = 16 / (int64_t)dtype_size(t);
+  return ((int64_t)nx + 3 + v - 1) / v * v;
+}
+
+GridArgs make_grid_args(const ps_grid* g, int coef_t) {
   GridArgs a;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g->n[d];
@@ -63,6 +68,7 @@ GridArgs make_grid_args(const ps_grid* g) {
     a.inv_h[d] = (double)g->n[d] / g->L[d];
     a.inv_hf[d] = (float)a.inv_h[d];
   }
+  a.rx = coef_t < 0 ? 0 : (int)coef_pitch(g->n[0], (ps_dtype)coef_t);
   return a;
 }
 
@@ -88,6 +94,11 @@ using namespace ps;
 extern "C" const char* ps_last_error(void) { return g_err; }
 
 extern "C" const char* ps_version(void) { return "ps 0.1 (sm_103a)"; }
+
+extern "C" int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t) {
+  if (nx < 1 || dtype_size(coef_t) == 0) return 0;
+  return coef_pitch(nx, coef_t);
+}
 
 extern "C" ps_status ps_status_clear(int32_t* status, void* stream) {
   if (!status) return fail(PS_ERR_INVALID_ARG, "status is NULL");

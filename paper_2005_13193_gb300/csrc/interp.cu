@@ -48,9 +48,9 @@ __device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
                                                               const float* scale,
                                                               const GridArgs& g, int c,
                                                               int Pz, int Py, int Px) {
-  const int64_t m0 = g.m[0], m1 = g.m[1], m2 = g.m[2];
+  const int64_t m1 = g.m[1], m2 = g.m[2];
   const int64_t row = ((int64_t)c * m2 + Pz) * m1 + Py;
-  typename AccOf<Tc>::type v = CoefLoad<Tc>::ld(coef + row * m0 + Px);
+  typename AccOf<Tc>::type v = CoefLoad<Tc>::ld(coef + row * g.rx + Px);
   if (IsQuant<Tc>::value) v *= __ldg(scale + row);
   return v;
 }
@@ -325,6 +325,7 @@ struct StagedArgs {
   int E;        // extra halo cells on each side
   int S[3];     // staged extent per axis: B + 3 + 2E
   int PS;       // plane stride in float4 units: >= S[0]*S[1], = 4 (mod 8)
+  int vec;      // 1: halo rows are whole 16-byte vectors inside the array
   const void* coef;
   const float* scale;
   const void* coef2;  // second-stage field of an RK2 step; NULL = same as coef
@@ -342,15 +343,6 @@ struct StagedArgs {
   float dtih[3];  // dt * n/L per axis
   int32_t* status;
 };
-
-// Stencil-local index of a cell inside the staged box starting at padded
-// index P0, or -1 if the 4-wide stencil does not fit.  Particles of the brick
-// itself always fit; anything else (a stale bin, a predictor that left the
-// brick) is served from global memory instead.
-__device__ __forceinline__ int local_index(int a, int P0, int S) {
-  const int la = a - P0;
-  return (unsigned)la <= (unsigned)(S - 4) ? la : -1;
-}
 
 // Padded index (any integer) -> interior padded index of the same node.
 __device__ __forceinline__ int wrap_row(int P, int n) {
@@ -374,7 +366,7 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
   const int RS = narrow ? 16 : 8;  // rows covered by the block per step
   const bool xact = tx < Sx;
   const int Px = wrap_row(P0[0] + tx, g.n[0]);
-  const int64_t m0 = g.m[0], m1 = g.m[1], m2 = g.m[2];
+  const int64_t m0 = g.rx, m1 = g.m[1], m2 = g.m[2];
   const int64_t cs = m0 * m1 * m2;
   const int nrows = Sy * Sz;
   int ly = ty % Sy, lz = ty / Sy;
@@ -413,195 +405,350 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
   __syncthreads();
 }
 
-// 8 lanes per particle: q = x column, kh = parity of the z row; each lane
-// covers rows (j = 0..3) x (k = kh, kh+2).  Accumulators per lane.
-template <int NC, bool GRAD>
-__device__ __forceinline__ void oct_rows_smem(const float4* __restrict__ halo, int PS,
-                                              int Sx, const int l[3],
-                                              const Basis<float, GRAD>& B, int q, int kh,
-                                              float acc[NC], float accy[NC],
-                                              float accz[NC]) {
+// Vector staging.  With E = 0 and bricks that tile the grid, the halo of
+// brick b spans padded indices [b B, b B + B + 2] on every axis, inside the
+// padded array; when B is a multiple of the vector width V (16 bytes) every
+// halo row starts on a 16-byte boundary (the row pitch is a multiple of 16
+// bytes), so each row is read with ceil(S_x / V) 16-byte loads per component
+// and transposed in registers into the float4-per-point layout.
+template <typename Tc> struct Vec16;
+template <> struct Vec16<float> {
+  static constexpr int V = 4;
+  static __device__ __forceinline__ void load(const float* p, float s, float out[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = v.x * s; out[1] = v.y * s; out[2] = v.z * s; out[3] = v.w * s;
+  }
+};
+template <typename H> struct Vec16Half {
+  static constexpr int V = 8;
+  static __device__ __forceinline__ void load(const H* p, float s, float out[8]) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const unsigned short lo = (unsigned short)(w[i] & 0xffffu), hi = (unsigned short)(w[i] >> 16);
+      out[2 * i] = CoefLoadBits<H>::f(lo) * s;
+      out[2 * i + 1] = CoefLoadBits<H>::f(hi) * s;
+    }
+  }
+};
+template <> struct Vec16<__nv_bfloat16> : Vec16Half<__nv_bfloat16> {};
+template <> struct Vec16<__half> : Vec16Half<__half> {};
+
+template <typename Tc, int NC>
+__device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __restrict__ coef,
+                                               const int P0[3], float4* halo) {
+  constexpr int V = Vec16<Tc>::V;
+  constexpr int U = 8 / V;               // rows in flight per thread
+  const GridArgs& g = a.g;
+  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
+  const int qx = (Sx + V - 1) / V;       // vectors per halo row (<= 4)
+  const int qd = threadIdx.x & 3, rs = threadIdx.x >> 2;
+  const int RS = blockDim.x >> 2;        // rows per block step
+  const int64_t rx = g.rx, m1 = g.m[1], m2 = g.m[2];
+  const int64_t cs = rx * m1 * m2;
+  const int nrows = Sy * Sz;
+  const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0] + qd * V;
+  for (int r0 = rs; r0 < nrows; r0 += U * RS) {
+    float v[U][NC][V];
+    int h0[U];
+    bool act[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u * RS;
+      act[u] = qd < qx && r < nrows;
+      const int lz = r / Sy, ly = r - lz * Sy;
+      h0[u] = lz * a.PS + ly * Sx + qd * V;
+      const int64_t roff = ((int64_t)lz * m1 + ly) * rx;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (act[u]) {
+          float s = 1.f;
+          if (IsQuant<Tc>::value)
+            s = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
+          Vec16<Tc>::load(base + c * cs + roff, s, v[u][c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (act[u])
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          if (qd * V + i < Sx)
+            halo[h0[u] + i] = make_float4(v[u][0][i], NC > 1 ? v[u][NC > 1 ? 1 : 0][i] : 0.f,
+                                          NC > 2 ? v[u][NC > 2 ? 2 : 0][i] : 0.f, 0.f);
+  }
+  __syncthreads();
+}
+
+// Particle records in shared memory (one per particle of the current round):
+//   rec[0] = (t_x, t_y, t_z, origin)  fractions and the halo index of the
+//            stencil origin (float bits of an int; -1 = not in the halo)
+//   rec[1] = (cell_x, cell_y, cell_z, ok) global cells for the fallback path
+//   rec[2] = (u, v, w, -)               result of the last gather
+constexpr int kRecords = 256;  // particles per round (= threads per CTA)
+constexpr int kRecW = 3;       // float4 per record
+
+// Cubic coefficients (t^3, t^2, t, 1) of basis function i, and of its
+// derivative (t^2, t, 1) when asked; i is a lane constant.
+__device__ __forceinline__ float4 basis_coeffs(int i) {
+  const float s = 1.f / 6.f;
+  return i == 0 ? make_float4(-s, 0.5f, -0.5f, s)
+       : i == 1 ? make_float4(0.5f, -1.f, 0.f, 4.f * s)
+       : i == 2 ? make_float4(-0.5f, 0.5f, 0.5f, s)
+                : make_float4(s, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float horner3(float4 c, float t) {
+  return fmaf(fmaf(fmaf(c.x, t, c.y), t, c.z), t, c.w);
+}
+__device__ __forceinline__ float dhorner3(float4 c, float t) {
+  return fmaf(fmaf(3.f * c.x, t, 2.f * c.y), t, c.z);
+}
+
+// Phase A: one thread per particle.  Locates the particle (exact FP64 index
+// arithmetic), writes its record.  Returns ok.
+__device__ __forceinline__ bool write_record(float4* rec, const int cell[3], const float t[3],
+                                             bool ok, const int P0[3], const int S[3], int PS,
+                                             int Sx) {
+  int l[3];
+  bool inh = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    l[d] = cell[d] - P0[d];
+    inh &= (unsigned)l[d] <= (unsigned)(S[d] - 4);
+  }
+  const int origin = inh ? l[2] * PS + l[1] * Sx + l[0] : -1;
+  rec[0] = make_float4(t[0], t[1], t[2], __int_as_float(origin));
+  rec[1] = make_float4(__int_as_float(cell[0]), __int_as_float(cell[1]),
+                       __int_as_float(cell[2]), __int_as_float(ok ? 1 : 0));
+  return ok;
+}
+
+// Phase B: 8 lanes per particle.  Lane (q, kh) covers stencil column
+// x = a_x + q and the z rows k = kh, kh + 2, all four y rows; the partial
+// sums meet in a 3-level butterfly.  Shared-memory reads of one particle
+// (one 8-lane phase of a 128-bit load) are conflict-free because rows k and
+// k+2 are PS = 4 (mod 8) float4 apart.
+template <typename Tc, int NC, bool GRAD>
+__device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS, int Sx,
+                                        const float4* rec, const GridArgs& g,
+                                        const Tc* __restrict__ coef,
+                                        const float* __restrict__ scale, int q, int kh,
+                                        float4 cq, float4 ck0, float4 ck1, float out[NC],
+                                        float dx[NC], float dy[NC], float dz[NC]) {
+  const float4 r0 = rec[0];
+  const float bxq = horner3(cq, r0.x);
+  float by[4], dby[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float4 cj = basis_coeffs(j);
+    by[j] = horner3(cj, r0.y);
+    if (GRAD) dby[j] = dhorner3(cj, r0.y);
+  }
+  const float bz0 = horner3(ck0, r0.z), bz1 = horner3(ck1, r0.z);
+  float dbz0 = 0.f, dbz1 = 0.f;
+  if (GRAD) {
+    dbz0 = dhorner3(ck0, r0.z);
+    dbz1 = dhorner3(ck1, r0.z);
+  }
+  float acc[NC], accy[NC], accz[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
-  const float4* hp = halo + (l[2] + kh) * PS + l[1] * Sx + l[0] + q;
+  const int origin = __float_as_int(r0.w);
+  if (origin >= 0) {
+    const float4* hp = halo + origin + kh * PS + q;
 #pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-    const float bzk = kh ? B.b[2][1 + 2 * kk] : B.b[2][2 * kk];
-    const float dbzk = GRAD ? (kh ? B.db[2][1 + 2 * kk] : B.db[2][2 * kk]) : 0.f;
+    for (int kk = 0; kk < 2; ++kk) {
+      const float bz = kk ? bz1 : bz0;
+      const float dbz = kk ? dbz1 : dbz0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 v = hp[2 * kk * PS + j * Sx];
-      const float vv[4] = {v.x, v.y, v.z, v.w};
-      const float w = B.b[1][j] * bzk;
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = hp[2 * kk * PS + j * Sx];
+        const float vv[3] = {v.x, v.y, v.z};
+        const float w = by[j] * bz;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += w * vv[c];
-      if (GRAD) {
-        const float wy = B.db[1][j] * bzk, wz = B.b[1][j] * dbzk;
+        for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
+        if (GRAD) {
+          const float wy = dby[j] * bz, wz = by[j] * dbz;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            accy[c] = fmaf(wy, vv[c], accy[c]);
+            accz[c] = fmaf(wz, vv[c], accz[c]);
+          }
+        }
+      }
+    }
+  } else {
+    const float4 r1 = rec[1];
+    const int ax = __float_as_int(r1.x), ay = __float_as_int(r1.y), az = __float_as_int(r1.z);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const float bz = kk ? bz1 : bz0;
+      const float dbz = kk ? dbz1 : dbz0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w = by[j] * bz;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          accy[c] += wy * vv[c];
-          accz[c] += wz * vv[c];
+          const float v = load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j, ax + q);
+          acc[c] = fmaf(w, v, acc[c]);
+          if (GRAD) {
+            accy[c] = fmaf(dby[j] * bz, v, accy[c]);
+            accz[c] = fmaf(by[j] * dbz, v, accz[c]);
+          }
         }
       }
     }
   }
-}
-
-template <typename Tc, int NC, bool GRAD>
-__device__ __forceinline__ void oct_rows_global(const GridArgs& g, const Tc* __restrict__ coef,
-                                                const float* __restrict__ scale,
-                                                const Basis<float, GRAD>& B, int q, int kh,
-                                                float acc[NC], float accy[NC],
-                                                float accz[NC]) {
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
+  for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
+  if (GRAD) {
+    const float dbxq = dhorner3(cq, r0.x);
 #pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-    const int k = kh + 2 * kk;
-    const float bzk = kh ? B.b[2][1 + 2 * kk] : B.b[2][2 * kk];
-    const float dbzk = GRAD ? (kh ? B.db[2][1 + 2 * kk] : B.db[2][2 * kk]) : 0.f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float w = B.b[1][j] * bzk;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float v = load_coef<Tc>(coef, scale, g, c, B.a[2] + k, B.a[1] + j, B.a[0] + q);
-        acc[c] += w * v;
-        if (GRAD) {
-          accy[c] += B.db[1][j] * bzk * v;
-          accz[c] += B.b[1][j] * dbzk * v;
-        }
-      }
+    for (int c = 0; c < NC; ++c) {
+      dx[c] = group_sum<8>(dbxq * acc[c]) * g.inv_hf[0];
+      dy[c] = group_sum<8>(bxq * accy[c]) * g.inv_hf[1];
+      dz[c] = group_sum<8>(bxq * accz[c]) * g.inv_hf[2];
     }
   }
 }
 
 // MODE 0: vel; 1: vel + grad; 2: fused Heun step.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, 4) interp_staged(StagedArgs a) {
-  extern __shared__ float4 halo[];
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
+  extern __shared__ float4 smem[];
   constexpr bool GRAD = MODE == 1;
-  const int64_t bin = blockIdx.x;
+  const int bin = blockIdx.x;
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   if (beg >= end) return;
   const GridArgs& g = a.g;
   const int nbx = a.b.nb[0], nby = a.b.nb[1];
-  const int bxi = (int)(bin % nbx);
-  const int byi = (int)((bin / nbx) % nby);
-  const int bzi = (int)(bin / ((int64_t)nbx * nby));
+  const int bzi = bin / (nbx * nby);
+  const int rem = bin - bzi * nbx * nby;
+  const int byi = rem / nbx, bxi = rem - byi * nbx;
   const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
   const Tc* coef = static_cast<const Tc*>(a.coef);
-  stage_halo<Tc, NC>(a, coef, P0, halo);
+  float4* halo = smem;
+  float4* recs = smem + a.S[2] * a.PS;
+  if (a.vec)
+    stage_halo_vec<Tc, NC>(a, coef, P0, halo);
+  else
+    stage_halo<Tc, NC>(a, coef, P0, halo);
 
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int q = lane & 3, kh = (lane >> 2) & 1, sub = lane & 7;
+  const int warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const float4 cq = basis_coeffs(q), ck0 = basis_coeffs(kh), ck1 = basis_coeffs(kh + 2);
   const int Sx = a.S[0];
-  const int lane = threadIdx.x & 31, q = lane & 3, kh = (lane >> 2) & 1;
-  const int sub = lane & 7;
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const float nanf_ = __int_as_float(0x7fc00000);
   const int64_t np = a.np;
-  for (int s0 = beg + warp * 4; s0 < end; s0 += nw * 4) {
-    const int s = s0 + (lane >> 3);
-    const bool valid = s < end;
-    const int64_t slot = valid ? s : beg;
-    const int64_t p = a.perm ? a.perm[slot] : slot;
-    int cell[3];
-    float t[3];
-    double xd;
-    bool ok = locate_group<8, float>(g, a.pos_in, np, p, lane, cell, t, xd);
-    Basis<float, GRAD> B;
-    B.set(cell, t);
-    int l[3];
-    bool inh = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      l[d] = local_index(cell[d], P0[d], a.S[d]);
-      inh &= l[d] >= 0;
-    }
-    float acc[NC], accy[NC], accz[NC];
-    if (inh)
-      oct_rows_smem<NC, GRAD>(halo, a.PS, Sx, l, B, q, kh, acc, accy, accz);
-    else
-      oct_rows_global<Tc, NC, GRAD>(g, coef, a.scale, B, q, kh, acc, accy, accz);
-    const float bq = pick4(B.b[0], q);
-    float u[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) u[c] = group_sum<8>(bq * acc[c]);
+  const float nanf_ = __int_as_float(0x7fc00000);
 
-    if constexpr (MODE <= 1) {
-      float gx[NC], gy[NC], gz[NC];
-      if (GRAD) {
-        const float dbq = pick4(B.db[0], q);
+  for (int cb = beg; cb < end; cb += kRecords) {
+    const int m = min(kRecords, end - cb);
+    // phase A: one thread per particle
+    const bool mine = tid < m;
+    int64_t p = 0;
+    double x[3] = {0.0, 0.0, 0.0};
+    int cell[3] = {0, 0, 0};
+    float t[3] = {0.f, 0.f, 0.f};
+    bool ok = true;
+    if (mine) {
+      p = a.perm ? a.perm[cb + tid] : (int64_t)(cb + tid);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          gx[c] = group_sum<8>(dbq * acc[c]) * g.inv_hf[0];
-          gy[c] = group_sum<8>(bq * accy[c]) * g.inv_hf[1];
-          gz[c] = group_sum<8>(bq * accz[c]) * g.inv_hf[2];
-        }
+      for (int d = 0; d < 3; ++d) {
+        x[d] = a.pos_in[d * np + p];
+        ok &= locate(x[d], g.inv_h[d], g.n[d], cell[d], t[d]);
       }
-      if (valid) {
-        if (!ok && sub == 0) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+      write_record(recs + tid * kRecW, cell, t, ok, P0, a.S, a.PS, Sx);
+    }
+    __syncthreads();
+    // phase B: gathers, 8 lanes per particle; the loop is uniform per warp
+    // (the butterfly uses full-warp shuffles), idle groups redo record b4
+    for (int b4 = warp * 4; b4 < m; b4 += nwarps * 4) {
+      const int i = b4 + (lane >> 3);
+      const bool vi = i < m;
+      float u[NC], dx[NC], dy[NC], dz[NC];
+      gather8<Tc, NC, GRAD>(halo, a.PS, Sx, recs + (vi ? i : b4) * kRecW, g, coef, a.scale, q,
+                            kh, cq, ck0, ck1, u, dx, dy, dz);
+      if (!vi) continue;
+      if constexpr (MODE <= 1) {
+        const int64_t pi = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
+        const bool oki = __float_as_int(recs[i * kRecW + 1].w) != 0;
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          if (sub == c) a.vel[(int64_t)c * np + p] = ok ? u[c] : nanf_;
+          if (sub == c) a.vel[(int64_t)c * np + pi] = oki ? u[c] : nanf_;
         if (GRAD && a.grad) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            if (sub == 0) a.grad[((int64_t)c * 3 + 0) * np + p] = ok ? gx[c] : nanf_;
-            if (sub == 1) a.grad[((int64_t)c * 3 + 1) * np + p] = ok ? gy[c] : nanf_;
-            if (sub == 2) a.grad[((int64_t)c * 3 + 2) * np + p] = ok ? gz[c] : nanf_;
+            if (sub == 3) a.grad[((int64_t)c * 3 + 0) * np + pi] = oki ? dx[c] : nanf_;
+            if (sub == 4) a.grad[((int64_t)c * 3 + 1) * np + pi] = oki ? dy[c] : nanf_;
+            if (sub == 5) a.grad[((int64_t)c * 3 + 2) * np + pi] = oki ? dz[c] : nanf_;
           }
         }
-      }
-    } else {
-      // fused Heun step: predictor located in FP32 from the stage-1 cell
-      int c2[3];
-      float t2[3];
-      bool inh2 = a.coef2 == nullptr;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float tt = t[d] + (ok ? u[d] * a.dtih[d] : 0.f);
-        float fl = floorf(tt);
-        if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
-        const int di = (int)fl;
-        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
-        c2[d] = cell[d] + di;
-        l[d] = local_index(c2[d], P0[d], a.S[d]);
-        inh2 &= l[d] >= 0;
-      }
-      if (!inh2)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          int c = c2[d];
-          if (c < 0 || c >= g.n[d]) {
-            c %= g.n[d];
-            if (c < 0) c += g.n[d];
-          }
-          c2[d] = c;
-        }
-      B.set(c2, t2);
-      const Tc* cf2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
-      const float* sc2 = a.coef2 ? a.scale2 : a.scale;
-      if (inh2)
-        oct_rows_smem<NC, false>(halo, a.PS, Sx, l, B, q, kh, acc, accy, accz);
-      else
-        oct_rows_global<Tc, NC, false>(g, cf2, sc2, B, q, kh, acc, accy, accz);
-      const float bq2 = pick4(B.b[0], q);
-      float u2[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) u2[c] = group_sum<8>(bq2 * acc[c]);
-      if (valid) {
-        if (!ok && sub == 0) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
-        if (sub < 3) {
-          const double w = (double)(sel3(u, sub) + sel3(u2, sub));
-          a.pos_out[(int64_t)sub * np + p] =
-              ok ? fma(a.dt * 0.5, w, xd) : __longlong_as_double(0x7ff8000000000000ll);
-        } else if (sub < 6) {
-          if (a.vel) a.vel[(int64_t)(sub - 3) * np + p] = ok ? sel3(u, sub - 3) : nanf_;
-        } else if (sub == 6 && a.ids_out) {
-          a.ids_out[p] = a.ids_in[p];
-        }
+      } else {
+        if (sub == 0) recs[i * kRecW + 2] = make_float4(u[0], u[1], u[2], 0.f);
       }
     }
+    if constexpr (MODE <= 1) {
+      if (mine && !ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+      __syncthreads();
+      continue;
+    }
+    __syncthreads();
+    // phase A': predictor located in FP32 relative to the stage-1 cell
+    float u1[3] = {0.f, 0.f, 0.f};
+    if (mine) {
+      const float4 r2 = recs[tid * kRecW + 2];
+      u1[0] = r2.x;
+      u1[1] = r2.y;
+      u1[2] = r2.z;
+      int c2[3];
+      float t2[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float tt = t[d] + (ok ? u1[d] * a.dtih[d] : 0.f);
+        float fl = floorf(tt);
+        if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
+        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
+        int c = cell[d] + (int)fl;
+        if (c < 0 || c >= g.n[d]) {
+          c %= g.n[d];
+          if (c < 0) c += g.n[d];
+        }
+        c2[d] = c;
+      }
+      write_record(recs + tid * kRecW, c2, t2, ok, P0, a.S, a.PS, Sx);
+      if (a.coef2) recs[tid * kRecW].w = __int_as_float(-1);  // second field: global path
+    }
+    __syncthreads();
+    // phase B': second gathers
+    const Tc* cf2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
+    const float* sc2 = a.coef2 ? a.scale2 : a.scale;
+    for (int b4 = warp * 4; b4 < m; b4 += nwarps * 4) {
+      const int i = b4 + (lane >> 3);
+      const bool vi = i < m;
+      float u[NC], dx[NC], dy[NC], dz[NC];
+      gather8<Tc, NC, false>(halo, a.PS, Sx, recs + (vi ? i : b4) * kRecW, g, cf2, sc2, q, kh,
+                             cq, ck0, ck1, u, dx, dy, dz);
+      if (vi && sub == 0) recs[i * kRecW + 2] = make_float4(u[0], u[1], u[2], 0.f);
+    }
+    __syncthreads();
+    // phase C: FP64 position update, one thread per particle
+    if (mine) {
+      const float4 r2 = recs[tid * kRecW + 2];
+      const float u2[3] = {r2.x, r2.y, r2.z};
+      const double half_dt = a.dt * 0.5;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        a.pos_out[d * np + p] =
+            ok ? fma(half_dt, (double)(u1[d] + u2[d]), x[d]) : __longlong_as_double(0x7ff8000000000000ll);
+        if (a.vel) a.vel[d * np + p] = ok ? u1[d] : nanf_;
+      }
+      if (a.ids_out) a.ids_out[p] = a.ids_in[p];
+      if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+    }
+    __syncthreads();
   }
 }
 
@@ -635,16 +782,24 @@ int plane_stride(int sx, int sy) {
   return ps;
 }
 
-ps_status fill_staged(const ps_grid* grid, const int32_t brick[3], int E, StagedArgs* a,
-                      size_t* smem) {
+ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[3], int E,
+                      StagedArgs* a, size_t* smem) {
   ps_status rc = make_brick_args(grid, brick, &a->b);
   if (rc) return rc;
-  a->g = make_grid_args(grid);
+  a->g = make_grid_args(grid, coef_t);
   a->E = E;
   for (int d = 0; d < 3; ++d) a->S[d] = a->b.B[d] + 3 + 2 * E;
   if (a->S[0] > 32) return fail(PS_ERR_UNSUPPORTED, "brick x extent above 29 cells");
   a->PS = plane_stride(a->S[0], a->S[1]);
-  *smem = (size_t)a->S[2] * a->PS * sizeof(float4);
+  // vector staging needs E = 0, bricks tiling the grid, 16-byte-aligned halo
+  // rows and the last row vector inside the row pitch
+  const int V = coef_t == PS_F32 ? 4 : (coef_t == PS_BF16 || coef_t == PS_F16 ? 8 : 0);
+  bool vec = E == 0 && V > 0 && a->b.B[0] % V == 0;
+  for (int d = 0; d < 3; ++d) vec = vec && grid->n[d] % a->b.B[d] == 0;
+  const int qx = (a->S[0] + V - 1) / (V > 0 ? V : 1);
+  vec = vec && qx <= 4 && (a->b.nb[0] - 1) * a->b.B[0] + qx * V <= a->g.rx;
+  a->vec = vec ? 1 : 0;
+  *smem = ((size_t)a->S[2] * a->PS + (size_t)kRecords * kRecW) * sizeof(float4);
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
 }
@@ -659,7 +814,7 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
     if (rc) return rc;
   }
   if (a.b.nbins > 0x7fffffff) return fail(PS_ERR_UNSUPPORTED, "too many bins");
-  kern<<<(unsigned)a.b.nbins, 256, smem, st>>>(a);
+  kern<<<(unsigned)a.b.nbins, kRecords, smem, st>>>(a);
   return check_launch("interp_staged");
 }
 
@@ -675,7 +830,7 @@ ps_status rk2_launch_direct(const ps_grid* grid, ps_dtype coef_t, const void* c0
                             const float* s0, const void* c1, const float* s1, int64_t np,
                             double* pos, float* vel_out, double dt, int32_t* status,
                             cudaStream_t st) {
-  GridArgs g = make_grid_args(grid);
+  GridArgs g = make_grid_args(grid, coef_t);
   const float3 dtih = dt_over_h(g, dt);
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
@@ -696,7 +851,7 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
     return fail(PS_ERR_UNSUPPORTED, "staged RK2 needs F32/BF16/F16 coefficients");
   StagedArgs a{};
   size_t smem;
-  ps_status rc = fill_staged(grid, brick, E, &a, &smem);
+  ps_status rc = fill_staged(grid, coef_t, brick, E, &a, &smem);
   if (rc) return rc;
   a.coef = c0;
   a.scale = s0;
@@ -741,7 +896,7 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   if (perm && !bin_offsets) return fail(PS_ERR_INVALID_ARG, "perm needs bin_offsets");
   if (bin_offsets && !brick) return fail(PS_ERR_INVALID_ARG, "bin_offsets needs brick");
   cudaStream_t st = as_stream(stream);
-  GridArgs g = make_grid_args(grid);
+  GridArgs g = make_grid_args(grid, coef_t);
   const bool staged = bin_offsets && coef_t != PS_F64;
   if (!staged) {
     return with_coef_type(coef_t, [&](auto tag) -> ps_status {
@@ -767,7 +922,7 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   }
   StagedArgs a{};
   size_t smem;
-  if ((rc = fill_staged(grid, brick, 0, &a, &smem))) return rc;
+  if ((rc = fill_staged(grid, coef_t, brick, 0, &a, &smem))) return rc;
   a.coef = coef;
   a.scale = scale;
   a.np = np;
@@ -802,7 +957,7 @@ extern "C" ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np > 0 && (!pos || !g_vel)) return fail(PS_ERR_INVALID_ARG, "pos and g_vel required");
   cudaStream_t st = as_stream(stream);
-  GridArgs g = make_grid_args(grid);
+  GridArgs g = make_grid_args(grid, coef_t);
   if (g_pos && np > 0) {
     if ((rc = check_coef(coef_t, coef, scale))) return rc;
     rc = with_coef_type(coef_t, [&](auto tag) -> ps_status {

@@ -52,10 +52,15 @@ size_t dtype_size(ps_dtype t);
 struct GridArgs {
   int n[3];        // nodes per axis
   int m[3];        // padded extents n+3
+  int rx;          // coefficient row pitch in elements (>= n[0]+3, 16-byte rows)
   double inv_h[3]; // n/L, computed on the host in FP64
   float inv_hf[3]; // the same, rounded to FP32 (derivative scaling)
 };
-GridArgs make_grid_args(const ps_grid* g);
+// rx is left 0 unless a coefficient dtype is given.
+GridArgs make_grid_args(const ps_grid* g, int coef_t = -1);
+// Row pitch (elements) of a padded coefficient array: nx+3 rounded up to a
+// multiple of 16 bytes.
+int64_t coef_pitch(int nx, ps_dtype t);
 
 struct BrickArgs {
   int B[3];   // brick edge in cells per axis
@@ -193,6 +198,19 @@ template <> struct CoefLoad<__nv_bfloat16> {
 template <> struct CoefLoad<__half> {
   static __device__ __forceinline__ float ld(const __half* p) {
     return __half2float(__ldg(p));
+  }
+};
+
+// Raw 16-bit pattern -> float.
+template <typename H> struct CoefLoadBits;
+template <> struct CoefLoadBits<__nv_bfloat16> {
+  static __device__ __forceinline__ float f(unsigned short b) {
+    return __uint_as_float((unsigned)b << 16);
+  }
+};
+template <> struct CoefLoadBits<__half> {
+  static __device__ __forceinline__ float f(unsigned short b) {
+    return __half2float(__ushort_as_half(b));
   }
 };
 

@@ -288,12 +288,14 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
     for (int iy = 0; iy < npy; ++iy) {
       const int Pz = pzs[iz], Py = pys[iy];
       Tout* orow = dst + dv.off + c * dv.sc + Pz * dv.sz + Py * dv.sy;
-      for (int P = lane; P < nx + 3; P += 32) {
+      // the row pitch dv.sy >= nx + 3; the tail of the row is zeroed
+      for (int P = lane; P < dv.sy; P += 32) {
         const int e = skew(padded_to_node(P, nx), inv_L);
+        const T val = P < nx + 3 ? buf[e] : T(0);
         if constexpr (sizeof(T) == 8)
-          orow[P] = cvt_out_d<Tout>((double)buf[e]);
+          orow[P] = cvt_out_d<Tout>((double)val);
         else
-          orow[P] = cvt_out<Tout>((float)buf[e]);
+          orow[P] = cvt_out<Tout>((float)val);
       }
       if (QUANT && lane == 0) scale[((int64_t)c * (nz + 3) + Pz) * (ny + 3) + Py] = sc;
     }
@@ -401,12 +403,13 @@ View unpadded_view(const ps_grid* g) {
   const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
   return View{0, nx * ny * nz, nx * ny, nx};
 }
-View padded_view(const ps_grid* g) {
-  const int64_t mx = g->n[0] + 3, my = g->n[1] + 3, mz = g->n[2] + 3;
-  return View{0, mx * my * mz, mx * my, mx};
+// Padded coefficient array with row pitch `rx` elements.
+View padded_view(const ps_grid* g, int64_t rx) {
+  const int64_t my = g->n[1] + 3, mz = g->n[2] + 3;
+  return View{0, rx * my * mz, rx * my, rx};
 }
-View interior_view(const ps_grid* g) {
-  View v = padded_view(g);
+View interior_view(const ps_grid* g, int64_t rx) {
+  View v = padded_view(g, rx);
   v.off = v.sz + v.sy + 1;
   return v;
 }
@@ -467,7 +470,8 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
     for (int d = 0; d < 3; ++d)
       if (grid->n[d] > 1024) return fail(PS_ERR_UNSUPPORTED, "FP64 coefficients need n <= 1024");
   cudaStream_t st = as_stream(stream);
-  const View fv = unpadded_view(grid), pv = padded_view(grid), iv = interior_view(grid);
+  const int64_t rx = coef_pitch(grid->n[0], coef_t);
+  const View fv = unpadded_view(grid), pv = padded_view(grid, rx), iv = interior_view(grid, rx);
   const float* ff = static_cast<const float*>(field);
   const double* fd = static_cast<const double*>(field);
 

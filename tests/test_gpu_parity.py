@@ -46,7 +46,7 @@ def test_spline_coeffs_f32(n):
     f = torch.from_numpy(field.astype(np.float32)).to(DEV)
     sf = ps.SplineField.from_field(f, torch.float32)
     ref32 = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
-    got = sf.coef.cpu().numpy()
+    got = sf.padded().cpu().numpy()
     assert got.shape == ref.shape
     assert np.abs(got - ref32).max() <= coef_tol(field)
 
@@ -56,9 +56,9 @@ def test_spline_coeffs_f64_field_and_coef():
     field = synth.random_field(n, ncomp=3, seed=5)
     ref = oracle.spline_coeffs(field)
     f = torch.from_numpy(field).to(DEV)
-    c64 = ps.SplineField.from_field(f, torch.float64).coef.cpu().numpy()
+    c64 = ps.SplineField.from_field(f, torch.float64).padded().cpu().numpy()
     assert np.abs(c64 - ref).max() <= 1e-13 * np.abs(field).max()
-    c32 = ps.SplineField.from_field(f, torch.float32).coef.cpu().numpy()
+    c32 = ps.SplineField.from_field(f, torch.float32).padded().cpu().numpy()
     assert np.abs(c32 - ref).max() <= coef_tol(field)
 
 
@@ -70,7 +70,7 @@ def test_spline_coeffs_long_pencils(n):
         shape = tuple(dims[p] for p in perm)
         field = synth.random_field(shape, ncomp=1, seed=n + perm[0])
         f = torch.from_numpy(field.astype(np.float32)).to(DEV)
-        got = ps.SplineField.from_field(f, torch.float32).coef.cpu().numpy()
+        got = ps.SplineField.from_field(f, torch.float32).padded().cpu().numpy()
         ref = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
         assert np.abs(got - ref).max() <= coef_tol(field), shape
 
@@ -274,7 +274,7 @@ def test_backward_positions_and_field():
     pg = torch.from_numpy(pos).to(DEV)
     g_pos = torch.empty_like(pg)
     g_field = torch.empty((3,) + tuple(reversed(n)), dtype=torch.float32, device=DEV)
-    ps.ps_interp_backward(sf.coef, pg, torch.from_numpy(w).to(DEV), g_pos, g_field)
+    ps.ps_interp_backward(sf.coef, sf.n, pg, torch.from_numpy(w).to(DEV), g_pos, g_field)
     gp = g_pos.cpu().numpy()
     scale_p = 3 * (n[0] / TWO_PI) * np.abs(cref).max() * np.abs(w).max() * 3
     assert np.abs(gp - gp_ref).max() <= 1e-5 * scale_p
