@@ -117,6 +117,14 @@ def ps_version() -> str:
     return _lib().ps_version().decode()
 
 
+def ps_tune_set(key: str, value: int):
+    _check(_lib().ps_tune_set(key.encode(), int(value)))
+
+
+def ps_tune_get(key: str) -> int:
+    return int(_lib().ps_tune_get(key.encode()))
+
+
 def ps_status_clear(status: torch.Tensor, stream=None):
     _dev(status, "status", torch.int32, 4)
     _check(_lib().ps_status_clear(_ptr(status), _stream(stream)))

@@ -39,6 +39,8 @@ SIGNATURES = {
     "ps_last_error": (ctypes.c_char_p, []),
     "ps_version": (ctypes.c_char_p, []),
     "ps_coef_row_pitch": (_I64, [_I, _I]),
+    "ps_tune_set": (_I, [ctypes.c_char_p, _I64]),
+    "ps_tune_get": (_I64, [ctypes.c_char_p]),
     "ps_status_clear": (_I, [_P, _P]),
     "ps_status_read": (_I, [_P, _P, _P]),
     "ps_spline_coeffs_workspace_size": (_SZ, [_GP, _I, _I]),

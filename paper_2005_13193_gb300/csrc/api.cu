@@ -87,11 +87,46 @@ ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* o
   return PS_OK;
 }
 
+Tuning& tuning() {
+  static Tuning t;
+  return t;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    return 1;
+  return n;
+}
+
 }  // namespace ps
 
 using namespace ps;
 
 extern "C" const char* ps_last_error(void) { return g_err; }
+
+extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
+  if (!key) return fail(PS_ERR_INVALID_ARG, "key is NULL");
+  if (!strcmp(key, "brick_kernel")) {
+    if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0 or 1");
+    tuning().brick_kernel = (int)value;
+    return PS_OK;
+  }
+  if (!strcmp(key, "brick_ctas_per_sm")) {
+    if (value < 1 || value > 8) return fail(PS_ERR_INVALID_ARG, "brick_ctas_per_sm in [1, 8]");
+    tuning().brick_ctas_per_sm = (int)value;
+    return PS_OK;
+  }
+  return fail(PS_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
+}
+
+extern "C" int64_t ps_tune_get(const char* key) {
+  if (!key) return -1;
+  if (!strcmp(key, "brick_kernel")) return tuning().brick_kernel;
+  if (!strcmp(key, "brick_ctas_per_sm")) return tuning().brick_ctas_per_sm;
+  return -1;
+}
 
 extern "C" const char* ps_version(void) { return "ps 0.1 (sm_103a)"; }
 

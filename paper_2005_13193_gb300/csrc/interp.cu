@@ -17,6 +17,7 @@
 // parallel); floor and fraction come from the bits of the product, the RK2
 // predictor position is located in FP32 relative to the stage-1 cell, and the
 // position update is one FMA per axis.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -614,28 +615,22 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
   }
 }
 
-// MODE 0: vel; 1: vel + grad; 2: fused Heun step.
-template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
-  extern __shared__ float4 smem[];
-  constexpr bool GRAD = MODE == 1;
-  const int bin = blockIdx.x;
-  const int beg = a.offs[bin], end = a.offs[bin + 1];
-  if (beg >= end) return;
-  const GridArgs& g = a.g;
-  const int nbx = a.b.nb[0], nby = a.b.nb[1];
-  const int bzi = bin / (nbx * nby);
-  const int rem = bin - bzi * nbx * nby;
-  const int byi = rem / nbx, bxi = rem - byi * nbx;
-  const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
-  const Tc* coef = static_cast<const Tc*>(a.coef);
-  float4* halo = smem;
-  float4* recs = smem + a.S[2] * a.PS;
-  if (a.vec)
-    stage_halo_vec<Tc, NC>(a, coef, P0, halo);
-  else
-    stage_halo<Tc, NC>(a, coef, P0, halo);
+template <typename Tc, int NC>
+__device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsigned char* raw,
+                                            double* pbuf);
 
+// Particles [beg, end) of one brick whose halo is in shared memory (phases
+// A, B, A', B', C described above).  pbuf: optional shared copy of the first
+// round's positions ([3][kRecords]).  raw_next: if set, the copies of brick
+// next_bin are issued as soon as phase A has consumed pbuf.
+template <typename Tc, int NC, int MODE>
+__device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int end,
+                                              const int P0[3], const float4* halo,
+                                              float4* recs, double* pbuf,
+                                              unsigned char* raw_next, int next_bin) {
+  constexpr bool GRAD = MODE == 1;
+  const GridArgs& g = a.g;
+  const Tc* coef = static_cast<const Tc*>(a.coef);
   const int tid = threadIdx.x, lane = tid & 31;
   const int q = lane & 3, kh = (lane >> 2) & 1, sub = lane & 7;
   const int warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -657,12 +652,13 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(St
       p = a.perm ? a.perm[cb + tid] : (int64_t)(cb + tid);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        x[d] = a.pos_in[d * np + p];
+        x[d] = (pbuf && cb == beg) ? pbuf[d * kRecords + tid] : a.pos_in[d * np + p];
         ok &= locate(x[d], g.inv_h[d], g.n[d], cell[d], t[d]);
       }
       write_record(recs + tid * kRecW, cell, t, ok, P0, a.S, a.PS, Sx);
     }
     __syncthreads();
+    if (raw_next && cb == beg) issue_brick<Tc, NC>(a, next_bin, raw_next, pbuf);
     // phase B: gathers, 8 lanes per particle; the loop is uniform per warp
     // (the butterfly uses full-warp shuffles), idle groups redo record b4
     for (int b4 = warp * 4; b4 < m; b4 += nwarps * 4) {
@@ -752,6 +748,172 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(St
   }
 }
 
+// MODE 0: vel; 1: vel + grad; 2: fused Heun step.  One CTA per brick.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
+  extern __shared__ float4 smem[];
+  const int bin = blockIdx.x;
+  const int beg = a.offs[bin], end = a.offs[bin + 1];
+  if (beg >= end) return;
+  const int nbx = a.b.nb[0], nby = a.b.nb[1];
+  const int bzi = bin / (nbx * nby);
+  const int rem = bin - bzi * nbx * nby;
+  const int byi = rem / nbx, bxi = rem - byi * nbx;
+  const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  float4* halo = smem;
+  float4* recs = smem + a.S[2] * a.PS;
+  if (a.vec)
+    stage_halo_vec<Tc, NC>(a, coef, P0, halo);
+  else
+    stage_halo<Tc, NC>(a, coef, P0, halo);
+  process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, recs, nullptr, nullptr, 0);
+}
+
+// ------------------------------------------------------ persistent form ----
+// Each CTA walks bricks b = blockIdx.x, blockIdx.x + gridDim.x, ...  While it
+// processes the particles of one brick, the halo rows of its next non-empty
+// brick (16-byte cp.async copies into a raw buffer) and that brick's first
+// kRecords positions are already in flight; at the top of the next iteration
+// the raw rows are transposed into the float4-per-point halo.  Needs the
+// vector staging conditions (a.vec).
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void brick_origin(const StagedArgs& a, int bin, int P0[3]) {
+  const int nbx = a.b.nb[0], nby = a.b.nb[1];
+  const int bzi = bin / (nbx * nby);
+  const int rem = bin - bzi * nbx * nby;
+  const int byi = rem / nbx, bxi = rem - byi * nbx;
+  P0[0] = bxi * a.b.B[0];
+  P0[1] = byi * a.b.B[1];
+  P0[2] = bzi * a.b.B[2];
+}
+
+// Next brick (in this CTA's sequence) holding particles, or nbins.
+__device__ __forceinline__ int next_busy(const StagedArgs& a, int bin) {
+  const int nb = (int)a.b.nbins;
+  while (bin < nb && a.offs[bin] >= a.offs[bin + 1]) bin += gridDim.x;
+  return bin < nb ? bin : nb;
+}
+
+// Raw row buffer: [NC][rows][qx * V] elements of Tc, rows 16-byte aligned.
+template <typename Tc, int NC>
+__device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsigned char* raw,
+                                            double* pbuf) {
+  constexpr int V = Vec16<Tc>::V;
+  const GridArgs& g = a.g;
+  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
+  const int qx = (Sx + V - 1) / V;
+  const int nrows = Sy * Sz;
+  int P0[3];
+  brick_origin(a, bin, P0);
+  const int64_t rx = g.rx, m1 = g.m[1], m2 = g.m[2];
+  const int64_t cs = rx * m1 * m2;
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
+  const int items = NC * nrows * qx;
+  Tc* rawt = reinterpret_cast<Tc*>(raw);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int q = it % qx;
+    const int rr = it / qx;
+    const int c = rr / nrows, r = rr - c * nrows;
+    const int lz = r / Sy, ly = r - lz * Sy;
+    cp_async16(rawt + (int64_t)(c * nrows + r) * (qx * V) + q * V,
+               base + c * cs + ((int64_t)lz * m1 + ly) * rx + q * V);
+  }
+  const int beg = a.offs[bin], end = a.offs[bin + 1];
+  const int m = min(kRecords, end - beg);
+  if (!a.perm && threadIdx.x < m)
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      cp_async8(pbuf + d * kRecords + threadIdx.x, a.pos_in + d * a.np + beg + threadIdx.x);
+  cp_async_commit();
+}
+
+// Raw rows -> float4 (u, v, w, 0) per halo point (with the x-line scale of
+// quantised coefficients).
+template <typename Tc, int NC>
+__device__ __forceinline__ void transpose_brick(const StagedArgs& a, const int P0[3],
+                                                const unsigned char* raw, float4* halo) {
+  constexpr int V = Vec16<Tc>::V;
+  const GridArgs& g = a.g;
+  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
+  const int qx = (Sx + V - 1) / V;
+  const int nrows = Sy * Sz;
+  const Tc* rawt = reinterpret_cast<const Tc*>(raw);
+  const int64_t m1 = g.m[1], m2 = g.m[2];
+  for (int it = threadIdx.x; it < nrows * qx; it += blockDim.x) {
+    const int q = it % qx, r = it / qx;
+    const int lz = r / Sy, ly = r - lz * Sy;
+    float v[NC][V];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float s = 1.f;
+      if (IsQuant<Tc>::value)
+        s = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
+      const Tc* src = rawt + (int64_t)(c * nrows + r) * (qx * V) + q * V;
+      if constexpr (std::is_same<Tc, float>::value) {
+        const float4 w = *reinterpret_cast<const float4*>(src);
+        v[c][0] = w.x; v[c][1] = w.y; v[c][2] = w.z; v[c][3] = w.w;
+      } else {
+        const uint4 w = *reinterpret_cast<const uint4*>(src);
+        const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          v[c][2 * i] = CoefLoadBits<Tc>::f((unsigned short)(ww[i] & 0xffffu)) * s;
+          v[c][2 * i + 1] = CoefLoadBits<Tc>::f((unsigned short)(ww[i] >> 16)) * s;
+        }
+      }
+    }
+    const int h0 = lz * a.PS + ly * Sx + q * V;
+#pragma unroll
+    for (int i = 0; i < V; ++i)
+      if (q * V + i < Sx)
+        halo[h0 + i] = make_float4(v[0][i], NC > 1 ? v[NC > 1 ? 1 : 0][i] : 0.f,
+                                   NC > 2 ? v[NC > 2 ? 2 : 0][i] : 0.f, 0.f);
+  }
+}
+
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256, 3) track_bricks(StagedArgs a) {
+  extern __shared__ float4 smem[];
+  float4* halo = smem;
+  float4* recs = halo + a.S[2] * a.PS;
+  double* pbuf = reinterpret_cast<double*>(recs + kRecords * kRecW);
+  unsigned char* raw = reinterpret_cast<unsigned char*>(pbuf + 3 * kRecords);
+  int bin = next_busy(a, blockIdx.x);
+  const int nb = (int)a.b.nbins;
+  if (bin >= nb) return;
+  issue_brick<Tc, NC>(a, bin, raw, pbuf);
+  while (bin < nb) {
+    cp_async_wait_all();
+    __syncthreads();
+    int P0[3];
+    brick_origin(a, bin, P0);
+    transpose_brick<Tc, NC>(a, P0, raw, halo);
+    __syncthreads();
+    const int beg = a.offs[bin], end = a.offs[bin + 1];
+    const int nxt = next_busy(a, bin + gridDim.x);
+    process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, recs, a.perm ? nullptr : pbuf,
+                                nxt < nb ? raw : nullptr, nxt);
+    bin = nxt;
+  }
+}
+
 // ------------------------------------------------------------------ host ----
 
 template <typename F>
@@ -806,6 +968,28 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
 
 template <typename Tc, int NC, int MODE>
 ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
+  if constexpr (sizeof(Tc) != 8) {
+    if (a.vec && tuning().brick_kernel == 1) {
+      constexpr int V = 16 / (int)sizeof(Tc);
+      const int qx = (a.S[0] + V - 1) / V;
+      const size_t raw = (size_t)NC * a.S[1] * a.S[2] * qx * V * sizeof(Tc);
+      const size_t sm = ((size_t)a.S[2] * a.PS + (size_t)kRecords * kRecW) * sizeof(float4) +
+                        3 * kRecords * sizeof(double) + raw;
+      if (sm <= 227 * 1024) {
+        auto pk = track_bricks<Tc, NC, MODE>;
+        if (sm > 48 * 1024) {
+          ps_status rc = check_cuda(
+              cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+              "persistent smem attribute");
+          if (rc) return rc;
+        }
+        const int64_t grid = std::min<int64_t>(a.b.nbins,
+                                               (int64_t)sm_count() * tuning().brick_ctas_per_sm);
+        pk<<<(unsigned)grid, kRecords, sm, st>>>(a);
+        return check_launch("track_bricks");
+      }
+    }
+  }
   auto kern = interp_staged<Tc, NC, MODE>;
   if (smem > 48 * 1024) {
     ps_status rc = check_cuda(

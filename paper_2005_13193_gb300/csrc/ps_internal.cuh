@@ -69,6 +69,14 @@ struct BrickArgs {
 };
 ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* out);
 
+// Launch-shape choices an autotuner may change (ps_tune_set).
+struct Tuning {
+  int brick_kernel = 1;       // 0: one CTA per brick; 1: persistent, pipelined
+  int brick_ctas_per_sm = 3;  // resident CTAs per SM of the persistent form
+};
+Tuning& tuning();
+int sm_count();
+
 // ------------------------------------------------------- cross-file API ----
 
 // Periodic solves in place on an unpadded F32 array [ncomp][nz][ny][nx]

@@ -171,6 +171,46 @@ def test_interp_staged_sorted_and_perm(brick):
     assert rel_err(vel_s, ref[:, perm]) <= 1e-5
 
 
+@pytest.fixture
+def brick_kernel():
+    old = ps.ps_tune_get("brick_kernel")
+    yield
+    ps.ps_tune_set("brick_kernel", old)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("dtype,bound", [(torch.float32, 1e-5), (torch.bfloat16, 1e-2)])
+def test_brick_kernels_on_tiling_grids(kernel, dtype, bound, brick_kernel):
+    # grids divisible by the brick: 16-byte halo rows, both brick kernels
+    ps.ps_tune_set("brick_kernel", kernel)
+    n = (48, 40, 32)
+    field, pos, cref = _case(n, 30000, seed=27, spread=1.4)
+    ref_v, ref_g = oracle.interp(cref, pos, grad=True)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), dtype)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins, sorted_pos = ps.bin_particles(n, (8, 8, 8), pg, want_sorted=True)
+    perm = bins.perm.cpu().numpy()
+    # positions in bin order, and through the permutation
+    v_s = sf.interp(sorted_pos, bins=ps.Bins(bins.brick, bins.offsets, bins.bin_of, None))
+    assert rel_err(v_s.cpu().numpy(), ref_v[:, perm]) <= bound
+    vel, grad = sf.interp(pg, grad=True, bins=bins)
+    assert rel_err(vel.cpu().numpy(), ref_v) <= bound
+    if dtype == torch.float32:
+        cmax = np.abs(cref).max()
+        for d in range(3):
+            tol = 1e-5 * 3 * (n[d] / TWO_PI) * cmax
+            assert np.abs(grad[:, d].cpu().numpy() - ref_g[:, d]).max() <= tol
+    # fused RK2 step on the sorted positions
+    dt = 1e-2
+    new_ref, u1_ref = oracle.rk2_step(cref, pos[:, perm], dt)
+    tr = ps.Tracker(sf, sorted_pos.clone(), brick=(8, 8, 8))
+    tr.step(dt)
+    ids = tr.ids.cpu().numpy()
+    rms = np.sqrt((u1_ref ** 2).mean())
+    tol = dt * bound * rms + 1e-14
+    assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= tol
+
+
 def test_interp_stale_bins_fall_back_correctly():
     # bins computed for other positions: every particle takes the global path
     n = (32, 32, 32)
