@@ -178,23 +178,33 @@ def brick_kernel():
     ps.ps_tune_set("brick_kernel", old)
 
 
+def abs_err(gpu, ref):
+    return np.abs(np.asarray(gpu, dtype=np.float64) - np.asarray(ref)).max()
+
+
 @pytest.mark.parametrize("kernel", [0, 1])
-@pytest.mark.parametrize("dtype,bound", [(torch.float32, 1e-5), (torch.bfloat16, 1e-2)])
-def test_brick_kernels_on_tiling_grids(kernel, dtype, bound, brick_kernel):
-    # grids divisible by the brick: 16-byte halo rows, both brick kernels
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_brick_kernels_on_tiling_grids(kernel, dtype, brick_kernel):
+    # Grids divisible by the brick: 16-byte halo rows, both brick kernels.
+    # Bounds: FP32 1e-5 of rms.  BF16 stores c/s with s a power of two, so each
+    # coefficient has relative error <= 2^-9; the basis weights are
+    # non-negative and sum to one, so |du| <= 2^-9 max|c| (2^-8 with margin).
+    # On this white-noise field max|c| is ~30x rms, hence an absolute bound.
     ps.ps_tune_set("brick_kernel", kernel)
     n = (48, 40, 32)
     field, pos, cref = _case(n, 30000, seed=27, spread=1.4)
     ref_v, ref_g = oracle.interp(cref, pos, grad=True)
+    rms = np.sqrt((ref_v ** 2).mean())
+    tol_u = 1e-5 * rms if dtype == torch.float32 else 2.0 ** -8 * np.abs(cref).max()
     sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), dtype)
     pg = torch.from_numpy(pos).to(DEV)
     bins, sorted_pos = ps.bin_particles(n, (8, 8, 8), pg, want_sorted=True)
     perm = bins.perm.cpu().numpy()
     # positions in bin order, and through the permutation
     v_s = sf.interp(sorted_pos, bins=ps.Bins(bins.brick, bins.offsets, bins.bin_of, None))
-    assert rel_err(v_s.cpu().numpy(), ref_v[:, perm]) <= bound
+    assert abs_err(v_s.cpu().numpy(), ref_v[:, perm]) <= tol_u
     vel, grad = sf.interp(pg, grad=True, bins=bins)
-    assert rel_err(vel.cpu().numpy(), ref_v) <= bound
+    assert abs_err(vel.cpu().numpy(), ref_v) <= tol_u
     if dtype == torch.float32:
         cmax = np.abs(cref).max()
         for d in range(3):
@@ -206,9 +216,7 @@ def test_brick_kernels_on_tiling_grids(kernel, dtype, bound, brick_kernel):
     tr = ps.Tracker(sf, sorted_pos.clone(), brick=(8, 8, 8))
     tr.step(dt)
     ids = tr.ids.cpu().numpy()
-    rms = np.sqrt((u1_ref ** 2).mean())
-    tol = dt * bound * rms + 1e-14
-    assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= tol
+    assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= dt * tol_u + 1e-14
 
 
 def test_interp_stale_bins_fall_back_correctly():
