@@ -483,16 +483,21 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
   __syncthreads();
 }
 
-// Particle records in shared memory (one per particle of the current round):
-//   rec[0] = (t_x, t_y, t_z, origin)  fractions and the halo index of the
-//            stencil origin (float bits of an int; -1 = not in the halo)
-//   rec[1] = (cell_x, cell_y, cell_z, ok) global cells for the fallback path
-//   rec[2] = (u, v, w, -)               result of the last gather
-constexpr int kRecords = 256;  // particles per round (= threads per CTA)
-constexpr int kRecW = 3;       // float4 per record
+// Particle records in shared memory (one per particle of the current round),
+// written by one thread per particle and read by the particle's 8 gather
+// lanes:
+//   rec[0]      = b_i(t_x), i = 0..3
+//   rec[1 + k]  = b_j(t_y) b_k(t_z), j = 0..3   (k = 0..3)
+//   rec[5]      = (origin, cell_x, cell_y, cell_z)  int bits; origin = halo
+//                 index of the stencil's first point, -1 = not in the halo
+//   rec[6]      = (t_x, t_y, t_z, ok)
+//   rec[7]      = (u, v, w, -) result of the last gather
+constexpr int kRecords = 128;  // particles per round
+constexpr int kRecW = 8;       // float4 per record
+constexpr int kThreads = 256;  // threads per brick CTA
 
-// Cubic coefficients (t^3, t^2, t, 1) of basis function i, and of its
-// derivative (t^2, t, 1) when asked; i is a lane constant.
+// Cubic coefficients (t^3, t^2, t, 1) of basis function i; i is a lane
+// constant (used for the derivative weights of the gradient).
 __device__ __forceinline__ float4 basis_coeffs(int i) {
   const float s = 1.f / 6.f;
   return i == 0 ? make_float4(-s, 0.5f, -0.5f, s)
@@ -507,9 +512,8 @@ __device__ __forceinline__ float dhorner3(float4 c, float t) {
   return fmaf(fmaf(3.f * c.x, t, 2.f * c.y), t, c.z);
 }
 
-// Phase A: one thread per particle.  Locates the particle (exact FP64 index
-// arithmetic), writes its record.  Returns ok.
-__device__ __forceinline__ bool write_record(float4* rec, const int cell[3], const float t[3],
+// Phases A and A': one thread per particle writes its record.
+__device__ __forceinline__ void write_record(float4* rec, const int cell[3], const float t[3],
                                              bool ok, const int P0[3], const int S[3], int PS,
                                              int Sx) {
   int l[3];
@@ -520,10 +524,21 @@ __device__ __forceinline__ bool write_record(float4* rec, const int cell[3], con
     inh &= (unsigned)l[d] <= (unsigned)(S[d] - 4);
   }
   const int origin = inh ? l[2] * PS + l[1] * Sx + l[0] : -1;
-  rec[0] = make_float4(t[0], t[1], t[2], __int_as_float(origin));
-  rec[1] = make_float4(__int_as_float(cell[0]), __int_as_float(cell[1]),
-                       __int_as_float(cell[2]), __int_as_float(ok ? 1 : 0));
-  return ok;
+  float bx[4], by[4], bz[4];
+  bspline<float>(t[0], bx);
+  bspline<float>(t[1], by);
+  bspline<float>(t[2], bz);
+  rec[0] = make_float4(bx[0], bx[1], bx[2], bx[3]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    rec[1 + k] = make_float4(by[0] * bz[k], by[1] * bz[k], by[2] * bz[k], by[3] * bz[k]);
+  rec[5] = make_float4(__int_as_float(origin), __int_as_float(cell[0]), __int_as_float(cell[1]),
+                       __int_as_float(cell[2]));
+  rec[6] = make_float4(t[0], t[1], t[2], __int_as_float(ok ? 1 : 0));
+}
+
+__device__ __forceinline__ float f4get(const float4 v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
 // Phase B: 8 lanes per particle.  Lane (q, kh) covers stencil column
@@ -536,42 +551,46 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
                                         const float4* rec, const GridArgs& g,
                                         const Tc* __restrict__ coef,
                                         const float* __restrict__ scale, int q, int kh,
-                                        float4 cq, float4 ck0, float4 ck1, float out[NC],
-                                        float dx[NC], float dy[NC], float dz[NC]) {
-  const float4 r0 = rec[0];
-  const float bxq = horner3(cq, r0.x);
-  float by[4], dby[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float4 cj = basis_coeffs(j);
-    by[j] = horner3(cj, r0.y);
-    if (GRAD) dby[j] = dhorner3(cj, r0.y);
-  }
-  const float bz0 = horner3(ck0, r0.z), bz1 = horner3(ck1, r0.z);
-  float dbz0 = 0.f, dbz1 = 0.f;
+                                        float out[NC], float dx[NC], float dy[NC],
+                                        float dz[NC]) {
+  const float bxq = reinterpret_cast<const float*>(rec)[q];
+  const float4 w0 = rec[1 + kh], w1 = rec[3 + kh];
+  const float4 r5 = rec[5];
+  const int origin = __float_as_int(r5.x);
+  // gradient weights from the fractions (only when asked)
+  float by[4], dby[4], bz[2], dbz[2];
   if (GRAD) {
-    dbz0 = dhorner3(ck0, r0.z);
-    dbz1 = dhorner3(ck1, r0.z);
+    const float4 r6 = rec[6];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 cj = basis_coeffs(j);
+      by[j] = horner3(cj, r6.y);
+      dby[j] = dhorner3(cj, r6.y);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const float4 ck = basis_coeffs(kh + 2 * kk);
+      bz[kk] = horner3(ck, r6.z);
+      dbz[kk] = dhorner3(ck, r6.z);
+    }
   }
   float acc[NC], accy[NC], accz[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
-  const int origin = __float_as_int(r0.w);
   if (origin >= 0) {
     const float4* hp = halo + origin + kh * PS + q;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
-      const float bz = kk ? bz1 : bz0;
-      const float dbz = kk ? dbz1 : dbz0;
+      const float4 wr = kk ? w1 : w0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float4 v = hp[2 * kk * PS + j * Sx];
         const float vv[3] = {v.x, v.y, v.z};
-        const float w = by[j] * bz;
+        const float w = f4get(wr, j);
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
         if (GRAD) {
-          const float wy = dby[j] * bz, wz = by[j] * dbz;
+          const float wy = dby[j] * bz[kk], wz = by[j] * dbz[kk];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             accy[c] = fmaf(wy, vv[c], accy[c]);
@@ -581,22 +600,20 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
       }
     }
   } else {
-    const float4 r1 = rec[1];
-    const int ax = __float_as_int(r1.x), ay = __float_as_int(r1.y), az = __float_as_int(r1.z);
+    const int ax = __float_as_int(r5.y), ay = __float_as_int(r5.z), az = __float_as_int(r5.w);
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
-      const float bz = kk ? bz1 : bz0;
-      const float dbz = kk ? dbz1 : dbz0;
+      const float4 wr = kk ? w1 : w0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float w = by[j] * bz;
+        const float w = f4get(wr, j);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const float v = load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j, ax + q);
           acc[c] = fmaf(w, v, acc[c]);
           if (GRAD) {
-            accy[c] = fmaf(dby[j] * bz, v, accy[c]);
-            accz[c] = fmaf(by[j] * dbz, v, accz[c]);
+            accy[c] = fmaf(dby[j] * bz[kk], v, accy[c]);
+            accz[c] = fmaf(by[j] * dbz[kk], v, accz[c]);
           }
         }
       }
@@ -605,7 +622,7 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
 #pragma unroll
   for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
   if (GRAD) {
-    const float dbxq = dhorner3(cq, r0.x);
+    const float dbxq = dhorner3(basis_coeffs(q), rec[6].x);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       dx[c] = group_sum<8>(dbxq * acc[c]) * g.inv_hf[0];
@@ -634,7 +651,6 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   const int tid = threadIdx.x, lane = tid & 31;
   const int q = lane & 3, kh = (lane >> 2) & 1, sub = lane & 7;
   const int warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const float4 cq = basis_coeffs(q), ck0 = basis_coeffs(kh), ck1 = basis_coeffs(kh + 2);
   const int Sx = a.S[0];
   const int64_t np = a.np;
   const float nanf_ = __int_as_float(0x7fc00000);
@@ -666,11 +682,11 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
       gather8<Tc, NC, GRAD>(halo, a.PS, Sx, recs + (vi ? i : b4) * kRecW, g, coef, a.scale, q,
-                            kh, cq, ck0, ck1, u, dx, dy, dz);
+                            kh, u, dx, dy, dz);
       if (!vi) continue;
       if constexpr (MODE <= 1) {
         const int64_t pi = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
-        const bool oki = __float_as_int(recs[i * kRecW + 1].w) != 0;
+        const bool oki = __float_as_int(recs[i * kRecW + 6].w) != 0;
 #pragma unroll
         for (int c = 0; c < NC; ++c)
           if (sub == c) a.vel[(int64_t)c * np + pi] = oki ? u[c] : nanf_;
@@ -683,7 +699,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
           }
         }
       } else {
-        if (sub == 0) recs[i * kRecW + 2] = make_float4(u[0], u[1], u[2], 0.f);
+        if (sub == 0) recs[i * kRecW + 7] = make_float4(u[0], u[1], u[2], 0.f);
       }
     }
     if constexpr (MODE <= 1) {
@@ -695,7 +711,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
     // phase A': predictor located in FP32 relative to the stage-1 cell
     float u1[3] = {0.f, 0.f, 0.f};
     if (mine) {
-      const float4 r2 = recs[tid * kRecW + 2];
+      const float4 r2 = recs[tid * kRecW + 7];
       u1[0] = r2.x;
       u1[1] = r2.y;
       u1[2] = r2.z;
@@ -715,7 +731,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
         c2[d] = c;
       }
       write_record(recs + tid * kRecW, c2, t2, ok, P0, a.S, a.PS, Sx);
-      if (a.coef2) recs[tid * kRecW].w = __int_as_float(-1);  // second field: global path
+      if (a.coef2) recs[tid * kRecW + 5].x = __int_as_float(-1);  // second field: global path
     }
     __syncthreads();
     // phase B': second gathers
@@ -726,13 +742,13 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
       gather8<Tc, NC, false>(halo, a.PS, Sx, recs + (vi ? i : b4) * kRecW, g, cf2, sc2, q, kh,
-                             cq, ck0, ck1, u, dx, dy, dz);
-      if (vi && sub == 0) recs[i * kRecW + 2] = make_float4(u[0], u[1], u[2], 0.f);
+                             u, dx, dy, dz);
+      if (vi && sub == 0) recs[i * kRecW + 7] = make_float4(u[0], u[1], u[2], 0.f);
     }
     __syncthreads();
     // phase C: FP64 position update, one thread per particle
     if (mine) {
-      const float4 r2 = recs[tid * kRecW + 2];
+      const float4 r2 = recs[tid * kRecW + 7];
       const float u2[3] = {r2.x, r2.y, r2.z};
       const double half_dt = a.dt * 0.5;
 #pragma unroll
@@ -825,15 +841,24 @@ __device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsign
   const int64_t cs = rx * m1 * m2;
   const Tc* coef = static_cast<const Tc*>(a.coef);
   const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
-  const int items = NC * nrows * qx;
   Tc* rawt = reinterpret_cast<Tc*>(raw);
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int q = it % qx;
-    const int rr = it / qx;
-    const int c = rr / nrows, r = rr - c * nrows;
-    const int lz = r / Sy, ly = r - lz * Sy;
-    cp_async16(rawt + (int64_t)(c * nrows + r) * (qx * V) + q * V,
-               base + c * cs + ((int64_t)lz * m1 + ly) * rx + q * V);
+  // thread -> (vector q of a row, row slot); rows advance by blockDim/4
+  const int q = threadIdx.x & 3, RS = blockDim.x >> 2;
+  if (q < qx) {
+    int ly = (threadIdx.x >> 2) % Sy, lz = (threadIdx.x >> 2) / Sy;
+    const int dly = RS % Sy, dlz = RS / Sy;
+    for (int r = threadIdx.x >> 2; r < nrows; r += RS) {
+      const Tc* src = base + ((int64_t)lz * m1 + ly) * rx + q * V;
+      Tc* dst = rawt + (int64_t)r * (qx * V) + q * V;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) cp_async16(dst + (int64_t)c * nrows * qx * V, src + c * cs);
+      ly += dly;
+      lz += dlz;
+      if (ly >= Sy) {
+        ly -= Sy;
+        ++lz;
+      }
+    }
   }
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   const int m = min(kRecords, end - beg);
@@ -856,9 +881,15 @@ __device__ __forceinline__ void transpose_brick(const StagedArgs& a, const int P
   const int nrows = Sy * Sz;
   const Tc* rawt = reinterpret_cast<const Tc*>(raw);
   const int64_t m1 = g.m[1], m2 = g.m[2];
-  for (int it = threadIdx.x; it < nrows * qx; it += blockDim.x) {
-    const int q = it % qx, r = it / qx;
-    const int lz = r / Sy, ly = r - lz * Sy;
+  const int q = threadIdx.x & 3, RS = blockDim.x >> 2;
+  if (q >= qx) return;
+  int ly = (threadIdx.x >> 2) % Sy, lz = (threadIdx.x >> 2) / Sy;
+  const int dly = RS % Sy, dlz = RS / Sy;
+  for (int r = threadIdx.x >> 2; r < nrows; r += RS, ly += dly, lz += dlz) {
+    if (ly >= Sy) {
+      ly -= Sy;
+      ++lz;
+    }
     float v[NC][V];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -985,7 +1016,7 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
         }
         const int64_t grid = std::min<int64_t>(a.b.nbins,
                                                (int64_t)sm_count() * tuning().brick_ctas_per_sm);
-        pk<<<(unsigned)grid, kRecords, sm, st>>>(a);
+        pk<<<(unsigned)grid, kThreads, sm, st>>>(a);
         return check_launch("track_bricks");
       }
     }
@@ -998,7 +1029,7 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
     if (rc) return rc;
   }
   if (a.b.nbins > 0x7fffffff) return fail(PS_ERR_UNSUPPORTED, "too many bins");
-  kern<<<(unsigned)a.b.nbins, kRecords, smem, st>>>(a);
+  kern<<<(unsigned)a.b.nbins, kThreads, smem, st>>>(a);
   return check_launch("interp_staged");
 }
 
