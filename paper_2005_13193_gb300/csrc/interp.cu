@@ -483,58 +483,51 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
   __syncthreads();
 }
 
-// Particle records in shared memory (one per particle of the current round),
-// written by one thread per particle and read by the particle's 8 gather
-// lanes:
-//   rec[0]      = b_i(t_x), i = 0..3
-//   rec[1 + k]  = b_j(t_y) b_k(t_z), j = 0..3   (k = 0..3)
-//   rec[5]      = (origin, cell_x, cell_y, cell_z)  int bits; origin = halo
-//                 index of the stencil's first point, -1 = not in the halo
-//   rec[6]      = (t_x, t_y, t_z, ok)
-//   rec[7]      = (u, v, w, -) result of the last gather
+// Particle records in shared memory, one entry per particle of the current
+// round (kRecords), stored field-major so that neither the per-axis writers
+// nor the 8-lane readers conflict on banks:
+//   b[d][i]    float4  b_0..3(t_d) of particle i along axis d
+//   db[d][i]   float4  b'_0..3(t_d)   (gradient mode)
+//   loc[d][i]  int     brick-local stencil start along d, -1 = outside halo
+//   cell[d][i] int     global cell along d, -1 = position not finite
+//   u[i]       float4  (u, v, w, ok) result of the last gather
 constexpr int kRecords = 128;  // particles per round
-constexpr int kRecW = 8;       // float4 per record
 constexpr int kThreads = 256;  // threads per brick CTA
 
-// Cubic coefficients (t^3, t^2, t, 1) of basis function i; i is a lane
-// constant (used for the derivative weights of the gradient).
-__device__ __forceinline__ float4 basis_coeffs(int i) {
-  const float s = 1.f / 6.f;
-  return i == 0 ? make_float4(-s, 0.5f, -0.5f, s)
-       : i == 1 ? make_float4(0.5f, -1.f, 0.f, 4.f * s)
-       : i == 2 ? make_float4(-0.5f, 0.5f, 0.5f, s)
-                : make_float4(s, 0.f, 0.f, 0.f);
-}
-__device__ __forceinline__ float horner3(float4 c, float t) {
-  return fmaf(fmaf(fmaf(c.x, t, c.y), t, c.z), t, c.w);
-}
-__device__ __forceinline__ float dhorner3(float4 c, float t) {
-  return fmaf(fmaf(3.f * c.x, t, 2.f * c.y), t, c.z);
+struct Recs {
+  float4* f;  // b[3], db[3], u: 7 * kRecords float4
+  int* ip;    // loc[3], cell[3]:  6 * kRecords int
+  __device__ __forceinline__ float4* b(int d) const { return f + d * kRecords; }
+  __device__ __forceinline__ float4* db(int d) const { return f + (3 + d) * kRecords; }
+  __device__ __forceinline__ float4* u() const { return f + 6 * kRecords; }
+  __device__ __forceinline__ int* loc(int d) const { return ip + d * kRecords; }
+  __device__ __forceinline__ int* cell(int d) const { return ip + (3 + d) * kRecords; }
+};
+constexpr size_t kRecBytes = (size_t)kRecords * (7 * sizeof(float4) + 6 * sizeof(int));
+
+__device__ __forceinline__ Recs carve_recs(void* base) {
+  Recs r;
+  r.f = static_cast<float4*>(base);
+  r.ip = reinterpret_cast<int*>(r.f + 7 * kRecords);
+  return r;
 }
 
-// Phases A and A': one thread per particle writes its record.
-__device__ __forceinline__ void write_record(float4* rec, const int cell[3], const float t[3],
-                                             bool ok, const int P0[3], const int S[3], int PS,
-                                             int Sx) {
-  int l[3];
-  bool inh = true;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    l[d] = cell[d] - P0[d];
-    inh &= (unsigned)l[d] <= (unsigned)(S[d] - 4);
+// One (particle, axis) task of phases A / A': basis along the axis and the
+// brick-local index of the stencil start.
+template <bool GRAD>
+__device__ __forceinline__ void write_axis(const Recs& R, int i, int d, int cell, float t,
+                                           bool ok, int P0, int S) {
+  float b[4];
+  bspline<float>(t, b);
+  R.b(d)[i] = make_float4(b[0], b[1], b[2], b[3]);
+  if (GRAD) {
+    float db[4];
+    dbspline<float>(t, db);
+    R.db(d)[i] = make_float4(db[0], db[1], db[2], db[3]);
   }
-  const int origin = inh ? l[2] * PS + l[1] * Sx + l[0] : -1;
-  float bx[4], by[4], bz[4];
-  bspline<float>(t[0], bx);
-  bspline<float>(t[1], by);
-  bspline<float>(t[2], bz);
-  rec[0] = make_float4(bx[0], bx[1], bx[2], bx[3]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    rec[1 + k] = make_float4(by[0] * bz[k], by[1] * bz[k], by[2] * bz[k], by[3] * bz[k]);
-  rec[5] = make_float4(__int_as_float(origin), __int_as_float(cell[0]), __int_as_float(cell[1]),
-                       __int_as_float(cell[2]));
-  rec[6] = make_float4(t[0], t[1], t[2], __int_as_float(ok ? 1 : 0));
+  const int l = cell - P0;
+  R.loc(d)[i] = (unsigned)l <= (unsigned)(S - 4) ? l : -1;
+  R.cell(d)[i] = ok ? cell : -1;
 }
 
 __device__ __forceinline__ float f4get(const float4 v, int j) {
@@ -545,52 +538,44 @@ __device__ __forceinline__ float f4get(const float4 v, int j) {
 // x = a_x + q and the z rows k = kh, kh + 2, all four y rows; the partial
 // sums meet in a 3-level butterfly.  Shared-memory reads of one particle
 // (one 8-lane phase of a 128-bit load) are conflict-free because rows k and
-// k+2 are PS = 4 (mod 8) float4 apart.
+// k+2 are PS = 4 (mod 8) float4 apart.  Returns ok (all axes finite).
 template <typename Tc, int NC, bool GRAD>
-__device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS, int Sx,
-                                        const float4* rec, const GridArgs& g,
+__device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS, int Sx,
+                                        const Recs& R, int i, const GridArgs& g,
                                         const Tc* __restrict__ coef,
                                         const float* __restrict__ scale, int q, int kh,
                                         float out[NC], float dx[NC], float dy[NC],
                                         float dz[NC]) {
-  const float bxq = reinterpret_cast<const float*>(rec)[q];
-  const float4 w0 = rec[1 + kh], w1 = rec[3 + kh];
-  const float4 r5 = rec[5];
-  const int origin = __float_as_int(r5.x);
-  // gradient weights from the fractions (only when asked)
-  float by[4], dby[4], bz[2], dbz[2];
+  const float bxq = reinterpret_cast<const float*>(R.b(0))[4 * i + q];
+  const float4 by = R.b(1)[i], bz4 = R.b(2)[i];
+  const float bz[2] = {kh ? bz4.y : bz4.x, kh ? bz4.w : bz4.z};
+  const int lx = R.loc(0)[i], ly = R.loc(1)[i], lz = R.loc(2)[i];
+  const int cx = R.cell(0)[i], cy = R.cell(1)[i], cz = R.cell(2)[i];
+  const bool ok = (cx | cy | cz) >= 0;
+  float4 dby = make_float4(0.f, 0.f, 0.f, 0.f);
+  float dbz[2] = {0.f, 0.f};
   if (GRAD) {
-    const float4 r6 = rec[6];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float4 cj = basis_coeffs(j);
-      by[j] = horner3(cj, r6.y);
-      dby[j] = dhorner3(cj, r6.y);
-    }
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const float4 ck = basis_coeffs(kh + 2 * kk);
-      bz[kk] = horner3(ck, r6.z);
-      dbz[kk] = dhorner3(ck, r6.z);
-    }
+    dby = R.db(1)[i];
+    const float4 d4 = R.db(2)[i];
+    dbz[0] = kh ? d4.y : d4.x;
+    dbz[1] = kh ? d4.w : d4.z;
   }
   float acc[NC], accy[NC], accz[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
-  if (origin >= 0) {
-    const float4* hp = halo + origin + kh * PS + q;
+  if ((lx | ly | lz) >= 0) {
+    const float4* hp = halo + (lz + kh) * PS + ly * Sx + lx + q;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
-      const float4 wr = kk ? w1 : w0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float4 v = hp[2 * kk * PS + j * Sx];
         const float vv[3] = {v.x, v.y, v.z};
-        const float w = f4get(wr, j);
+        const float w = f4get(by, j) * bz[kk];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
         if (GRAD) {
-          const float wy = dby[j] * bz[kk], wz = by[j] * dbz[kk];
+          const float wy = f4get(dby, j) * bz[kk], wz = f4get(by, j) * dbz[kk];
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             accy[c] = fmaf(wy, vv[c], accy[c]);
@@ -600,20 +585,19 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
       }
     }
   } else {
-    const int ax = __float_as_int(r5.y), ay = __float_as_int(r5.z), az = __float_as_int(r5.w);
+    const int ax = max(cx, 0), ay = max(cy, 0), az = max(cz, 0);
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
-      const float4 wr = kk ? w1 : w0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float w = f4get(wr, j);
+        const float w = f4get(by, j) * bz[kk];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const float v = load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j, ax + q);
           acc[c] = fmaf(w, v, acc[c]);
           if (GRAD) {
-            accy[c] = fmaf(dby[j] * bz[kk], v, accy[c]);
-            accz[c] = fmaf(by[j] * dbz[kk], v, accz[c]);
+            accy[c] = fmaf(f4get(dby, j) * bz[kk], v, accy[c]);
+            accz[c] = fmaf(f4get(by, j) * dbz[kk], v, accz[c]);
           }
         }
       }
@@ -622,7 +606,7 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
 #pragma unroll
   for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
   if (GRAD) {
-    const float dbxq = dhorner3(basis_coeffs(q), rec[6].x);
+    const float dbxq = reinterpret_cast<const float*>(R.db(0))[4 * i + q];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       dx[c] = group_sum<8>(dbxq * acc[c]) * g.inv_hf[0];
@@ -630,20 +614,28 @@ __device__ __forceinline__ void gather8(const float4* __restrict__ halo, int PS,
       dz[c] = group_sum<8>(bxq * accz[c]) * g.inv_hf[2];
     }
   }
+  return ok;
 }
 
 template <typename Tc, int NC>
 __device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsigned char* raw,
                                             double* pbuf);
 
-// Particles [beg, end) of one brick whose halo is in shared memory (phases
-// A, B, A', B', C described above).  pbuf: optional shared copy of the first
-// round's positions ([3][kRecords]).  raw_next: if set, the copies of brick
-// next_bin are issued as soon as phase A has consumed pbuf.
+// Particles [beg, end) of one brick whose halo is in shared memory, in rounds
+// of kRecords:
+//   A  one thread per (particle, axis): locate (exact FP64 index arithmetic),
+//      basis along the axis, brick-local index;
+//   B  8 lanes per particle: gather and sum (writes the result or u1);
+//   A' (Heun) one thread per (particle, axis): predictor cell in FP32;
+//   B' second gather (u2);
+//   C  one thread per (particle, axis): FP64 position update and stores.
+// pbuf: optional shared copy of the first round's positions ([3][kRecords]).
+// raw_next: if set, the copies of brick next_bin are issued as soon as phase
+// A has consumed pbuf.
 template <typename Tc, int NC, int MODE>
 __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int end,
                                               const int P0[3], const float4* halo,
-                                              float4* recs, double* pbuf,
+                                              const Recs& R, double* pbuf,
                                               unsigned char* raw_next, int next_bin) {
   constexpr bool GRAD = MODE == 1;
   const GridArgs& g = a.g;
@@ -654,24 +646,31 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   const int Sx = a.S[0];
   const int64_t np = a.np;
   const float nanf_ = __int_as_float(0x7fc00000);
+  constexpr int TPT = (3 * kRecords + kThreads - 1) / kThreads;  // tasks per thread
 
   for (int cb = beg; cb < end; cb += kRecords) {
     const int m = min(kRecords, end - cb);
-    // phase A: one thread per particle
-    const bool mine = tid < m;
-    int64_t p = 0;
-    double x[3] = {0.0, 0.0, 0.0};
-    int cell[3] = {0, 0, 0};
-    float t[3] = {0.f, 0.f, 0.f};
-    bool ok = true;
-    if (mine) {
-      p = a.perm ? a.perm[cb + tid] : (int64_t)(cb + tid);
+    // phase A: tasks (particle i, axis d), task = d * m + i
+    int ti[TPT], td[TPT], tcell[TPT];
+    float tt[TPT];
+    double tx[TPT];
+    int64_t tp[TPT];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        x[d] = (pbuf && cb == beg) ? pbuf[d * kRecords + tid] : a.pos_in[d * np + p];
-        ok &= locate(x[d], g.inv_h[d], g.n[d], cell[d], t[d]);
+    for (int k = 0; k < TPT; ++k) {
+      const int task = tid + k * kThreads;
+      td[k] = task < 3 * m ? task / m : -1;
+      ti[k] = task - max(td[k], 0) * m;
+      tcell[k] = 0;
+      tt[k] = 0.f;
+      tx[k] = 0.0;
+      tp[k] = 0;
+      if (td[k] >= 0) {
+        const int i = ti[k], d = td[k];
+        tp[k] = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
+        tx[k] = (pbuf && cb == beg) ? pbuf[d * kRecords + i] : a.pos_in[d * np + tp[k]];
+        const bool ok = locate(tx[k], g.inv_h[d], g.n[d], tcell[k], tt[k]);
+        write_axis<GRAD>(R, i, d, tcell[k], tt[k], ok, sel3(P0, d), a.S[d]);
       }
-      write_record(recs + tid * kRecW, cell, t, ok, P0, a.S, a.PS, Sx);
     }
     __syncthreads();
     if (raw_next && cb == beg) issue_brick<Tc, NC>(a, next_bin, raw_next, pbuf);
@@ -681,12 +680,11 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = b4 + (lane >> 3);
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
-      gather8<Tc, NC, GRAD>(halo, a.PS, Sx, recs + (vi ? i : b4) * kRecW, g, coef, a.scale, q,
-                            kh, u, dx, dy, dz);
+      const bool oki = gather8<Tc, NC, GRAD>(halo, a.PS, Sx, R, vi ? i : b4, g, coef, a.scale,
+                                             q, kh, u, dx, dy, dz);
       if (!vi) continue;
       if constexpr (MODE <= 1) {
         const int64_t pi = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
-        const bool oki = __float_as_int(recs[i * kRecW + 6].w) != 0;
 #pragma unroll
         for (int c = 0; c < NC; ++c)
           if (sub == c) a.vel[(int64_t)c * np + pi] = oki ? u[c] : nanf_;
@@ -698,40 +696,35 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
             if (sub == 5) a.grad[((int64_t)c * 3 + 2) * np + pi] = oki ? dz[c] : nanf_;
           }
         }
+        if (sub == 7 && !oki) flag_status(a.status, PS_DEV_NONFINITE_POS, pi);
       } else {
-        if (sub == 0) recs[i * kRecW + 7] = make_float4(u[0], u[1], u[2], 0.f);
+        if (sub == 0) R.u()[i] = make_float4(u[0], u[1], u[2], __int_as_float(oki ? 1 : 0));
       }
     }
-    if constexpr (MODE <= 1) {
-      if (mine && !ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
-      __syncthreads();
-      continue;
-    }
     __syncthreads();
+    if constexpr (MODE == 2) {
     // phase A': predictor located in FP32 relative to the stage-1 cell
-    float u1[3] = {0.f, 0.f, 0.f};
-    if (mine) {
-      const float4 r2 = recs[tid * kRecW + 7];
-      u1[0] = r2.x;
-      u1[1] = r2.y;
-      u1[2] = r2.z;
-      int c2[3];
-      float t2[3];
+    float tu1[TPT];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float tt = t[d] + (ok ? u1[d] * a.dtih[d] : 0.f);
-        float fl = floorf(tt);
+    for (int k = 0; k < TPT; ++k) {
+      tu1[k] = 0.f;
+      if (td[k] >= 0) {
+        const int i = ti[k], d = td[k];
+        const float4 r = R.u()[i];
+        const bool ok = __float_as_int(r.w) != 0;
+        tu1[k] = f4get(r, d);
+        float t2 = tt[k] + (ok ? tu1[k] * a.dtih[d] : 0.f);
+        float fl = floorf(t2);
         if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
-        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
-        int c = cell[d] + (int)fl;
+        t2 = fminf(fmaxf(t2 - fl, 0.f), 1.f);
+        int c = tcell[k] + (int)fl;
         if (c < 0 || c >= g.n[d]) {
           c %= g.n[d];
           if (c < 0) c += g.n[d];
         }
-        c2[d] = c;
+        write_axis<false>(R, i, d, c, t2, ok, sel3(P0, d), a.S[d]);
+        if (a.coef2) R.loc(d)[i] = -1;  // second field: global path
       }
-      write_record(recs + tid * kRecW, c2, t2, ok, P0, a.S, a.PS, Sx);
-      if (a.coef2) recs[tid * kRecW + 5].x = __int_as_float(-1);  // second field: global path
     }
     __syncthreads();
     // phase B': second gathers
@@ -741,26 +734,30 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = b4 + (lane >> 3);
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
-      gather8<Tc, NC, false>(halo, a.PS, Sx, recs + (vi ? i : b4) * kRecW, g, cf2, sc2, q, kh,
-                             u, dx, dy, dz);
-      if (vi && sub == 0) recs[i * kRecW + 7] = make_float4(u[0], u[1], u[2], 0.f);
+      const bool oki = gather8<Tc, NC, false>(halo, a.PS, Sx, R, vi ? i : b4, g, cf2, sc2, q,
+                                              kh, u, dx, dy, dz);
+      if (vi && sub == 0) R.u()[i] = make_float4(u[0], u[1], u[2], __int_as_float(oki ? 1 : 0));
     }
     __syncthreads();
-    // phase C: FP64 position update, one thread per particle
-    if (mine) {
-      const float4 r2 = recs[tid * kRecW + 7];
-      const float u2[3] = {r2.x, r2.y, r2.z};
-      const double half_dt = a.dt * 0.5;
+    // phase C: FP64 position update, one thread per (particle, axis)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        a.pos_out[d * np + p] =
-            ok ? fma(half_dt, (double)(u1[d] + u2[d]), x[d]) : __longlong_as_double(0x7ff8000000000000ll);
-        if (a.vel) a.vel[d * np + p] = ok ? u1[d] : nanf_;
+    for (int k = 0; k < TPT; ++k) {
+      if (td[k] >= 0) {
+        const int i = ti[k], d = td[k];
+        const float4 r = R.u()[i];
+        const bool ok = __float_as_int(r.w) != 0;
+        const int64_t pp = tp[k];
+        a.pos_out[d * np + pp] = ok ? fma(a.dt * 0.5, (double)(tu1[k] + f4get(r, d)), tx[k])
+                                    : __longlong_as_double(0x7ff8000000000000ll);
+        if (a.vel) a.vel[d * np + pp] = ok ? tu1[k] : nanf_;
+        if (d == 0) {
+          if (a.ids_out) a.ids_out[pp] = a.ids_in[pp];
+          if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, pp);
+        }
       }
-      if (a.ids_out) a.ids_out[p] = a.ids_in[p];
-      if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
     }
     __syncthreads();
+    }  // MODE == 2
   }
 }
 
@@ -778,12 +775,12 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(St
   const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
   const Tc* coef = static_cast<const Tc*>(a.coef);
   float4* halo = smem;
-  float4* recs = smem + a.S[2] * a.PS;
+  const Recs R = carve_recs(smem + a.S[2] * a.PS);
   if (a.vec)
     stage_halo_vec<Tc, NC>(a, coef, P0, halo);
   else
     stage_halo<Tc, NC>(a, coef, P0, halo);
-  process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, recs, nullptr, nullptr, 0);
+  process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
 }
 
 // ------------------------------------------------------ persistent form ----
@@ -923,8 +920,9 @@ template <typename Tc, int NC, int MODE>
 __global__ void __launch_bounds__(256, 3) track_bricks(StagedArgs a) {
   extern __shared__ float4 smem[];
   float4* halo = smem;
-  float4* recs = halo + a.S[2] * a.PS;
-  double* pbuf = reinterpret_cast<double*>(recs + kRecords * kRecW);
+  const Recs R = carve_recs(halo + a.S[2] * a.PS);
+  double* pbuf = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(halo + a.S[2] * a.PS) +
+                                           kRecBytes);
   unsigned char* raw = reinterpret_cast<unsigned char*>(pbuf + 3 * kRecords);
   int bin = next_busy(a, blockIdx.x);
   const int nb = (int)a.b.nbins;
@@ -939,7 +937,7 @@ __global__ void __launch_bounds__(256, 3) track_bricks(StagedArgs a) {
     __syncthreads();
     const int beg = a.offs[bin], end = a.offs[bin + 1];
     const int nxt = next_busy(a, bin + gridDim.x);
-    process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, recs, a.perm ? nullptr : pbuf,
+    process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, a.perm ? nullptr : pbuf,
                                 nxt < nb ? raw : nullptr, nxt);
     bin = nxt;
   }
@@ -992,7 +990,7 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   const int qx = (a->S[0] + V - 1) / (V > 0 ? V : 1);
   vec = vec && qx <= 4 && (a->b.nb[0] - 1) * a->b.B[0] + qx * V <= a->g.rx;
   a->vec = vec ? 1 : 0;
-  *smem = ((size_t)a->S[2] * a->PS + (size_t)kRecords * kRecW) * sizeof(float4);
+  *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + kRecBytes;
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
 }
@@ -1004,7 +1002,7 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
       constexpr int V = 16 / (int)sizeof(Tc);
       const int qx = (a.S[0] + V - 1) / V;
       const size_t raw = (size_t)NC * a.S[1] * a.S[2] * qx * V * sizeof(Tc);
-      const size_t sm = ((size_t)a.S[2] * a.PS + (size_t)kRecords * kRecW) * sizeof(float4) +
+      const size_t sm = (size_t)a.S[2] * a.PS * sizeof(float4) + kRecBytes +
                         3 * kRecords * sizeof(double) + raw;
       if (sm <= 227 * 1024) {
         auto pk = track_bricks<Tc, NC, MODE>;
