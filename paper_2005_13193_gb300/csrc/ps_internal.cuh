@@ -71,7 +71,7 @@ ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* o
 
 // Launch-shape choices an autotuner may change (ps_tune_set).
 struct Tuning {
-  int brick_kernel = 1;       // 0: one CTA per brick; 1: persistent, pipelined
+  int brick_kernel = 0;       // 0: one CTA per brick; 1: persistent, pipelined
   int brick_ctas_per_sm = 3;  // resident CTAs per SM of the persistent form
 };
 Tuning& tuning();
