@@ -109,7 +109,7 @@ extern "C" const char* ps_last_error(void) { return g_err; }
 extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
   if (!key) return fail(PS_ERR_INVALID_ARG, "key is NULL");
   if (!strcmp(key, "brick_kernel")) {
-    if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0 or 1");
+    if (value < 0 || value > 2) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0, 1 or 2");
     tuning().brick_kernel = (int)value;
     return PS_OK;
   }

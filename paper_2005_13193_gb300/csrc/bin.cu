@@ -256,3 +256,4 @@ extern "C" ps_status ps_bin_particles(const ps_grid* grid, const int32_t brick[3
   return bin_run(ga, ba, np, pos, bin_of, bin_offsets, perm, pos_sorted, nullptr, nullptr,
                  counts, rank, scan_tmp, status, as_stream(stream));
 }
+

@@ -364,7 +364,7 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
   const bool narrow = Sx <= 16;
   const int tx = narrow ? (threadIdx.x & 15) : (threadIdx.x & 31);
   const int ty = narrow ? (threadIdx.x >> 4) : (threadIdx.x >> 5);
-  const int RS = narrow ? 16 : 8;  // rows covered by the block per step
+  const int RS = narrow ? (int)(blockDim.x >> 4) : (int)(blockDim.x >> 5);  // rows per step
   const bool xact = tx < Sx;
   const int Px = wrap_row(P0[0] + tx, g.n[0]);
   const int64_t m0 = g.rx, m1 = g.m[1], m2 = g.m[2];
@@ -783,6 +783,203 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(St
   process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
 }
 
+// ------------------------------------------------- thread per particle ----
+// One thread carries a particle through every step: exact location, the 12
+// basis values, its 64 stencil points read from the staged halo (128-bit
+// loads; lanes of a warp hit random banks, the price of needing no records,
+// shuffles or further barriers), the Heun predictor and the FP64 update.
+
+template <int NC, bool GRAD>
+struct Sum1 {
+  float u[NC], gx[NC], gy[NC], gz[NC];
+};
+
+// 64-term sum of Eq. (spline) by one thread; `row(k, j)` returns the four
+// x-consecutive points of stencil row (j, k) as float4 (u, v, w, -).
+template <int NC, bool GRAD, typename RowFn>
+__device__ __forceinline__ void sum64(const float bx[4], const float by[4], const float bz[4],
+                                      const float dbx[4], const float dby[4], const float dbz[4],
+                                      RowFn row, Sum1<NC, GRAD>& r) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) r.u[c] = r.gx[c] = r.gy[c] = r.gz[c] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float4 v[4];
+      row(k, j, v);
+      const float w = by[j] * bz[k];
+      float wy = 0.f, wz = 0.f;
+      if (GRAD) {
+        wy = dby[j] * bz[k];
+        wz = by[j] * dbz[k];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float v0 = c == 0 ? v[0].x : (c == 1 ? v[0].y : v[0].z);
+        const float v1 = c == 0 ? v[1].x : (c == 1 ? v[1].y : v[1].z);
+        const float v2 = c == 0 ? v[2].x : (c == 1 ? v[2].y : v[2].z);
+        const float v3 = c == 0 ? v[3].x : (c == 1 ? v[3].y : v[3].z);
+        float sx = bx[0] * v0;
+        sx = fmaf(bx[1], v1, sx);
+        sx = fmaf(bx[2], v2, sx);
+        sx = fmaf(bx[3], v3, sx);
+        r.u[c] = fmaf(w, sx, r.u[c]);
+        if (GRAD) {
+          float dx = dbx[0] * v0;
+          dx = fmaf(dbx[1], v1, dx);
+          dx = fmaf(dbx[2], v2, dx);
+          dx = fmaf(dbx[3], v3, dx);
+          r.gx[c] = fmaf(w, dx, r.gx[c]);
+          r.gy[c] = fmaf(wy, sx, r.gy[c]);
+          r.gz[c] = fmaf(wz, sx, r.gz[c]);
+        }
+      }
+    }
+}
+
+template <typename Tc, int NC, bool GRAD>
+__device__ __forceinline__ void gather1(const StagedArgs& a, const Tc* __restrict__ coef,
+                                        const float* __restrict__ scale,
+                                        const float4* __restrict__ halo, const int P0[3],
+                                        const int cell[3], const float t[3],
+                                        Sum1<NC, GRAD>& r) {
+  const GridArgs& g = a.g;
+  float bx[4], by[4], bz[4], dbx[4], dby[4], dbz[4];
+  bspline<float>(t[0], bx);
+  bspline<float>(t[1], by);
+  bspline<float>(t[2], bz);
+  if (GRAD) {
+    dbspline<float>(t[0], dbx);
+    dbspline<float>(t[1], dby);
+    dbspline<float>(t[2], dbz);
+  }
+  const int lx = cell[0] - P0[0], ly = cell[1] - P0[1], lz = cell[2] - P0[2];
+  const bool inh = (unsigned)lx <= (unsigned)(a.S[0] - 4) &&
+                   (unsigned)ly <= (unsigned)(a.S[1] - 4) &&
+                   (unsigned)lz <= (unsigned)(a.S[2] - 4);
+  if (inh) {
+    const float4* base = halo + lz * a.PS + ly * a.S[0] + lx;
+    const int PS = a.PS, Sx = a.S[0];
+    sum64<NC, GRAD>(bx, by, bz, dbx, dby, dbz,
+                    [&](int k, int j, float4 v[4]) {
+                      const float4* rp = base + k * PS + j * Sx;
+                      v[0] = rp[0];
+                      v[1] = rp[1];
+                      v[2] = rp[2];
+                      v[3] = rp[3];
+                    },
+                    r);
+  } else {
+    sum64<NC, GRAD>(bx, by, bz, dbx, dby, dbz,
+                    [&](int k, int j, float4 v[4]) {
+#pragma unroll
+                      for (int i = 0; i < 4; ++i) {
+                        float vv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int c = 0; c < NC; ++c)
+                          vv[c] = load_coef<Tc>(coef, scale, g, c, cell[2] + k, cell[1] + j,
+                                                cell[0] + i);
+                        v[i] = make_float4(vv[0], vv[1], vv[2], 0.f);
+                      }
+                    },
+                    r);
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      r.gx[c] *= g.inv_hf[0];
+      r.gy[c] *= g.inv_hf[1];
+      r.gz[c] *= g.inv_hf[2];
+    }
+  }
+}
+
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(64) interp_thread(StagedArgs a) {
+  extern __shared__ float4 smem[];
+  constexpr bool GRAD = MODE == 1;
+  const int bin = blockIdx.x;
+  const int beg = a.offs[bin], end = a.offs[bin + 1];
+  if (beg >= end) return;
+  const int nbx = a.b.nb[0], nby = a.b.nb[1];
+  const int bzi = bin / (nbx * nby);
+  const int rem = bin - bzi * nbx * nby;
+  const int byi = rem / nbx, bxi = rem - byi * nbx;
+  const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  float4* halo = smem;
+  if (a.vec)
+    stage_halo_vec<Tc, NC>(a, coef, P0, halo);
+  else
+    stage_halo<Tc, NC>(a, coef, P0, halo);
+  const GridArgs& g = a.g;
+  const int64_t np = a.np;
+  const float nanf_ = __int_as_float(0x7fc00000);
+  for (int s = beg + threadIdx.x; s < end; s += blockDim.x) {
+    const int64_t p = a.perm ? a.perm[s] : (int64_t)s;
+    double x[3];
+    int cell[3];
+    float t[3];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      x[d] = a.pos_in[d * np + p];
+      ok &= locate(x[d], g.inv_h[d], g.n[d], cell[d], t[d]);
+    }
+    Sum1<NC, GRAD> r;
+    gather1<Tc, NC, GRAD>(a, coef, a.scale, halo, P0, cell, t, r);
+    if constexpr (MODE <= 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) a.vel[(int64_t)c * np + p] = ok ? r.u[c] : nanf_;
+      if (GRAD && a.grad) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          a.grad[((int64_t)c * 3 + 0) * np + p] = ok ? r.gx[c] : nanf_;
+          a.grad[((int64_t)c * 3 + 1) * np + p] = ok ? r.gy[c] : nanf_;
+          a.grad[((int64_t)c * 3 + 2) * np + p] = ok ? r.gz[c] : nanf_;
+        }
+      }
+      if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+    } else {
+      const float u1[3] = {r.u[0], r.u[1], r.u[2]};
+      int c2[3];
+      float t2[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float tt = t[d] + (ok ? u1[d] * a.dtih[d] : 0.f);
+        float fl = floorf(tt);
+        if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
+        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
+        int c = cell[d] + (int)fl;
+        if (c < 0 || c >= g.n[d]) {
+          c %= g.n[d];
+          if (c < 0) c += g.n[d];
+        }
+        c2[d] = c;
+      }
+      Sum1<NC, false> r2;
+      if (a.coef2) {
+        // second field: its coefficients are not staged
+        int far[3] = {P0[0] - 1000000, 0, 0};
+        gather1<Tc, NC, false>(a, static_cast<const Tc*>(a.coef2), a.scale2, halo, far, c2, t2,
+                               r2);
+      } else {
+        gather1<Tc, NC, false>(a, coef, a.scale, halo, P0, c2, t2, r2);
+      }
+      const double half_dt = a.dt * 0.5;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        a.pos_out[d * np + p] = ok ? fma(half_dt, (double)(u1[d] + r2.u[d]), x[d])
+                                   : __longlong_as_double(0x7ff8000000000000ll);
+        if (a.vel) a.vel[d * np + p] = ok ? u1[d] : nanf_;
+      }
+      if (a.ids_out) a.ids_out[p] = a.ids_in[p];
+      if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+    }
+  }
+}
+
 // ------------------------------------------------------ persistent form ----
 // Each CTA walks bricks b = blockIdx.x, blockIdx.x + gridDim.x, ...  While it
 // processes the particles of one brick, the halo rows of its next non-empty
@@ -1018,6 +1215,18 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
         return check_launch("track_bricks");
       }
     }
+  }
+  if (tuning().brick_kernel == 2) {
+    auto tk = interp_thread<Tc, NC, MODE>;
+    const size_t hs = (size_t)a.S[2] * a.PS * sizeof(float4);
+    if (hs > 48 * 1024) {
+      ps_status rc = check_cuda(
+          cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs),
+          "thread-kernel smem attribute");
+      if (rc) return rc;
+    }
+    tk<<<(unsigned)a.b.nbins, 64, hs, st>>>(a);
+    return check_launch("interp_thread");
   }
   auto kern = interp_staged<Tc, NC, MODE>;
   if (smem > 48 * 1024) {

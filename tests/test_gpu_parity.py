@@ -134,6 +134,14 @@ def test_binning_empty_and_single():
 
 # ----------------------------------------------------------------- interp ----
 
+@pytest.fixture
+def brick_kernel():
+    old = ps.ps_tune_get("brick_kernel")
+    yield
+    ps.ps_tune_set("brick_kernel", old)
+
+
+
 def _case(n, np_, seed, L=(TWO_PI,) * 3, ncomp=3, spread=1.0):
     field = synth.random_field(n, ncomp=ncomp, seed=seed).astype(np.float32)
     pos = synth.uniform_particles(np_, seed=seed + 1)
@@ -153,8 +161,10 @@ def test_interp_direct(n, np_):
     assert rel_err(vel, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("kernel", [0, 2])
 @pytest.mark.parametrize("brick", [(8, 8, 8), (4, 4, 4), (16, 8, 4), (5, 7, 3), (1, 1, 1)])
-def test_interp_staged_sorted_and_perm(brick):
+def test_interp_staged_sorted_and_perm(brick, kernel, brick_kernel):
+    ps.ps_tune_set("brick_kernel", kernel)
     n = (40, 36, 33)
     field, pos, cref = _case(n, 20000, seed=21, spread=2.0)
     ref = oracle.interp(cref, pos)
@@ -171,18 +181,11 @@ def test_interp_staged_sorted_and_perm(brick):
     assert rel_err(vel_s, ref[:, perm]) <= 1e-5
 
 
-@pytest.fixture
-def brick_kernel():
-    old = ps.ps_tune_get("brick_kernel")
-    yield
-    ps.ps_tune_set("brick_kernel", old)
-
-
 def abs_err(gpu, ref):
     return np.abs(np.asarray(gpu, dtype=np.float64) - np.asarray(ref)).max()
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_brick_kernels_on_tiling_grids(kernel, dtype, brick_kernel):
     # Grids divisible by the brick: 16-byte halo rows, both brick kernels.
