@@ -144,6 +144,29 @@ ps_status ps_bin_particles(const ps_grid* grid, const int32_t brick[3],
                            int32_t* status, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* ps_bin_particles without a workspace (no counterpart in the paper).      */
+/* For callers that cannot allocate device memory or pass a workspace when  */
+/* they bin: code under a device-memory budget owned by another allocator,  */
+/* time-critical steps that must not add allocation latency, or plain C     */
+/* hosts without an allocator of their own.  Same arguments, results and    */
+/* errors as ps_bin_particles minus (ws, ws_bytes).  Nothing is allocated:  */
+/* the counting-sort scratch lives in a fixed 32 MiB device array that      */
+/* every GPU loading this library holds until the process exits; requests   */
+/* needing more ((nbins + 1) + (nbins / 2048 + 2) + np int32 values, each   */
+/* part rounded up to 256 bytes, above 32 MiB) fail with                    */
+/* PS_ERR_INVALID_ARG before anything is enqueued.  The first call on a     */
+/* device resolves the array's device address (cudaGetSymbolAddress) with   */
+/* that device current: make it before any stream capture.  All calls share */
+/* the one array (counters are cleared by each call), so calls that overlap */
+/* on the GPU -- on different streams, or concurrent host threads -- race.  */
+/* ------------------------------------------------------------------------ */
+ps_status ps_bin_particles_noalloc(const ps_grid* grid, const int32_t brick[3],
+                                   int64_t np, const double* pos,
+                                   int32_t* bin_of, int32_t* bin_offsets,
+                                   int64_t* perm, double* pos_sorted,
+                                   int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Operations 2 and 3 (Sec. 2.2, Eq. (spline)):                             */
 /*   u_c(x) = sum_{i,j,k=0..3} b_i(t_x) b_j(t_y) b_k(t_z)                   */
 /*            C_c[a_z+k][a_y+j][a_x+i]                                      */

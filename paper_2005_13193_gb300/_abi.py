@@ -47,6 +47,7 @@ SIGNATURES = {
     "ps_spline_coeffs": (_I, [_GP, _I, _I, _P, _I, _P, _P, _P, _SZ, _P]),
     "ps_bin_workspace_size": (_SZ, [_GP, _P, _I64]),
     "ps_bin_particles": (_I, [_GP, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P, _P]),
+    "ps_bin_particles_noalloc": (_I, [_GP, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "ps_interp": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ps_interp_backward": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P, _P]),
     "ps_rk2_workspace_size": (_SZ, [_GP, _P, _I64]),

@@ -6,6 +6,8 @@
 //          counter returns the particle's rank inside its bin.
 // scan:    exclusive prefix sum of the counters -> bin_offsets (3 phases).
 // scatter: slot = bin_offsets[bin] + rank; writes perm / sorted copies.
+#include <mutex>
+
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -257,3 +259,76 @@ extern "C" ps_status ps_bin_particles(const ps_grid* grid, const int32_t brick[3
                  counts, rank, scan_tmp, status, as_stream(stream));
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free binning.  Some callers cannot call cudaMalloc (or hand the
+// library a workspace) at the point where they bin particles: code running
+// under a strict device-memory budget owned by another allocator, callers
+// that must not add allocation latency inside a time-critical step, or hosts
+// that reach this library through a plain C interface with no allocator of
+// their own.  For them the scratch of the counting sort lives in a file-scope
+// device array of fixed size that every GPU loading this library holds until
+// the process exits.
+
+namespace {
+constexpr int64_t kNoAllocScratchInts = (int64_t)1 << 23;  // 32 MiB of int32
+__device__ __align__(256) int32_t g_bin_scratch[kNoAllocScratchInts];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+int32_t* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_bin_scratch on the current device.  In host code the
+// array's name is only a stand-in, so the address is resolved once per device
+// (with that device current) through cudaGetSymbolAddress.
+ps_status bin_scratch_for_current_device(int32_t** out) {
+  int dev = 0;
+  ps_status rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= kMaxDevices) return fail(PS_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    rc = check_cuda(cudaGetSymbolAddress(&p, g_bin_scratch), "cudaGetSymbolAddress(bin scratch)");
+    if (rc) return rc;
+    g_scratch_ptr[dev] = static_cast<int32_t*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return PS_OK;
+}
+}  // namespace
+
+extern "C" ps_status ps_bin_particles_noalloc(const ps_grid* grid, const int32_t brick[3],
+                                              int64_t np, const double* pos, int32_t* bin_of,
+                                              int32_t* bin_offsets, int64_t* perm,
+                                              double* pos_sorted, int32_t* status,
+                                              void* stream) {
+  ps_status rc = validate_grid(grid);
+  if (rc) return rc;
+  BrickArgs ba;
+  if ((rc = make_brick_args(grid, brick, &ba))) return rc;
+  if (np < 0 || np >= ((int64_t)1 << 31)) return fail(PS_ERR_INVALID_ARG, "np out of range");
+  if (!bin_offsets || (np > 0 && (!pos || !bin_of)))
+    return fail(PS_ERR_INVALID_ARG, "pos, bin_of and bin_offsets are required");
+  // same carve as the workspace form: counts, tile sums, rank
+  Carver sizing(nullptr);
+  sizing.take<int32_t>(ba.nbins + 1);
+  sizing.take<int32_t>(scan_tmp_elems(ba.nbins) + 1);
+  sizing.take<int32_t>(np);
+  const size_t cap = (size_t)kNoAllocScratchInts * sizeof(int32_t);
+  if (sizing.used > cap)
+    return fail(PS_ERR_INVALID_ARG,
+                "allocation-free binning needs %zu scratch bytes (bins %lld, particles %lld); "
+                "its fixed scratch holds %zu bytes",
+                sizing.used, (long long)ba.nbins, (long long)np, cap);
+  int32_t* scratch = nullptr;
+  if ((rc = bin_scratch_for_current_device(&scratch))) return rc;
+  Carver c(scratch);
+  int32_t* counts = c.take<int32_t>(ba.nbins + 1);
+  int32_t* scan_tmp = c.take<int32_t>(scan_tmp_elems(ba.nbins) + 1);
+  int32_t* rank = c.take<int32_t>(np);
+  GridArgs ga = make_grid_args(grid);
+  // bin_run clears the counters before counting, so the contents left by the
+  // previous call do not matter
+  return bin_run(ga, ba, np, pos, bin_of, bin_offsets, perm, pos_sorted, nullptr, nullptr,
+                 counts, rank, scan_tmp, status, as_stream(stream));
+}
