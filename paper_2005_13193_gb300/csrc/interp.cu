@@ -325,7 +325,8 @@ struct StagedArgs {
   BrickArgs b;
   int E;        // extra halo cells on each side
   int S[3];     // staged extent per axis: B + 3 + 2E
-  int PS;       // plane stride in float4 units: >= S[0]*S[1], = 4 (mod 8)
+  int SX;       // row stride in float4 units (= S[0])
+  int PS;       // plane stride in float4 units: >= SX*S[1], = 4 (mod 8)
   int vec;      // 1: halo rows are whole 16-byte vectors inside the array
   const void* coef;
   const float* scale;
@@ -381,7 +382,7 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
       const int Py = wrap_row(P0[1] + ly, g.n[1]);
       const int Pz = wrap_row(P0[2] + lz, g.n[2]);
       const int64_t row = (int64_t)Pz * m1 + Py;
-      dst[u] = lz * a.PS + ly * Sx + tx;
+      dst[u] = lz * a.PS + ly * a.SX + tx;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         float x = 0.f;
@@ -449,6 +450,39 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
   const int64_t rx = g.rx, m1 = g.m[1], m2 = g.m[2];
   const int64_t cs = rx * m1 * m2;
   const int nrows = Sy * Sz;
+  if (V == 4 && qx == 3 && (Sx & 1)) {
+    // Items in groups of 24 = 8 rows x 3 vectors, ordered so that the eight
+    // lanes of each 128-bit store phase write (rows r..r+3, vectors 0-1) or
+    // (rows r..r+7, vector 2): with an odd row stride these hit eight distinct
+    // 16-byte bank groups.
+    const Tc* b0 = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
+    const int nitems = (nrows + 7) / 8 * 24;
+    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+      const int grp = it / 24, l = it - grp * 24;
+      const int rr = l < 16 ? (l >> 1) : l - 16;
+      const int q = l < 16 ? (l & 1) : 2;
+      const int r = grp * 8 + rr;
+      if (r >= nrows) continue;
+      const int lz = r / Sy, ly = r - lz * Sy;
+      const int64_t roff = ((int64_t)lz * m1 + ly) * rx + q * 4;
+      float v[NC][4];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float sc = 1.f;
+        if (IsQuant<Tc>::value)
+          sc = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
+        Vec16<Tc>::load(b0 + c * cs + roff, sc, v[c]);
+      }
+      const int h0 = lz * a.PS + ly * a.SX + q * 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (q * 4 + i < Sx)
+          halo[h0 + i] = make_float4(v[0][i], NC > 1 ? v[NC > 1 ? 1 : 0][i] : 0.f,
+                                     NC > 2 ? v[NC > 2 ? 2 : 0][i] : 0.f, 0.f);
+    }
+    __syncthreads();
+    return;
+  }
   const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0] + qd * V;
   for (int r0 = rs; r0 < nrows; r0 += U * RS) {
     float v[U][NC][V];
@@ -459,7 +493,7 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
       const int r = r0 + u * RS;
       act[u] = qd < qx && r < nrows;
       const int lz = r / Sy, ly = r - lz * Sy;
-      h0[u] = lz * a.PS + ly * Sx + qd * V;
+      h0[u] = lz * a.PS + ly * a.SX + qd * V;
       const int64_t roff = ((int64_t)lz * m1 + ly) * rx;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -496,14 +530,16 @@ constexpr int kThreads = 256;  // threads per brick CTA
 
 struct Recs {
   float4* f;  // b[3], db[3], u: 7 * kRecords float4
-  int* ip;    // loc[3], cell[3]:  6 * kRecords int
+  int* ip;    // lw, cell[3]:     4 * kRecords int
   __device__ __forceinline__ float4* b(int d) const { return f + d * kRecords; }
   __device__ __forceinline__ float4* db(int d) const { return f + (3 + d) * kRecords; }
   __device__ __forceinline__ float4* u() const { return f + 6 * kRecords; }
-  __device__ __forceinline__ int* loc(int d) const { return ip + d * kRecords; }
-  __device__ __forceinline__ int* cell(int d) const { return ip + (3 + d) * kRecords; }
+  // byte d of lw[i]: brick-local stencil start along d, -1 outside the halo,
+  // -2 position not finite
+  __device__ __forceinline__ int* lw() const { return ip; }
+  __device__ __forceinline__ int* cell(int d) const { return ip + (1 + d) * kRecords; }
 };
-constexpr size_t kRecBytes = (size_t)kRecords * (7 * sizeof(float4) + 6 * sizeof(int));
+constexpr size_t kRecBytes = (size_t)kRecords * (7 * sizeof(float4) + 4 * sizeof(int));
 
 __device__ __forceinline__ Recs carve_recs(void* base) {
   Recs r;
@@ -513,21 +549,24 @@ __device__ __forceinline__ Recs carve_recs(void* base) {
 }
 
 // One (particle, axis) task of phases A / A': basis along the axis and the
-// brick-local index of the stencil start.
+// brick-local index of the stencil start.  The z basis is stored in the order
+// (b0, b2, b1, b3) so that a gather lane reads its pair (b_kh, b_kh+2) at once.
 template <bool GRAD>
 __device__ __forceinline__ void write_axis(const Recs& R, int i, int d, int cell, float t,
                                            bool ok, int P0, int S) {
   float b[4];
   bspline<float>(t, b);
-  R.b(d)[i] = make_float4(b[0], b[1], b[2], b[3]);
+  R.b(d)[i] = d == 2 ? make_float4(b[0], b[2], b[1], b[3]) : make_float4(b[0], b[1], b[2], b[3]);
   if (GRAD) {
     float db[4];
     dbspline<float>(t, db);
-    R.db(d)[i] = make_float4(db[0], db[1], db[2], db[3]);
+    R.db(d)[i] =
+        d == 2 ? make_float4(db[0], db[2], db[1], db[3]) : make_float4(db[0], db[1], db[2], db[3]);
   }
   const int l = cell - P0;
-  R.loc(d)[i] = (unsigned)l <= (unsigned)(S - 4) ? l : -1;
-  R.cell(d)[i] = ok ? cell : -1;
+  const int code = !ok ? -2 : ((unsigned)l <= (unsigned)(S - 4) ? l : -1);
+  reinterpret_cast<signed char*>(R.lw())[4 * i + d] = (signed char)code;
+  R.cell(d)[i] = cell;
 }
 
 __device__ __forceinline__ float f4get(const float4 v, int j) {
@@ -547,23 +586,26 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
                                         float out[NC], float dx[NC], float dy[NC],
                                         float dz[NC]) {
   const float bxq = reinterpret_cast<const float*>(R.b(0))[4 * i + q];
-  const float4 by = R.b(1)[i], bz4 = R.b(2)[i];
-  const float bz[2] = {kh ? bz4.y : bz4.x, kh ? bz4.w : bz4.z};
-  const int lx = R.loc(0)[i], ly = R.loc(1)[i], lz = R.loc(2)[i];
-  const int cx = R.cell(0)[i], cy = R.cell(1)[i], cz = R.cell(2)[i];
-  const bool ok = (cx | cy | cz) >= 0;
+  const float4 by = R.b(1)[i];
+  const float2 bzp = reinterpret_cast<const float2*>(R.b(2))[2 * i + kh];
+  const float bz[2] = {bzp.x, bzp.y};
+  const int w = R.lw()[i];
+  const bool ok = (__vcmpeq4(w, 0xfefefefe) & 0x00ffffff) == 0;
+  const bool inh = (w & 0x00808080) == 0;
   float4 dby = make_float4(0.f, 0.f, 0.f, 0.f);
   float dbz[2] = {0.f, 0.f};
   if (GRAD) {
     dby = R.db(1)[i];
-    const float4 d4 = R.db(2)[i];
-    dbz[0] = kh ? d4.y : d4.x;
-    dbz[1] = kh ? d4.w : d4.z;
+    const float2 d2 = reinterpret_cast<const float2*>(R.db(2))[2 * i + kh];
+    dbz[0] = d2.x;
+    dbz[1] = d2.y;
   }
   float acc[NC], accy[NC], accz[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
-  if ((lx | ly | lz) >= 0) {
+  if (inh) {
+    const int lx = (signed char)(w & 0xff), ly = (signed char)((w >> 8) & 0xff),
+              lz = (signed char)((w >> 16) & 0xff);
     const float4* hp = halo + (lz + kh) * PS + ly * Sx + lx + q;
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
@@ -585,7 +627,7 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
       }
     }
   } else {
-    const int ax = max(cx, 0), ay = max(cy, 0), az = max(cz, 0);
+    const int ax = max(R.cell(0)[i], 0), ay = max(R.cell(1)[i], 0), az = max(R.cell(2)[i], 0);
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
@@ -643,7 +685,6 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   const int tid = threadIdx.x, lane = tid & 31;
   const int q = lane & 3, kh = (lane >> 2) & 1, sub = lane & 7;
   const int warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int Sx = a.S[0];
   const int64_t np = a.np;
   const float nanf_ = __int_as_float(0x7fc00000);
   constexpr int TPT = (3 * kRecords + kThreads - 1) / kThreads;  // tasks per thread
@@ -680,7 +721,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = b4 + (lane >> 3);
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
-      const bool oki = gather8<Tc, NC, GRAD>(halo, a.PS, Sx, R, vi ? i : b4, g, coef, a.scale,
+      const bool oki = gather8<Tc, NC, GRAD>(halo, a.PS, a.SX, R, vi ? i : b4, g, coef, a.scale,
                                              q, kh, u, dx, dy, dz);
       if (!vi) continue;
       if constexpr (MODE <= 1) {
@@ -723,7 +764,8 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
           if (c < 0) c += g.n[d];
         }
         write_axis<false>(R, i, d, c, t2, ok, sel3(P0, d), a.S[d]);
-        if (a.coef2) R.loc(d)[i] = -1;  // second field: global path
+        if (a.coef2 && ok)  // second field: its coefficients are not staged
+          reinterpret_cast<signed char*>(R.lw())[4 * i + d] = (signed char)-1;
       }
     }
     __syncthreads();
@@ -734,7 +776,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = b4 + (lane >> 3);
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
-      const bool oki = gather8<Tc, NC, false>(halo, a.PS, Sx, R, vi ? i : b4, g, cf2, sc2, q,
+      const bool oki = gather8<Tc, NC, false>(halo, a.PS, a.SX, R, vi ? i : b4, g, cf2, sc2, q,
                                               kh, u, dx, dy, dz);
       if (vi && sub == 0) R.u()[i] = make_float4(u[0], u[1], u[2], __int_as_float(oki ? 1 : 0));
     }
@@ -859,8 +901,8 @@ __device__ __forceinline__ void gather1(const StagedArgs& a, const Tc* __restric
                    (unsigned)ly <= (unsigned)(a.S[1] - 4) &&
                    (unsigned)lz <= (unsigned)(a.S[2] - 4);
   if (inh) {
-    const float4* base = halo + lz * a.PS + ly * a.S[0] + lx;
-    const int PS = a.PS, Sx = a.S[0];
+    const float4* base = halo + lz * a.PS + ly * a.SX + lx;
+    const int PS = a.PS, Sx = a.SX;
     sum64<NC, GRAD>(bx, by, bz, dbx, dby, dbz,
                     [&](int k, int j, float4 v[4]) {
                       const float4* rp = base + k * PS + j * Sx;
@@ -1104,7 +1146,7 @@ __device__ __forceinline__ void transpose_brick(const StagedArgs& a, const int P
         }
       }
     }
-    const int h0 = lz * a.PS + ly * Sx + q * V;
+    const int h0 = lz * a.PS + ly * a.SX + q * V;
 #pragma unroll
     for (int i = 0; i < V; ++i)
       if (q * V + i < Sx)
@@ -1178,7 +1220,8 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   a->E = E;
   for (int d = 0; d < 3; ++d) a->S[d] = a->b.B[d] + 3 + 2 * E;
   if (a->S[0] > 32) return fail(PS_ERR_UNSUPPORTED, "brick x extent above 29 cells");
-  a->PS = plane_stride(a->S[0], a->S[1]);
+  a->SX = a->S[0];
+  a->PS = plane_stride(a->SX, a->S[1]);
   // vector staging needs E = 0, bricks tiling the grid, 16-byte-aligned halo
   // rows and the last row vector inside the row pitch
   const int V = coef_t == PS_F32 ? 4 : (coef_t == PS_BF16 || coef_t == PS_F16 ? 8 : 0);
