@@ -359,7 +359,7 @@ __device__ __forceinline__ int wrap_row(int P, int n) {
 // before storing them so that the loads overlap.
 template <typename Tc, int NC>
 __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __restrict__ coef,
-                                           const int P0[3], float4* halo) {
+                                           const int P0[3], float4* halo, bool sync = true) {
   const GridArgs& g = a.g;
   const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
   const bool narrow = Sx <= 16;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
         halo[dst[u]] = make_float4(v[u][0], NC > 1 ? v[u][NC > 1 ? 1 : 0] : 0.f,
                                    NC > 2 ? v[u][NC > 2 ? 2 : 0] : 0.f, 0.f);
   }
-  __syncthreads();
+  if (sync) __syncthreads();
 }
 
 // Vector staging.  With E = 0 and bricks that tile the grid, the halo of
@@ -439,7 +439,7 @@ template <> struct Vec16<__half> : Vec16Half<__half> {};
 
 template <typename Tc, int NC>
 __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __restrict__ coef,
-                                               const int P0[3], float4* halo) {
+                                               const int P0[3], float4* halo, bool sync = true) {
   constexpr int V = Vec16<Tc>::V;
   constexpr int U = 8 / V;               // rows in flight per thread
   const GridArgs& g = a.g;
@@ -480,7 +480,7 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
           halo[h0 + i] = make_float4(v[0][i], NC > 1 ? v[NC > 1 ? 1 : 0][i] : 0.f,
                                      NC > 2 ? v[NC > 2 ? 2 : 0][i] : 0.f, 0.f);
     }
-    __syncthreads();
+    if (sync) __syncthreads();
     return;
   }
   const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0] + qd * V;
@@ -514,7 +514,7 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
             halo[h0[u] + i] = make_float4(v[u][0][i], NC > 1 ? v[u][NC > 1 ? 1 : 0][i] : 0.f,
                                           NC > 2 ? v[u][NC > 2 ? 2 : 0][i] : 0.f, 0.f);
   }
-  __syncthreads();
+  if (sync) __syncthreads();
 }
 
 // Particle records in shared memory, one entry per particle of the current
@@ -818,10 +818,12 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(St
   const Tc* coef = static_cast<const Tc*>(a.coef);
   float4* halo = smem;
   const Recs R = carve_recs(smem + a.S[2] * a.PS);
+  // no barrier here: phase A of the first round does not read the halo, and
+  // the barrier that follows it also publishes the staged halo
   if (a.vec)
-    stage_halo_vec<Tc, NC>(a, coef, P0, halo);
+    stage_halo_vec<Tc, NC>(a, coef, P0, halo, false);
   else
-    stage_halo<Tc, NC>(a, coef, P0, halo);
+    stage_halo<Tc, NC>(a, coef, P0, halo, false);
   process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
 }
 
