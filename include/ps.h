@@ -236,6 +236,48 @@ ps_status ps_rk2_step(const ps_grid* grid, ps_dtype coef_t, const void* coef_n,
                       const int32_t brick[3], int rebin, int32_t* bin_offsets,
                       void* ws, size_t ws_bytes, int32_t* status, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Many fields at once (no counterpart in the paper: a way of running many  */
+/* of its problems together on one device).  A plan fixes the fields' grids */
+/* and particle counts; particles of all fields live in one concatenated    */
+/* [3][np_total] FP64 array, field f owning [base_f, base_{f+1})            */
+/* (ps_batch_particle_base).  ps_batch_run optionally solves every field's  */
+/* spline coefficients (solve = 1; ps_spline_coeffs per field), then takes  */
+/* nsteps Heun steps of every particle (frozen fields): each step is one    */
+/* bin sort over all particles (global bin = first bin of the field + bin   */
+/* in the field) and one brick-kernel launch over the bricks of all fields. */
+/* Particles end in bin order per field, as with ps_rk2_step(rebin=1); ids  */
+/* (optional, int64 [np_total]) and vel_out (optional, [3][np_total] = u at */
+/* the start of the last step) follow them.  use_graph = 1 captures the     */
+/* nsteps steps in a CUDA graph on the first run and replays it while the   */
+/* pointers, nsteps and dt stay the same (the capture uses a stream owned   */
+/* by the plan; the graph is launched on `stream`).  The plan holds host    */
+/* metadata, that stream and the graph; device scratch comes from ws        */
+/* (ps_batch_workspace_size).  tune_cache: optional text file whose line    */
+/* "brick <bx> <by> <bz>" overrides `brick` (written by the autotuner).     */
+/* Coefficients: PS_F32, PS_BF16 or PS_F16; the batch uses the              */
+/* one-CTA-per-brick kernel.                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct ps_plan ps_plan;
+typedef struct {
+  const void* field; /* [3][nz][ny][nx] F32; read when solve = 1 */
+  void* coef;        /* [3][nz+3][ny+3][rx] of coef_t */
+  float* scale;      /* [3][nz+3][ny+3] for BF16/F16, else NULL */
+} ps_batch_field;
+
+ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int64_t* nps,
+                        ps_dtype coef_t, const int32_t brick[3],
+                        const char* tune_cache, ps_plan** out);
+size_t ps_batch_workspace_size(const ps_plan* plan);
+int64_t ps_batch_num_particles(const ps_plan* plan);
+/* First particle of field `field` (field = nfields gives np_total). */
+int64_t ps_batch_particle_base(const ps_plan* plan, int field);
+ps_status ps_batch_run(ps_plan* plan, const ps_batch_field* fields, int solve,
+                       double* pos, int64_t* ids, float* vel_out, int nsteps,
+                       double dt, int use_graph, void* ws, size_t ws_bytes,
+                       int32_t* status, void* stream);
+void ps_plan_destroy(ps_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

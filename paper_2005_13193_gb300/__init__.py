@@ -414,5 +414,70 @@ class InterpFn(torch.autograd.Function):
         return g_pos, g_field, None
 
 
+class BatchPlan:
+    """Many periodic fields and their particle sets advanced together
+    (ps_batch_plan / ps_batch_run).  `grids` is a list of (n, L) or n tuples;
+    particles of all fields are one concatenated [3][np_total] array."""
+
+    def __init__(self, grids, nps, coef_dtype=torch.float32, brick=(8, 8, 8),
+                 tune_cache: Optional[str] = None):
+        gl = []
+        for g in grids:
+            n, L = (g if isinstance(g[0], (tuple, list)) else (g, DEFAULT_L))
+            gl.append(make_grid(n, L))
+        self.grids = [(tuple(g.n), tuple(g.L)) for g in gl]
+        self.nfields = len(gl)
+        arr = (PsGrid * self.nfields)(*gl)
+        nps_arr = (ctypes.c_int64 * self.nfields)(*[int(v) for v in nps])
+        self.coef_dtype = coef_dtype
+        self._plan = ctypes.c_void_p()
+        _check(_lib().ps_batch_plan(self.nfields, arr, ctypes.cast(nps_arr, ctypes.c_void_p),
+                                    _DT[coef_dtype], _brick_arr(brick),
+                                    tune_cache.encode() if tune_cache else None,
+                                    ctypes.byref(self._plan)))
+        self.np_total = int(_lib().ps_batch_num_particles(self._plan))
+        self.base = [int(_lib().ps_batch_particle_base(self._plan, f))
+                     for f in range(self.nfields + 1)]
+        self.ws_bytes = int(_lib().ps_batch_workspace_size(self._plan))
+        self._ws = None
+
+    def workspace(self, device="cuda") -> torch.Tensor:
+        if self._ws is None or self._ws.device != torch.device(device):
+            self._ws = workspace(self.ws_bytes, device)
+        return self._ws
+
+    def run(self, fields, pos: torch.Tensor, nsteps: int, dt: float, solve: bool = True,
+            ids: Optional[torch.Tensor] = None, vel: Optional[torch.Tensor] = None,
+            use_graph: bool = True, status: Optional[torch.Tensor] = None, stream=None):
+        """fields: list of (field tensor or None, SplineField) per field."""
+        assert len(fields) == self.nfields
+        _dev(pos, "pos", torch.float64, 3 * self.np_total)
+        _dev(ids, "ids", torch.int64, self.np_total)
+        _dev(vel, "vel", torch.float32, 3 * self.np_total)
+        _dev(status, "status", torch.int32, 4)
+        bf = (_abi.PsBatchField * self.nfields)()
+        for f, (fld, sf) in enumerate(fields):
+            if fld is not None:
+                _dev(fld, "field", torch.float32)
+            _check_coef_shape(sf.coef, self.grids[f][0])
+            bf[f].field = fld.data_ptr() if fld is not None else None
+            bf[f].coef = sf.coef.data_ptr()
+            bf[f].scale = sf.scale.data_ptr() if sf.scale is not None else None
+        ws = self.workspace(pos.device)
+        _check(_lib().ps_batch_run(self._plan, ctypes.cast(bf, ctypes.c_void_p), 1 if solve else 0,
+                                   _ptr(pos), _ptr(ids), _ptr(vel), int(nsteps), float(dt),
+                                   1 if use_graph else 0, _ptr(ws), self.ws_bytes, _ptr(status),
+                                   _stream(stream)))
+
+    def __del__(self):
+        plan = getattr(self, "_plan", None)
+        if plan is not None and plan.value:
+            try:
+                _lib().ps_plan_destroy(plan)
+            except Exception:
+                pass
+            self._plan = None
+
+
 def interp_autograd(pos: torch.Tensor, field: torch.Tensor, L=DEFAULT_L) -> torch.Tensor:
     return InterpFn.apply(pos, field, L)

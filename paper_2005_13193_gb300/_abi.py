@@ -27,6 +27,10 @@ class PsGrid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("L", ctypes.c_double * 3)]
 
 
+class PsBatchField(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("scale", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -50,6 +54,12 @@ SIGNATURES = {
     "ps_bin_particles_noalloc": (_I, [_GP, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "ps_interp": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ps_interp_backward": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P, _P]),
+    "ps_batch_plan": (_I, [_I, _GP, _P, _I, _P, ctypes.c_char_p, _P]),
+    "ps_batch_workspace_size": (_SZ, [_P]),
+    "ps_batch_num_particles": (_I64, [_P]),
+    "ps_batch_particle_base": (_I64, [_P, _I]),
+    "ps_batch_run": (_I, [_P, _P, _I, _P, _P, _P, _I, _D, _I, _P, _SZ, _P, _P]),
+    "ps_plan_destroy": (None, [_P]),
     "ps_rk2_workspace_size": (_SZ, [_GP, _P, _I64]),
     "ps_rk2_step": (_I, [_GP, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _D, _P, _I, _P, _P, _SZ,
                          _P, _P]),

@@ -165,6 +165,46 @@ __global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
   }
 }
 
+// Counting pass over the concatenated particles of many fields: particle p of
+// field f (pbase[f] <= p < pbase[f+1]) goes to global bin bin_base[f] + its
+// bin in field f.
+__global__ void bin_count_batch_kernel(const BinField* __restrict__ tab, int nfields,
+                                       int64_t np, const double* __restrict__ pos,
+                                       int32_t* __restrict__ bin_of, int32_t* __restrict__ rank,
+                                       int32_t* __restrict__ counts, int32_t* status) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t warp_start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane;
+  for (int64_t base = warp_start; base < np; base += stride) {
+    const int64_t p = base + lane;
+    const bool valid = p < np;
+    int key = -1 - lane;
+    if (valid) {
+      int lo = 0, hi = nfields;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tab[mid].pbase <= p) lo = mid;
+        else hi = mid;
+      }
+      bool ok;
+      key = tab[lo].bin_base +
+            bin_of_position(tab[lo].g, tab[lo].b, pos[p], pos[np + p], pos[2 * np + p], ok);
+      if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+    }
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int leader = __ffs(peers) - 1;
+    const int within = __popc(peers & ((1u << lane) - 1));
+    int basev = 0;
+    if (valid && lane == leader) basev = atomicAdd(&counts[key], __popc(peers));
+    basev = __shfl_sync(peers, basev, leader);
+    if (valid) {
+      bin_of[p] = key;
+      rank[p] = basev + within;
+    }
+  }
+}
+
 int persistent_blocks(int64_t work, int threads) {
   static int sms = 0;
   if (!sms) {
@@ -219,6 +259,35 @@ ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np, const dou
   if (np > 0 && (perm || pos_sorted || ids_sorted)) {
     bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
         np, pos, bin_of, rank, bin_offsets, perm, pos_sorted, ids, ids_sorted);
+    if ((rc = check_launch("bin_scatter"))) return rc;
+  }
+  return PS_OK;
+}
+
+ps_status bin_run_batch(const BinField* d_tab, int nfields, int64_t total_bins, int64_t np,
+                        const double* pos, int32_t* bin_of, int32_t* bin_offsets,
+                        double* pos_sorted, const int64_t* ids, int64_t* ids_sorted,
+                        int32_t* counts, int32_t* rank, int32_t* scan_tmp, int32_t* status,
+                        cudaStream_t st) {
+  ps_status rc = check_cuda(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (total_bins + 1), st),
+                            "batch counts memset");
+  if (rc) return rc;
+  if (np > 0) {
+    bin_count_batch_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
+        d_tab, nfields, np, pos, bin_of, rank, counts, status);
+    if ((rc = check_launch("bin_count_batch"))) return rc;
+  }
+  const int64_t ntiles = (int64_t)scan_tmp_elems(total_bins);
+  scan_tile_sums<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, total_bins, scan_tmp);
+  if ((rc = check_launch("scan_tile_sums"))) return rc;
+  scan_tile_offsets<<<1, kScanThreads, 0, st>>>(scan_tmp, ntiles);
+  if ((rc = check_launch("scan_tile_offsets"))) return rc;
+  scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, total_bins, scan_tmp,
+                                                        bin_offsets);
+  if ((rc = check_launch("scan_tiles"))) return rc;
+  if (np > 0) {
+    bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
+        np, pos, bin_of, rank, bin_offsets, nullptr, pos_sorted, ids, ids_sorted);
     if ((rc = check_launch("bin_scatter"))) return rc;
   }
   return PS_OK;

@@ -19,6 +19,7 @@
 // position update is one FMA per axis.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "ps_internal.cuh"
@@ -803,11 +804,9 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   }
 }
 
-// MODE 0: vel; 1: vel + grad; 2: fused Heun step.  One CTA per brick.
+// One brick: stage its halo, then process its particles.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
-  extern __shared__ float4 smem[];
-  const int bin = blockIdx.x;
+__device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4* smem) {
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   if (beg >= end) return;
   const int nbx = a.b.nb[0], nby = a.b.nb[1];
@@ -825,6 +824,37 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(St
   else
     stage_halo<Tc, NC>(a, coef, P0, halo, false);
   process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
+}
+
+// MODE 0: vel; 1: vel + grad; 2: fused Heun step.  One CTA per brick.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
+  extern __shared__ float4 smem[];
+  brick_body<Tc, NC, MODE>(a, blockIdx.x, smem);
+}
+
+// Many fields in one launch: block b handles global brick b; the field is the
+// last f with bin_base[f] <= b, and its parameters are copied to shared memory.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3)
+    interp_staged_batch(const StagedArgs* __restrict__ tab, const int* __restrict__ bin_base,
+                        int nfields) {
+  extern __shared__ float4 smem[];
+  __shared__ StagedArgs sa;
+  __shared__ int local_bin;
+  if (threadIdx.x == 0) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = nfields;  // bin_base[lo] <= b < bin_base[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (bin_base[mid] <= b) lo = mid;
+      else hi = mid;
+    }
+    sa = tab[lo];
+    local_bin = b - bin_base[lo];
+  }
+  __syncthreads();
+  brick_body<Tc, NC, MODE>(sa, local_bin, smem);
 }
 
 // ------------------------------------------------- thread per particle ----
@@ -1291,6 +1321,69 @@ float3 dt_over_h(const GridArgs& g, double dt) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- batch ----
+// Helpers of the many-field form (batch.cu); StagedArgs stays private to this
+// file and travels as opaque bytes.
+
+size_t staged_args_size() { return sizeof(StagedArgs); }
+
+// Arguments of one field's fused Heun step inside a batch: positions are the
+// concatenated [3][np_total] arrays, offs points at the field's first bin.
+ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[3],
+                          const void* coef, const float* scale, int64_t np_total,
+                          const double* pos_in, double* pos_out, const int32_t* offs,
+                          float* vel, const int64_t* ids_in, int64_t* ids_out, double dt,
+                          int32_t* status, void* out, size_t* smem) {
+  if (coef_t == PS_F64) return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
+  StagedArgs a{};
+  ps_status rc = fill_staged(grid, coef_t, brick, 0, &a, smem);
+  if (rc) return rc;
+  a.coef = coef;
+  a.scale = scale;
+  a.np = np_total;
+  a.pos_in = pos_in;
+  a.pos_out = pos_out;
+  a.offs = offs;
+  a.vel = vel;
+  a.ids_in = ids_in;
+  a.ids_out = ids_out;
+  a.dt = dt;
+  const float3 d = dt_over_h(a.g, dt);
+  a.dtih[0] = d.x;
+  a.dtih[1] = d.y;
+  a.dtih[2] = d.z;
+  a.status = status;
+  memcpy(out, &a, sizeof(a));
+  return PS_OK;
+}
+
+// Launch the batched fused Heun step over total_bins bricks of nfields
+// fields.  Set prepare = true once before any stream capture (it only sets the
+// shared-memory limit of the kernel).
+ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
+                              int nfields, int64_t total_bins, size_t smem, bool prepare,
+                              cudaStream_t st) {
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    if constexpr (sizeof(Tc) == 8) {
+      return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
+    } else {
+      auto kern = interp_staged_batch<Tc, 3, 2>;
+      if (prepare) {
+        if (smem > 48 * 1024)
+          return check_cuda(
+              cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+              "batch smem attribute");
+        return PS_OK;
+      }
+      if (total_bins <= 0) return PS_OK;
+      kern<<<(unsigned)total_bins, kThreads, smem, st>>>(
+          static_cast<const StagedArgs*>(d_tab), d_bin_base, nfields);
+      return check_launch("interp_staged_batch");
+    }
+  });
+}
 
 // RK2 kernels used by ps_rk2_step (rk2.cu).
 ps_status rk2_launch_direct(const ps_grid* grid, ps_dtype coef_t, const void* c0,

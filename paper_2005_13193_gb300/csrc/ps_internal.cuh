@@ -94,6 +94,30 @@ ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np,
                   int32_t* scan_tmp, int32_t* status, cudaStream_t st);
 size_t scan_tmp_elems(int64_t nbins);
 
+// Many-field binning (batch.cu): one entry per field.
+struct BinField {
+  GridArgs g;
+  BrickArgs b;
+  int64_t pbase;     // first particle of the field in the concatenated arrays
+  int32_t bin_base;  // first global bin of the field
+};
+ps_status bin_run_batch(const BinField* d_tab, int nfields, int64_t total_bins, int64_t np,
+                        const double* pos, int32_t* bin_of, int32_t* bin_offsets,
+                        double* pos_sorted, const int64_t* ids, int64_t* ids_sorted,
+                        int32_t* counts, int32_t* rank, int32_t* scan_tmp, int32_t* status,
+                        cudaStream_t st);
+
+// Many-field brick kernel (interp.cu).
+size_t staged_args_size();
+ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[3],
+                          const void* coef, const float* scale, int64_t np_total,
+                          const double* pos_in, double* pos_out, const int32_t* offs,
+                          float* vel, const int64_t* ids_in, int64_t* ids_out, double dt,
+                          int32_t* status, void* out, size_t* smem);
+ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
+                              int nfields, int64_t total_bins, size_t smem, bool prepare,
+                              cudaStream_t st);
+
 // -------------------------------------------------------------- device ----
 
 #ifdef __CUDACC__

@@ -1,0 +1,136 @@
+"""Parity at the workloads' own sizes, in the launch configuration bench.py
+times (spline solve, then binned RK2 steps with 8^3 bricks re-binned every
+step), on outputs the FP64 oracle computes one by one.
+
+Bars as in test_gpu_parity: interpolation max |du| <= 1e-5 rms(u); cell and
+bin results bit-exact; one RK2 step <= dt * 1e-5 * rms(u) + 1e-14 in position;
+gradients <= 1e-5 * 3 * (n/L) * max|c|.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2005_13193_gb300 as ps
+from paper_2005_13193_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2 * math.pi
+DEV = "cuda"
+
+
+def rel_err(gpu, ref):
+    ref = np.asarray(ref)
+    return np.abs(np.asarray(gpu, dtype=np.float64) - ref).max() / np.sqrt((ref ** 2).mean())
+
+
+def test_tiny_config():
+    # 32^3 FP64 field (k^-5/3, 1 <= |k| <= 10), 4096 particles, coefficients,
+    # interpolation and one RK2 step with dt = 1e-3
+    n, dt = 32, 1e-3
+    field = synth.spectral_field(n, 10, seed=1000, device="cpu", dtype=torch.float64).numpy()
+    pos = synth.uniform_particles(4096, seed=2000)
+    cref = oracle.spline_coeffs(field)
+    ref = oracle.interp(cref, pos)
+    f = torch.from_numpy(field).to(DEV)
+    for dtype, bound in ((torch.float32, 1e-5), (torch.float64, 5e-7)):
+        sf = ps.SplineField.from_field(f, dtype)
+        assert rel_err(sf.interp(torch.from_numpy(pos).to(DEV)).cpu().numpy(), ref) <= bound
+    sf = ps.SplineField.from_field(f, torch.float32)
+    tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=(8, 8, 8))
+    tr.step(dt)
+    new_ref, u1 = oracle.rk2_step(cref, pos, dt)
+    ids = tr.ids.cpu().numpy()
+    rms = np.sqrt((u1 ** 2).mean())
+    assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= dt * 1e-5 * rms + 1e-14
+
+
+def test_mid_config_full_size():
+    # 512^3 FP32 (k^-5/3, 1 <= |k| <= 170), 16,777,216 particles, 10 RK2 steps
+    # (dt = 1e-3) re-binned into 8^3 bricks every step.  After 9 steps the
+    # bins, the velocities and the 10th step are checked particle by particle
+    # on a seeded sample against the oracle started from the GPU's positions.
+    N, NP, dt, brick = 512, 1 << 24, 1e-3, (8, 8, 8)
+    free, _ = torch.cuda.mem_get_info()
+    if free < 16e9:
+        pytest.skip("needs 16 GB of free device memory")
+    field = synth.spectral_field(N, 170, seed=1001, device=DEV, dtype=torch.float32)
+    pos = torch.from_numpy(synth.uniform_particles(NP, seed=2001)).to(DEV)
+    sf = ps.SplineField.from_field(field, torch.float32)
+    tr = ps.Tracker(sf, pos, brick=brick)
+    for _ in range(9):
+        tr.step(dt)
+    assert ps.ps_status_read(tr.status)[0] == 0
+    x9 = tr.pos.cpu().numpy()
+    ids9 = tr.ids.cpu().numpy()
+    tr.step(dt)
+    torch.cuda.synchronize()
+    x10 = tr.pos.cpu().numpy()
+    ids10 = tr.ids.cpu().numpy()
+    u1 = tr.vel.cpu().numpy()
+    offs = tr.offsets.cpu().numpy()
+    # bins of x9 (the 10th step re-binned them): bit-exact
+    _, off_ref, _ = oracle.bin_particles((N, N, N), brick, x9)
+    np.testing.assert_array_equal(offs, off_ref)
+    # oracle coefficients of the same FP32 field
+    oracle.set_num_threads(0)
+    cref = oracle.spline_coeffs(field.cpu().numpy().astype(np.float64))
+    del field
+    rng = np.random.default_rng(5)
+    sample = rng.choice(NP, size=20000, replace=False)   # slots after step 10
+    pid = ids10[sample]
+    where9 = np.empty(NP, dtype=np.int64)
+    where9[ids9] = np.arange(NP)
+    xs9 = x9[:, where9[pid]]
+    new_ref, u_ref = oracle.rk2_step(cref, xs9, dt)
+    rms = np.sqrt((u_ref ** 2).mean())
+    assert np.abs(u1[:, sample] - u_ref).max() <= 1e-5 * rms
+    assert np.abs(x10[:, sample] - new_ref).max() <= dt * 1e-5 * rms + 1e-14
+
+
+def test_diff_config_full_size():
+    # 256^3 FP32 (k^-5/3, 1 <= |k| <= 85), 4,194,304 particles: forward
+    # interpolation, the 9-component velocity-gradient tensor, and the
+    # backward with respect to positions and to the field, against the oracle;
+    # the gradient also against FP64 central differences (h = 1e-6) of the
+    # oracle on 1024 particles.
+    N, NP = 256, 1 << 22
+    field = synth.spectral_field(N, 85, seed=1003, device=DEV, dtype=torch.float32)
+    pos_h = synth.uniform_particles(NP, seed=2003)
+    pos = torch.from_numpy(pos_h).to(DEV)
+    sf = ps.SplineField.from_field(field, torch.float32)
+    bins, pos_s = ps.bin_particles((N,) * 3, (8, 8, 8), pos, want_sorted=True)
+    vel, grad = sf.interp(pos, grad=True, bins=bins)
+    w = np.random.default_rng(6).standard_normal((3, NP)).astype(np.float32)
+    g_pos = torch.empty_like(pos)
+    g_field = torch.empty((3, N, N, N), dtype=torch.float32, device=DEV)
+    ps.ps_interp_backward(sf.coef, sf.n, pos, torch.from_numpy(w).to(DEV), g_pos, g_field)
+    torch.cuda.synchronize()
+    oracle.set_num_threads(0)
+    f64 = field.cpu().numpy().astype(np.float64)
+    cref = oracle.spline_coeffs(f64)
+    sample = np.random.default_rng(7).choice(NP, size=1024, replace=False)
+    ps_ = pos_h[:, sample]
+    v_ref, g_ref = oracle.interp(cref, ps_, grad=True)
+    rms = np.sqrt((v_ref ** 2).mean())
+    assert np.abs(vel.cpu().numpy()[:, sample] - v_ref).max() <= 1e-5 * rms
+    gg = grad.cpu().numpy()[:, :, sample]
+    cmax = np.abs(cref).max()
+    tol = 1e-5 * 3 * (N / TWO_PI) * cmax
+    assert np.abs(gg - g_ref).max() <= tol
+    # FP64 central differences of the oracle, h = 1e-6
+    for d in range(3):
+        p1, p0 = ps_.copy(), ps_.copy()
+        p1[d] += 1e-6
+        p0[d] -= 1e-6
+        fd = (oracle.interp(cref, p1) - oracle.interp(cref, p0)) / 2e-6
+        assert np.abs(gg[:, d] - fd).max() <= tol + 1e-6 * np.abs(fd).max()
+    # backward: positions on the sample, field everywhere
+    gp_ref, _ = oracle.interp_backward(cref, ps_, w[:, sample].astype(np.float64),
+                                       want_field=False)
+    assert np.abs(g_pos.cpu().numpy()[:, sample] - gp_ref).max() <= 3 * tol * np.abs(w).max()
+    _, gf_ref = oracle.interp_backward(cref, pos_h, w.astype(np.float64), want_pos=False)
+    gf = g_field.cpu().numpy()
+    assert np.abs(gf - gf_ref).max() <= 1e-5 * np.abs(gf_ref).max()
