@@ -89,6 +89,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, pg, device) -> float:
+    """The slowest rank's time: every rank's units count only once all are done."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units processed by all ranks (replicas of the same problem) per second."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks ----
 
 class ClockSampler:
@@ -228,11 +243,7 @@ def run_ours(args):
     clk = clocks.stop()
     if pg:
         pg.barrier()
-    ms = t0.elapsed_time(t1) / K
-    if pg:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t0.elapsed_time(t1) / K, pg, dev)
 
     solve_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_solve)
     rk_ms = [a.elapsed_time(b) for step in ev_rk for a, b in step]
@@ -244,7 +255,7 @@ def run_ours(args):
     solve_pass_bytes = 3 * 4 * N ** 3 * 5 + coef_bytes
     achieved = rk_alg_bytes / (rk_avg * 1e-3) / 1e9
     units = 2 * RK_STEPS * NP
-    value = ws_ * units / (ms * 1e-3)
+    value = whole_job_rate(units, ws_, ms)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": K,
@@ -273,6 +284,8 @@ def run_ours(args):
 
     if not args.no_extras and rank == 0:
         result["interp_sorted_vs_unsorted"] = interp_extras(ps, torch, dev, coef, bufs[0], n3)
+        result["coef_forms"] = precision_forms(ps, torch, dev, field, coef, bufs[0], n3)
+        result["batched_48_fields"] = batch_extras(ps, torch, dev)
     if not args.no_e2e:
         result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg)
     if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
@@ -310,6 +323,118 @@ def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
         t = a.elapsed_time(b) / 5
         out[name] = {"ms": t, "particles_per_s": NP / (t * 1e-3)}
     return out
+
+
+def _event_ms(torch, fn, reps, warmup=2):
+    for _ in range(warmup):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def precision_forms(ps, torch, dev, field, coef32, pos_now, n3):
+    """The same solve and binned RK2 step with BF16 and FP16 coefficients
+    (power-of-two scale per x-line) beside FP32: kernel times, and the
+    velocity error of every particle against the FP32 form, relative to the
+    rms velocity."""
+    # positions stored in bin order (the staged kernel's precondition)
+    bins, pos_binned = ps.bin_particles(n3, BRICK, pos_now, want_sorted=True,
+                                        want_perm=False)
+    offs = bins.offsets
+    del bins
+    vel32 = torch.empty((3, NP), dtype=torch.float32, device=dev)
+    vel = torch.empty_like(vel32)
+    pos = torch.empty_like(pos_binned)
+    status = torch.zeros(4, dtype=torch.int32, device=dev)
+    out = {}
+    for name, dt_ in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        if dt_ == torch.float32:
+            c, s, wsq = coef32, None, None
+        else:
+            c = torch.empty(ps.coef_shape(n3, 3, dt_), dtype=dt_, device=dev)
+            s = torch.empty((3, N + 3, N + 3), dtype=torch.float32, device=dev)
+            wsq = ps.workspace(ps.ps_spline_coeffs_workspace_size(n3, 3, dt_), dev)
+        t_solve = _event_ms(torch, lambda: ps.ps_spline_coeffs(field, c, scale=s, ws=wsq), 3)
+
+        evs = []
+
+        def rk():
+            # every run starts from the binned positions (the bins stay valid)
+            pos.copy_(pos_binned)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ps.ps_rk2_step(c, n3, pos, DT, scale_n=s, vel_out=vel, brick=BRICK, rebin=False,
+                           bin_offsets=offs, status=status)
+            b.record()
+            evs.append((a, b))
+        for _ in range(2):
+            rk()
+        evs.clear()
+        for _ in range(5):
+            rk()
+        torch.cuda.synchronize()
+        t_rk = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        e = {"solve_ms": t_solve, "rk2_kernel_ms": t_rk,
+             "rk2_particles_per_s": 2 * NP / (t_rk * 1e-3),
+             "coef_bytes": c.numel() * c.element_size()}
+        if dt_ == torch.float32:
+            vel32.copy_(vel)
+        else:
+            d = (vel - vel32).double()
+            rms = float(torch.sqrt((vel32.double() ** 2).mean()))
+            e["max_err_vs_f32_rel_rms"] = float(d.abs().max()) / rms
+            e["rms_err_vs_f32_rel_rms"] = float(torch.sqrt((d ** 2).mean())) / rms
+        out[name] = e
+        del c, s, wsq
+    if ps.ps_status_read(status)[0] != 0:
+        raise RuntimeError("device status set in the coefficient-form runs")
+    return out
+
+
+def batch_extras(ps, torch, dev):
+    """The many-fields workload: 48 fields with edges uniform over {64, 96,
+    128, 192, 256}, 10k..2M particles per field (log-uniform), 20 Heun steps
+    (dt 1e-3).  Batched plan (autotuned brick, steps replayed from a CUDA
+    graph) against a loop of single-field Tracker steps on the same GPU."""
+    from paper_2005_13193_gb300 import autotune, synth
+    sizes, nps = synth.batch_sizes(48, seed=3000)
+    nsteps, dt = 20, 1e-3
+    flds = []
+    for i, n in enumerate(sizes):
+        f = synth.spectral_field(n, n // 3, seed=3100 + i, device=dev, dtype=torch.float32)
+        flds.append((f, ps.SplineField.from_field(f)))
+    pos0 = torch.cat([torch.from_numpy(synth.uniform_particles(v, seed=3200 + i))
+                      for i, v in enumerate(nps)], dim=1).to(dev)
+    grids = [(n,) * 3 for n in sizes]
+    best, table = autotune.tune_batch(grids, nps, flds, pos0)
+    plan = ps.BatchPlan(grids, nps, brick=best)
+    pos = pos0.clone()
+    ids = torch.arange(plan.np_total, dtype=torch.int64, device=dev)
+    plan.run(flds, pos, nsteps, dt, solve=False, ids=ids, use_graph=True)  # capture
+    t_graph = _event_ms(torch, lambda: plan.run(flds, pos, nsteps, dt, solve=False, ids=ids,
+                                                use_graph=True), 3, warmup=1)
+    trackers = []
+    for f, (n, v) in enumerate(zip(sizes, nps)):
+        b = plan.base[f]
+        trackers.append(ps.Tracker(flds[f][1], pos0[:, b:b + v].clone(), brick=BRICK,
+                                   keep_velocity=False))
+
+    def loop():
+        for _ in range(nsteps):
+            for tr in trackers:
+                tr.step(dt)
+    t_loop = _event_ms(torch, loop, 2, warmup=1)
+    units = 2 * nsteps * plan.np_total
+    return {"fields": len(sizes), "particles": plan.np_total, "rk2_steps": nsteps,
+            "autotuned_brick": list(best),
+            "autotune_ms_per_step": {"x".join(map(str, k)): v for k, v in table.items()},
+            "batched_graph_ms": t_graph, "batched_particles_per_s": units / (t_graph * 1e-3),
+            "per_field_loop_ms": t_loop, "loop_particles_per_s": units / (t_loop * 1e-3)}
 
 
 def e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg):
@@ -351,13 +476,9 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg):
         step()
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / steps
-    if pg:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(a.elapsed_time(b) / steps, pg, dev)
     units = 2 * RK_STEPS * NP
-    return {"value": ws_ * units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+    return {"value": whole_job_rate(units, ws_, ms), "unit": UNIT, "ms_per_step": ms,
             "h2d_bytes_per_step": field_h.numel() * 4 + pos_h.numel() * 8,
             "d2h_bytes_per_step": pos_out_h.numel() * 8 + vel_h.numel() * 4,
             "api": "ps_spline_coeffs + ps_rk2_step(rebin=1, ids)"}

@@ -70,6 +70,67 @@ def spectral_field(n: int, kmax: int | None = None, seed: int = 1000,
     return out
 
 
+def spectral_field_planes(n: int, kmax: int | None = None, seed: int = 1000,
+                          device: str | torch.device = "cpu", dtype=torch.float32,
+                          ncomp: int = 3, chunk: int = 64) -> torch.Tensor:
+    """The same k^-5/3 random-phase recipe as `spectral_field`, built one kz
+    plane at a time so that a 1536^3 field fits next to its coefficients.
+
+    The Gaussian draws of plane kz come from a generator seeded with
+    (seed << 12) + (plane index), so they differ from `spectral_field`'s;
+    planes with |kz| > kmax are zero and draw nothing.  The inverse FFT is done
+    separably (x-y per block of planes, then z per block of rows) in place on
+    one complex component, and the rms rescale is accumulated in FP64 per
+    block.  Peak extra memory: one complex component (8 n^3 bytes).
+    """
+    if kmax is None:
+        kmax = n // 3
+    if n > 4096:
+        raise ValueError("n <= 4096")
+    dev = torch.device(device)
+    cdt = torch.complex128 if dtype == torch.float64 else torch.complex64
+    rdt = torch.float64 if dtype == torch.float64 else torch.float32
+    k1 = torch.fft.fftfreq(n, d=1.0 / n, device=dev, dtype=rdt)
+    kz_host = np.fft.fftfreq(n, d=1.0 / n)
+    ky = k1.view(n, 1)
+    kx = k1.view(1, n)
+    kin = ky * ky + kx * kx
+    out = torch.empty((ncomp, n, n, n), device=dev, dtype=dtype)
+    spec = torch.empty((n, n, n), device=dev, dtype=cdt)
+    gen = torch.Generator(device=dev)
+    for c in range(ncomp):
+        for iz in range(n):
+            kz = float(kz_host[iz])
+            if abs(kz) > kmax:
+                spec[iz].zero_()
+                continue
+            k2 = kin + kz * kz
+            mask = (k2 >= 1) & (k2 <= kmax * kmax)
+            amp = torch.where(mask, torch.sqrt(k2.clamp(min=1)).pow(-11.0 / 6.0),
+                              torch.zeros_like(k2))
+            gen.manual_seed((int(seed) << 12) + iz)
+            a = torch.complex(torch.randn((3, n, n), generator=gen, device=dev, dtype=rdt),
+                              torch.randn((3, n, n), generator=gen, device=dev, dtype=rdt))
+            kd = (kx * a[0] + ky * a[1] + kz * a[2]) / k2.clamp(min=1)
+            kv = (kx, ky, kz)
+            ac = a[c % 3] - kv[c % 3] * kd
+            others = [a[d] - kv[d] * kd for d in range(3)]
+            norm = torch.sqrt(sum((o.real ** 2 + o.imag ** 2) for o in others)).clamp(min=1e-30)
+            spec[iz] = ac * (amp / norm)
+        for z0 in range(0, n, chunk):
+            spec[z0:z0 + chunk] = torch.fft.ifft2(spec[z0:z0 + chunk], dim=(1, 2))
+        for y0 in range(0, n, chunk):
+            spec[:, y0:y0 + chunk] = torch.fft.ifft(spec[:, y0:y0 + chunk], dim=0)
+        ss = 0.0
+        for z0 in range(0, n, chunk):
+            ss += float((spec[z0:z0 + chunk].real.double() ** 2).sum())
+        rms = math.sqrt(ss / float(n) ** 3)
+        for z0 in range(0, n, chunk):
+            out[c, z0:z0 + chunk] = (spec[z0:z0 + chunk].real / rms).to(dtype)
+    del spec
+    return out
+
+
 def uniform_particles(np_: int, seed: int = 2000, L: float = TWO_PI) -> np.ndarray:
     """[3][np] FP64 positions, i.i.d. uniform on [0, L)^3 (numpy PCG64)."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))

@@ -122,3 +122,45 @@ def test_batch_config_48_fields():
         # trajectories' divergence over t = 0.02 (|grad u| <= n/3 |u|)
         growth = math.exp(nsteps * dt * (n / 3) * u_max)
         assert np.abs(got[:, pick] - x).max() <= nsteps * dt * 1e-5 * u_max * growth + 1e-13
+
+
+def test_autotune_tracker_and_batch(tmp_path):
+    from paper_2005_13193_gb300 import autotune
+    old = ps.ps_tune_get("brick_kernel")
+    try:
+        f = synth.spectral_field(64, 21, seed=700, device=DEV, dtype=torch.float32)
+        sf = ps.SplineField.from_field(f)
+        pos = torch.from_numpy(synth.uniform_particles(200000, seed=701)).to(DEV)
+        before = pos.clone()
+        cache = str(tmp_path / "tracker.tune")
+        best, table = autotune.tune_tracker(sf, pos, candidates=((8, 8, 8), (8, 8, 4)),
+                                            kernels=(0, 2), cache=cache)
+        assert best in table and len(table) == 4
+        assert all(v > 0 for v in table.values())
+        assert torch.equal(pos, before)
+        assert ps.ps_tune_get("brick_kernel") == best[0]
+        assert autotune.load_cache(cache) == {"kernel": (best[0],), "brick": best[1]}
+    finally:
+        ps.ps_tune_set("brick_kernel", old)
+
+    sizes, nps = [32, 64, 48], [30000, 80000, 5000]
+    flds = _fields(sizes, 710)
+    pos0 = _positions(nps, 720)
+    pos = torch.from_numpy(pos0.copy()).to(DEV)
+    fields = [(fl, s) for fl, s in flds]
+    cache = str(tmp_path / "batch.tune")
+    bbest, btable = autotune.tune_batch([(n,) * 3 for n in sizes], nps, fields, pos,
+                                        candidates=((8, 8, 8), (8, 4, 4), (16, 8, 8)),
+                                        cache=cache)
+    assert bbest in btable and np.array_equal(pos.cpu().numpy(), pos0)
+    # a plan built from the cache runs the tuned shape: bit-identical (per
+    # particle label; the order inside a bin is unspecified) to an explicit
+    # plan with that brick
+    outs = []
+    for kw in ({"tune_cache": cache}, {"brick": bbest}):
+        plan = ps.BatchPlan([(n,) * 3 for n in sizes], nps, **kw)
+        p = torch.from_numpy(pos0.copy()).to(DEV)
+        ids = torch.arange(plan.np_total, dtype=torch.int64, device=DEV)
+        plan.run(fields, p, 3, 2e-3, solve=False, ids=ids, use_graph=False)
+        outs.append(_by_label(p.cpu().numpy(), ids.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0], outs[1])

@@ -6,6 +6,7 @@ Bars as in test_gpu_parity: interpolation max |du| <= 1e-5 rms(u); cell and
 bin results bit-exact; one RK2 step <= dt * 1e-5 * rms(u) + 1e-14 in position;
 gradients <= 1e-5 * 3 * (n/L) * max|c|.
 """
+import json
 import math
 
 import numpy as np
@@ -134,3 +135,75 @@ def test_diff_config_full_size():
     _, gf_ref = oracle.interp_backward(cref, pos_h, w.astype(np.float64), want_pos=False)
     gf = g_field.cpu().numpy()
     assert np.abs(gf - gf_ref).max() <= 1e-5 * np.abs(gf_ref).max()
+
+
+def test_precision_config_full_size():
+    # 1536^3 FP32 field (k^-5/3, 1 <= |k| <= 512), 300,000,000 particles: one
+    # coefficient solve, interpolation and one RK2 step (dt = 1e-3) with FP32,
+    # BF16 and FP16 coefficients (BF16/FP16 with a power-of-two scale per
+    # x-line).  FP32 is checked against the windowed FP64 oracle on 4096
+    # particles with the bars above; BF16/FP16 against the FP32 result on a
+    # seeded 1,000,000-particle subsample and against the oracle on the 4096,
+    # at most 1e-2 (BF16) and 1e-3 (FP16) of the rms velocity, and within the
+    # a-priori rounding bound 2^-8 max|c| (BF16), 2^-10 max|c| (FP16): the
+    # basis weights are non-negative and sum to one.
+    N, NP, dt, brick = 1536, 300_000_000, 1e-3, (8, 8, 8)
+    free, _ = torch.cuda.mem_get_info()
+    if free < 170e9:
+        pytest.skip("needs 170 GB of free device memory")
+    field = synth.spectral_field_planes(N, 512, seed=1002, device=DEV)
+    pos_h = synth.uniform_particles(NP, seed=2002)
+    pos = torch.from_numpy(pos_h).to(DEV)
+    rng = np.random.default_rng(8)
+    sub_h = np.sort(rng.choice(NP, size=1_000_000, replace=False))
+    kpick = rng.choice(sub_h.size, size=4096, replace=False)
+    sub = torch.from_numpy(sub_h).to(DEV)
+    bins = ps.bin_particles((N,) * 3, brick, pos)
+    got, cmax = {}, None
+    for dtype in (torch.float32, torch.bfloat16, torch.float16):
+        sf = ps.SplineField.from_field(field, dtype)
+        if dtype == torch.float32:
+            cmax = max(float(sf.coef[c].abs().max()) for c in range(3))
+        st = torch.zeros(4, dtype=torch.int32, device=DEV)
+        vel = sf.interp(pos, bins=bins, status=st)
+        u_sub = vel[:, sub].cpu().numpy()
+        del vel
+        tr = ps.Tracker(sf, pos.clone(), brick=brick, keep_velocity=False)
+        tr.step(dt)
+        where = torch.empty_like(tr.ids)
+        where[tr.ids] = torch.arange(NP, dtype=torch.int64, device=DEV)
+        x_sub = tr.pos[:, where[sub]].cpu().numpy()
+        assert ps.ps_status_read(st)[0] == 0 and ps.ps_status_read(tr.status)[0] == 0
+        got[dtype] = (u_sub, x_sub)
+        del tr, where, sf
+        torch.cuda.empty_cache()
+    f_h = field.cpu().numpy()
+    del field
+    oracle.set_num_threads(0)
+    xk = pos_h[:, sub_h[kpick]]
+    u1 = oracle.interp_windowed(f_h, xk)
+    # Heun step from the oracle's own predictor
+    u2 = oracle.interp_windowed(f_h, xk + dt * u1)
+    x1 = xk + 0.5 * dt * (u1 + u2)
+    rms = np.sqrt((u1 ** 2).mean())
+    u32, x32 = got[torch.float32]
+    rms32 = np.sqrt((u32.astype(np.float64) ** 2).mean())
+    report = {"rms_u": rms, "max_abs_c": cmax}
+    for dtype, name, bar, ulp in ((torch.float32, "f32", 1e-5, 0.0),
+                                  (torch.bfloat16, "bf16", 1e-2, 2.0 ** -8),
+                                  (torch.float16, "f16", 1e-3, 2.0 ** -10)):
+        u, x = got[dtype]
+        e_ora = np.abs(u[:, kpick] - u1).max() / rms
+        e_ora_rms = np.sqrt(((u[:, kpick] - u1) ** 2).mean()) / rms
+        ex_ora = np.abs(x[:, kpick] - x1).max()
+        report[name] = {"max_err_vs_oracle": e_ora, "rms_err_vs_oracle": e_ora_rms,
+                        "pos_err_vs_oracle": ex_ora}
+        assert e_ora <= bar
+        assert ex_ora <= dt * bar * rms + 1e-14
+        if dtype != torch.float32:
+            d = np.abs(u.astype(np.float64) - u32)
+            report[name]["max_err_vs_f32_1M"] = d.max() / rms32
+            report[name]["rms_err_vs_f32_1M"] = np.sqrt((d ** 2).mean()) / rms32
+            assert d.max() <= ulp * cmax + 1e-5 * rms32
+            assert d.max() / rms32 + report["f32"]["max_err_vs_oracle"] <= bar
+    print("PRECISION " + json.dumps(report))

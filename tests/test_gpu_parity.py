@@ -388,3 +388,27 @@ def test_rk2_multi_step_and_time_dependent():
         ref, _ = oracle.rk2_step(cref, ref, dt, coef_np1=cref2 if two else None)
     ids = tr.ids.cpu().numpy()
     assert np.abs(tr.pos.cpu().numpy() - ref[:, ids]).max() <= 4 * dt * 3e-5 * 3 + 1e-13
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_rk2_every_autotune_candidate(kernel, dtype, brick_kernel):
+    # every brick shape the autotuner may pick, with every brick kernel, on a
+    # grid all of them tile (so the 16-byte staging path is taken where the
+    # shape allows it) and on a ragged one
+    from paper_2005_13193_gb300 import autotune
+    ps.ps_tune_set("brick_kernel", kernel)
+    for n in ((64, 32, 48), (37, 21, 26)):
+        field, pos, cref = _case(n, 20000, seed=121, spread=1.3)
+        dt = 1e-2
+        new_ref, u1_ref = oracle.rk2_step(cref, pos, dt)
+        rms = np.sqrt((u1_ref ** 2).mean())
+        tol_u = 1e-5 * rms if dtype == torch.float32 else 2.0 ** -8 * np.abs(cref).max()
+        sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), dtype)
+        for brick in autotune.CANDIDATES:
+            tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick)
+            tr.step(dt)
+            assert ps.ps_status_read(tr.status)[0] == 0
+            ids = tr.ids.cpu().numpy()
+            assert np.abs(tr.vel.cpu().numpy() - u1_ref[:, ids]).max() <= tol_u, brick
+            assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= dt * tol_u + 1e-14
