@@ -90,11 +90,16 @@ const char* ps_version(void);
 int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
 
 /* Launch-shape knobs (not part of the method): "brick_kernel" 0 = one CTA per
- * brick, 8 lanes per particle (default), 1 = persistent CTAs that prefetch the
- * next brick's halo while processing the current one, 2 = one CTA per brick,
- * one thread per particle; "brick_ctas_per_sm" in [1, 8] (default 3,
- * persistent form only).  Process-wide; set them before capturing work in a graph.
- * ps_tune_get returns -1 for an unknown key. */
+ * brick, 8 lanes per particle, phases separated by block barriers (default),
+ * 1 = persistent CTAs that prefetch the next brick's halo while processing the
+ * current one, 2 = one CTA per brick, one thread per particle, 3 = one CTA per
+ * brick, every warp walking its own particles with no barrier after the
+ * staging; "brick_ctas_per_sm" in [1, 8] (default 3,
+ * persistent form only); "brick_min_stage" in [0, 2^20] (default 8): in the
+ * one-CTA-per-brick kernel, bricks holding fewer particles skip the halo
+ * staging and gather their stencils from global memory.  Process-wide; set
+ * them before capturing work in a graph.  ps_tune_get returns -1 for an
+ * unknown key. */
 ps_status ps_tune_set(const char* key, int64_t value);
 int64_t ps_tune_get(const char* key);
 

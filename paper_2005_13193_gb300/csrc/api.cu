@@ -109,8 +109,13 @@ extern "C" const char* ps_last_error(void) { return g_err; }
 extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
   if (!key) return fail(PS_ERR_INVALID_ARG, "key is NULL");
   if (!strcmp(key, "brick_kernel")) {
-    if (value < 0 || value > 2) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0, 1 or 2");
+    if (value < 0 || value > 3) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0, 1, 2 or 3");
     tuning().brick_kernel = (int)value;
+    return PS_OK;
+  }
+  if (!strcmp(key, "brick_min_stage")) {
+    if (value < 0 || value > (1 << 20)) return fail(PS_ERR_INVALID_ARG, "brick_min_stage in [0, 2^20]");
+    tuning().brick_min_stage = (int)value;
     return PS_OK;
   }
   if (!strcmp(key, "brick_ctas_per_sm")) {
@@ -125,6 +130,7 @@ extern "C" int64_t ps_tune_get(const char* key) {
   if (!key) return -1;
   if (!strcmp(key, "brick_kernel")) return tuning().brick_kernel;
   if (!strcmp(key, "brick_ctas_per_sm")) return tuning().brick_ctas_per_sm;
+  if (!strcmp(key, "brick_min_stage")) return tuning().brick_min_stage;
   return -1;
 }
 

@@ -329,6 +329,7 @@ struct StagedArgs {
   int SX;       // row stride in float4 units (= S[0])
   int PS;       // plane stride in float4 units: >= SX*S[1], = 4 (mod 8)
   int vec;      // 1: halo rows are whole 16-byte vectors inside the array
+  int min_stage;  // bricks with fewer particles gather from global memory
   const void* coef;
   const float* scale;
   const void* coef2;  // second-stage field of an RK2 step; NULL = same as coef
@@ -346,6 +347,24 @@ struct StagedArgs {
   float dtih[3];  // dt * n/L per axis
   int32_t* status;
 };
+
+// Halo geometry (extents, row and plane strides in float4 units).  KS > 0
+// fixes at compile time the cubic halo of KS points per axis of the 8^3
+// brick (KS = 11, plane stride 124 = 4 mod 8), so that every index in the
+// staging and the gathers folds into immediates; KS = 0 reads the launch
+// arguments.
+template <int KS> struct HaloGeo {
+  int Sx, Sy, Sz, SX, PS;
+  __device__ __forceinline__ explicit HaloGeo(const StagedArgs& a)
+      : Sx(a.S[0]), Sy(a.S[1]), Sz(a.S[2]), SX(a.SX), PS(a.PS) {}
+};
+template <> struct HaloGeo<11> {
+  static constexpr int Sx = 11, Sy = 11, Sz = 11, SX = 11, PS = 124;
+  __device__ __forceinline__ explicit HaloGeo(const StagedArgs&) {}
+};
+__device__ __forceinline__ bool is_cube11(const StagedArgs& a) {
+  return a.S[0] == 11 && a.S[1] == 11 && a.S[2] == 11 && a.SX == 11 && a.PS == 124;
+}
 
 // Padded index (any integer) -> interior padded index of the same node.
 __device__ __forceinline__ int wrap_row(int P, int n) {
@@ -438,13 +457,14 @@ template <typename H> struct Vec16Half {
 template <> struct Vec16<__nv_bfloat16> : Vec16Half<__nv_bfloat16> {};
 template <> struct Vec16<__half> : Vec16Half<__half> {};
 
-template <typename Tc, int NC>
+template <typename Tc, int NC, int KS = 0>
 __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __restrict__ coef,
                                                const int P0[3], float4* halo, bool sync = true) {
   constexpr int V = Vec16<Tc>::V;
   constexpr int U = 8 / V;               // rows in flight per thread
   const GridArgs& g = a.g;
-  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
+  const HaloGeo<KS> hg(a);
+  const int Sx = hg.Sx, Sy = hg.Sy, Sz = hg.Sz;
   const int qx = (Sx + V - 1) / V;       // vectors per halo row (<= 4)
   const int qd = threadIdx.x & 3, rs = threadIdx.x >> 2;
   const int RS = blockDim.x >> 2;        // rows per block step
@@ -474,7 +494,7 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
           sc = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
         Vec16<Tc>::load(b0 + c * cs + roff, sc, v[c]);
       }
-      const int h0 = lz * a.PS + ly * a.SX + q * 4;
+      const int h0 = lz * hg.PS + ly * hg.SX + q * 4;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
         if (q * 4 + i < Sx)
@@ -494,7 +514,7 @@ __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __
       const int r = r0 + u * RS;
       act[u] = qd < qx && r < nrows;
       const int lz = r / Sy, ly = r - lz * Sy;
-      h0[u] = lz * a.PS + ly * a.SX + qd * V;
+      h0[u] = lz * hg.PS + ly * hg.SX + qd * V;
       const int64_t roff = ((int64_t)lz * m1 + ly) * rx;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -675,7 +695,7 @@ __device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsign
 // pbuf: optional shared copy of the first round's positions ([3][kRecords]).
 // raw_next: if set, the copies of brick next_bin are issued as soon as phase
 // A has consumed pbuf.
-template <typename Tc, int NC, int MODE>
+template <typename Tc, int NC, int MODE, int KS = 0>
 __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int end,
                                               const int P0[3], const float4* halo,
                                               const Recs& R, double* pbuf,
@@ -689,6 +709,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   const int64_t np = a.np;
   const float nanf_ = __int_as_float(0x7fc00000);
   constexpr int TPT = (3 * kRecords + kThreads - 1) / kThreads;  // tasks per thread
+  const HaloGeo<KS> hg(a);
 
   for (int cb = beg; cb < end; cb += kRecords) {
     const int m = min(kRecords, end - cb);
@@ -700,7 +721,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
       const int task = tid + k * kThreads;
-      td[k] = task < 3 * m ? task / m : -1;
+      td[k] = task < m ? 0 : (task < 2 * m ? 1 : (task < 3 * m ? 2 : -1));
       ti[k] = task - max(td[k], 0) * m;
       tcell[k] = 0;
       tt[k] = 0.f;
@@ -711,7 +732,8 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
         tp[k] = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
         tx[k] = (pbuf && cb == beg) ? pbuf[d * kRecords + i] : a.pos_in[d * np + tp[k]];
         const bool ok = locate(tx[k], g.inv_h[d], g.n[d], tcell[k], tt[k]);
-        write_axis<GRAD>(R, i, d, tcell[k], tt[k], ok, sel3(P0, d), a.S[d]);
+        write_axis<GRAD>(R, i, d, tcell[k], tt[k], ok, sel3(P0, d),
+                         d == 0 ? hg.Sx : (d == 1 ? hg.Sy : hg.Sz));
       }
     }
     __syncthreads();
@@ -722,7 +744,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = b4 + (lane >> 3);
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
-      const bool oki = gather8<Tc, NC, GRAD>(halo, a.PS, a.SX, R, vi ? i : b4, g, coef, a.scale,
+      const bool oki = gather8<Tc, NC, GRAD>(halo, hg.PS, hg.SX, R, vi ? i : b4, g, coef, a.scale,
                                              q, kh, u, dx, dy, dz);
       if (!vi) continue;
       if constexpr (MODE <= 1) {
@@ -764,7 +786,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
           c %= g.n[d];
           if (c < 0) c += g.n[d];
         }
-        write_axis<false>(R, i, d, c, t2, ok, sel3(P0, d), a.S[d]);
+        write_axis<false>(R, i, d, c, t2, ok, sel3(P0, d), d == 0 ? hg.Sx : (d == 1 ? hg.Sy : hg.Sz));
         if (a.coef2 && ok)  // second field: its coefficients are not staged
           reinterpret_cast<signed char*>(R.lw())[4 * i + d] = (signed char)-1;
       }
@@ -777,7 +799,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = b4 + (lane >> 3);
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
-      const bool oki = gather8<Tc, NC, false>(halo, a.PS, a.SX, R, vi ? i : b4, g, cf2, sc2, q,
+      const bool oki = gather8<Tc, NC, false>(halo, hg.PS, hg.SX, R, vi ? i : b4, g, cf2, sc2, q,
                                               kh, u, dx, dy, dz);
       if (vi && sub == 0) R.u()[i] = make_float4(u[0], u[1], u[2], __int_as_float(oki ? 1 : 0));
     }
@@ -804,9 +826,287 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   }
 }
 
-// One brick: stage its halo, then process its particles.
+// ------------------------------------------------ warp-autonomous form ----
+// After the brick's halo is staged, every warp walks its own particles, four
+// at a time (8 lanes each), with no further block-level barrier: lanes 0-2 of
+// a group locate the particle along x, y, z (exact FP64 index arithmetic) and
+// broadcast (cell, t) to the group by shuffles; every lane then evaluates
+// only the basis values its share of the stencil needs, gathers, and the
+// group's butterfly leaves the sum in all 8 lanes, so the Heun predictor is
+// located redundantly by each lane in FP32 and the second gather follows at
+// once; lanes 0-2 write the FP64 update of their axis.
+
+// Lane-constant selector of one B-spline basis function b_i (Sec. 2.2,
+// Operation 2), evaluated in cancellation-free forms: b_0 = s^3/6,
+// b_1 = (3t^3 - 6t^2 + 4)/6, b_2(t) = b_1(1 - t), b_3 = t^3/6 (s = 1 - t).
+struct BasisPick {
+  bool flip, outer;
+};
+__device__ __forceinline__ BasisPick basis_pick(int i) {
+  return BasisPick{i == 0 || i == 2, i == 0 || i == 3};
+}
+__device__ __forceinline__ float basis_one(BasisPick k, float t) {
+  const float u = k.flip ? 1.f - t : t;
+  const float u2 = u * u;
+  return (k.outer ? u2 * u : fmaf(u2, fmaf(3.f, u, -6.f), 4.f)) * (1.f / 6.f);
+}
+__device__ __forceinline__ float dbasis_one(BasisPick k, float t) {
+  const float u = k.flip ? 1.f - t : t;
+  const float v = (k.outer ? u * u : u * fmaf(3.f, u, -4.f)) * 0.5f;
+  return k.flip ? -v : v;
+}
+
+// Stencil of one particle by its group of 8 lanes: lane (q, kh) covers
+// column a_x + q and z rows kh, kh + 2.  `inh`: the stencil lies in the
+// staged halo (local start l*); otherwise the rows are read from global
+// memory.  All lanes of the group return the sums.
+template <typename Tc, int NC, bool GRAD>
+__device__ __forceinline__ void gather_group(const float4* __restrict__ halo, int PS, int SX,
+                                             bool inh, const int l[3], const int cell[3],
+                                             const float t[3], const GridArgs& g,
+                                             const Tc* __restrict__ coef,
+                                             const float* __restrict__ scale, int q, int kh,
+                                             BasisPick kx, BasisPick kz0, BasisPick kz1,
+                                             float out[NC], float dx[NC], float dy[NC],
+                                             float dz[NC]) {
+  const float bxq = basis_one(kx, t[0]);
+  float by[4];
+  bspline<float>(t[1], by);
+  const float bz[2] = {basis_one(kz0, t[2]), basis_one(kz1, t[2])};
+  float dbxq = 0.f, dby[4] = {0.f, 0.f, 0.f, 0.f}, dbz[2] = {0.f, 0.f};
+  if (GRAD) {
+    dbxq = dbasis_one(kx, t[0]);
+    dbspline<float>(t[1], dby);
+    dbz[0] = dbasis_one(kz0, t[2]);
+    dbz[1] = dbasis_one(kz1, t[2]);
+  }
+  float acc[NC], accy[NC], accz[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
+  if (inh) {
+    const float4* hp = halo + (l[2] + kh) * PS + l[1] * SX + l[0] + q;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = hp[2 * kk * PS + j * SX];
+        const float vv[3] = {v.x, v.y, v.z};
+        const float w = by[j] * bz[kk];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
+        if (GRAD) {
+          const float wy = dby[j] * bz[kk], wz = by[j] * dbz[kk];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            accy[c] = fmaf(wy, vv[c], accy[c]);
+            accz[c] = fmaf(wz, vv[c], accz[c]);
+          }
+        }
+      }
+    }
+  } else {
+    const int ax = max(cell[0], 0), ay = max(cell[1], 0), az = max(cell[2], 0);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float w = by[j] * bz[kk];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float v = load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j, ax + q);
+          acc[c] = fmaf(w, v, acc[c]);
+          if (GRAD) {
+            accy[c] = fmaf(dby[j] * bz[kk], v, accy[c]);
+            accz[c] = fmaf(by[j] * dbz[kk], v, accz[c]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
+  if (GRAD) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      dx[c] = group_sum<8>(dbxq * acc[c]) * g.inv_hf[0];
+      dy[c] = group_sum<8>(bxq * accy[c]) * g.inv_hf[1];
+      dz[c] = group_sum<8>(bxq * accz[c]) * g.inv_hf[2];
+    }
+  }
+}
+
+// Stencil start relative to the halo origin, and whether it lies inside.
+template <int KS>
+__device__ __forceinline__ bool in_halo(const HaloGeo<KS>& hg, const int P0[3],
+                                        const int cell[3], int l[3]) {
+  const int S[3] = {hg.Sx, hg.Sy, hg.Sz};
+  bool in = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    l[d] = cell[d] - P0[d];
+    in = in && (unsigned)l[d] <= (unsigned)(S[d] - 4);
+  }
+  return in;
+}
+
+// Particles [beg, end) of one brick.  `staged`: the halo stores were issued
+// by this block and are published by the barrier below (taken by every
+// thread); otherwise all stencils come from global memory.
+template <typename Tc, int NC, int MODE, int KS>
+__device__ __forceinline__ void brick_warps(const StagedArgs& a, int beg, int end,
+                                            const int P0[3], const float4* halo, bool staged) {
+  constexpr bool GRAD = MODE == 1;
+  const HaloGeo<KS> hg(a);
+  static_assert(MODE != 2 || NC == 3, "the Heun step advances three components");
+  const GridArgs& g = a.g;
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int q = lane & 3, kh = (lane >> 2) & 1, sub = lane & 7, gb = lane & ~7;
+  const BasisPick kx = basis_pick(q), kz0 = basis_pick(kh), kz1 = basis_pick(kh + 2);
+  const int64_t np = a.np;
+  const int m = end - beg;
+  const float nanf_ = __int_as_float(0x7fc00000);
+  const int ax = sub < 3 ? sub : 0;  // the axis this lane locates
+
+  // stage-1 location of this warp's first particles, before the barrier that
+  // publishes the staged halo; later iterations load the next particles'
+  // positions before working on the current ones
+  const int step = nwarps * 4;
+  int b4 = warp * 4;
+  double x = 0.0, xn = 0.0;
+  int64_t p = 0, pn = 0;
+  int cl = 0;
+  float tl = 0.f;
+  auto load_mine = [&](int base, int64_t& pp, double& xx) {
+    const int i = base + (lane >> 3);
+    const int ii = i < m ? i : base;
+    pp = a.perm ? a.perm[beg + ii] : (int64_t)(beg + ii);
+    if (sub < 3) xx = a.pos_in[ax * np + pp];
+  };
+  auto locate_mine = [&]() {
+    cl = 0;
+    tl = 0.f;
+    if (sub < 3 && !locate(x, g.inv_h[ax], g.n[ax], cl, tl)) cl = -1;
+  };
+  if (b4 < m) {
+    load_mine(b4, p, x);
+    locate_mine();
+  }
+  if (staged) __syncthreads();
+  for (; b4 < m; b4 += step) {
+    const bool more = b4 + step < m;
+    if (more) load_mine(b4 + step, pn, xn);
+    const bool vi = b4 + (lane >> 3) < m;
+    int cell[3];
+    float t[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cell[d] = __shfl_sync(FULL, cl, gb + d);
+      t[d] = __shfl_sync(FULL, tl, gb + d);
+    }
+    const bool ok = (cell[0] | cell[1] | cell[2]) >= 0;
+    int l[3];
+    const bool inh = staged && ok && in_halo(hg, P0, cell, l);
+    float u[NC], dx[NC], dy[NC], dz[NC];
+    gather_group<Tc, NC, GRAD>(halo, hg.PS, hg.SX, inh, l, cell, t, g, coef, a.scale, q, kh, kx,
+                               kz0, kz1, u, dx, dy, dz);
+    if constexpr (MODE <= 1) {
+      if (vi) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (sub == c) a.vel[(int64_t)c * np + p] = ok ? u[c] : nanf_;
+        if (GRAD && a.grad) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            if (sub == 3) a.grad[((int64_t)c * 3 + 0) * np + p] = ok ? dx[c] : nanf_;
+            if (sub == 4) a.grad[((int64_t)c * 3 + 1) * np + p] = ok ? dy[c] : nanf_;
+            if (sub == 5) a.grad[((int64_t)c * 3 + 2) * np + p] = ok ? dz[c] : nanf_;
+          }
+        }
+        if (sub == 7 && !ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+      }
+    } else {
+      // Heun predictor x* = x + dt u1, located in FP32 relative to the
+      // stage-1 cell by every lane of the group
+      int c2[3];
+      float t2[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float tt = t[d] + (ok ? u[d] * a.dtih[d] : 0.f);
+        float fl = floorf(tt);
+        if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
+        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
+        int c = cell[d] + (int)fl;
+        if (c < 0 || c >= g.n[d]) {
+          c %= g.n[d];
+          if (c < 0) c += g.n[d];
+        }
+        c2[d] = ok ? c : -1;
+      }
+      // a second field's coefficients are not staged
+      const bool inh2 = staged && ok && !a.coef2 && in_halo(hg, P0, c2, l);
+      const Tc* cf2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
+      const float* sc2 = a.coef2 ? a.scale2 : a.scale;
+      float u2[NC];
+      gather_group<Tc, NC, false>(halo, hg.PS, hg.SX, inh2, l, c2, t2, g, cf2, sc2, q, kh, kx, kz0,
+                                  kz1, u2, dx, dy, dz);
+      if (vi && sub < 3) {
+        const float u1d = sel3(u, ax), u2d = sel3(u2, ax);
+        a.pos_out[ax * np + p] = ok ? fma(a.dt * 0.5, (double)(u1d + u2d), x)
+                                    : __longlong_as_double(0x7ff8000000000000ll);
+        if (a.vel) a.vel[ax * np + p] = ok ? u1d : nanf_;
+        if (sub == 0) {
+          if (a.ids_out) a.ids_out[p] = a.ids_in[p];
+          if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+        }
+      }
+    }
+    if (more) {
+      p = pn;
+      x = xn;
+      locate_mine();
+    }
+  }
+}
+
+// One brick: stage its halo (unless it holds fewer than min_stage
+// particles), then process its particles warp by warp.
+template <typename Tc, int NC, int MODE, int KS>
+__device__ __forceinline__ void brick_body_g(const StagedArgs& a, int bin, float4* smem) {
+  const int beg = a.offs[bin], end = a.offs[bin + 1];
+  if (beg >= end) return;
+  const int nbx = a.b.nb[0], nby = a.b.nb[1];
+  const int bzi = bin / (nbx * nby);
+  const int rem = bin - bzi * nbx * nby;
+  const int byi = rem / nbx, bxi = rem - byi * nbx;
+  const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  float4* halo = smem;
+  // a few particles: staging the whole halo would move more bytes than
+  // their stencils
+  const bool staged = end - beg >= a.min_stage;
+  if (staged) {
+    if (a.vec)
+      stage_halo_vec<Tc, NC, KS>(a, coef, P0, halo, false);
+    else
+      stage_halo<Tc, NC>(a, coef, P0, halo, false);
+  }
+  brick_warps<Tc, NC, MODE, KS>(a, beg, end, P0, halo, staged);
+}
+
 template <typename Tc, int NC, int MODE>
 __device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4* smem) {
+  if (is_cube11(a))
+    brick_body_g<Tc, NC, MODE, 11>(a, bin, smem);
+  else
+    brick_body_g<Tc, NC, MODE, 0>(a, bin, smem);
+}
+
+// Phased form of one brick: stage the halo (unless the brick holds fewer than
+// min_stage particles, whose stencils are then read from global memory), then
+// the location / gather / update phases of process_brick.
+template <typename Tc, int NC, int MODE>
+__device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float4* smem) {
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   if (beg >= end) return;
   const int nbx = a.b.nb[0], nby = a.b.nb[1];
@@ -817,8 +1117,19 @@ __device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4*
   const Tc* coef = static_cast<const Tc*>(a.coef);
   float4* halo = smem;
   const Recs R = carve_recs(smem + a.S[2] * a.PS);
+  if (end - beg < a.min_stage) {
+    // an origin far from every cell sends every stencil to global memory
+    const int far[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
+    process_brick<Tc, NC, MODE>(a, beg, end, far, halo, R, nullptr, nullptr, 0);
+    return;
+  }
   // no barrier here: phase A of the first round does not read the halo, and
   // the barrier that follows it also publishes the staged halo
+  if (a.vec && is_cube11(a)) {
+    stage_halo_vec<Tc, NC, 11>(a, coef, P0, halo, false);
+    process_brick<Tc, NC, MODE, 11>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
+    return;
+  }
   if (a.vec)
     stage_halo_vec<Tc, NC>(a, coef, P0, halo, false);
   else
@@ -830,13 +1141,21 @@ __device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4*
 template <typename Tc, int NC, int MODE>
 __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
   extern __shared__ float4 smem[];
+  brick_phased<Tc, NC, MODE>(a, blockIdx.x, smem);
+}
+
+// The warp-autonomous form ("brick_kernel" 3): no particle records, no block
+// barrier after the staging.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged_warp(StagedArgs a) {
+  extern __shared__ float4 smem[];
   brick_body<Tc, NC, MODE>(a, blockIdx.x, smem);
 }
 
 // Many fields in one launch: block b handles global brick b; the field is the
 // last f with bin_base[f] <= b, and its parameters are copied to shared memory.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3)
+__global__ void __launch_bounds__(256, 3)
     interp_staged_batch(const StagedArgs* __restrict__ tab, const int* __restrict__ bin_base,
                         int nfields) {
   extern __shared__ float4 smem[];
@@ -854,7 +1173,7 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3)
     local_bin = b - bin_base[lo];
   }
   __syncthreads();
-  brick_body<Tc, NC, MODE>(sa, local_bin, smem);
+  brick_phased<Tc, NC, MODE>(sa, local_bin, smem);
 }
 
 // ------------------------------------------------- thread per particle ----
@@ -1262,6 +1581,7 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   const int qx = (a->S[0] + V - 1) / (V > 0 ? V : 1);
   vec = vec && qx <= 4 && (a->b.nb[0] - 1) * a->b.B[0] + qx * V <= a->g.rx;
   a->vec = vec ? 1 : 0;
+  a->min_stage = tuning().brick_min_stage;
   *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + kRecBytes;
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
@@ -1302,6 +1622,18 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
     }
     tk<<<(unsigned)a.b.nbins, 64, hs, st>>>(a);
     return check_launch("interp_thread");
+  }
+  if (tuning().brick_kernel == 3) {
+    auto wk = interp_staged_warp<Tc, NC, MODE>;
+    const size_t hs = (size_t)a.S[2] * a.PS * sizeof(float4);
+    if (hs > 48 * 1024) {
+      ps_status rc = check_cuda(
+          cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs),
+          "warp-form smem attribute");
+      if (rc) return rc;
+    }
+    wk<<<(unsigned)a.b.nbins, kThreads, hs, st>>>(a);
+    return check_launch("interp_staged_warp");
   }
   auto kern = interp_staged<Tc, NC, MODE>;
   if (smem > 48 * 1024) {

@@ -73,6 +73,7 @@ ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* o
 struct Tuning {
   int brick_kernel = 0;       // 0: one CTA per brick; 1: persistent, pipelined
   int brick_ctas_per_sm = 3;  // resident CTAs per SM of the persistent form
+  int brick_min_stage = 8;    // per-brick kernel: fewer particles skip the halo
 };
 Tuning& tuning();
 int sm_count();

@@ -412,3 +412,28 @@ def test_rk2_every_autotune_candidate(kernel, dtype, brick_kernel):
             ids = tr.ids.cpu().numpy()
             assert np.abs(tr.vel.cpu().numpy() - u1_ref[:, ids]).max() <= tol_u, brick
             assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= dt * tol_u + 1e-14
+
+
+@pytest.mark.parametrize("min_stage", [0, 8, 1 << 20])
+def test_sparse_brick_knob(min_stage):
+    # bricks below the threshold gather from global memory instead of the
+    # staged halo; results stay within the same bars either way
+    old = ps.ps_tune_get("brick_min_stage")
+    try:
+        ps.ps_tune_set("brick_min_stage", min_stage)
+        n = (64, 32, 40)
+        field, pos, cref = _case(n, 6000, seed=131, spread=1.2)  # ~3 per 8^3 brick
+        ref = oracle.interp(cref, pos)
+        sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+        pg = torch.from_numpy(pos).to(DEV)
+        bins = ps.bin_particles(n, (8, 8, 8), pg)
+        assert rel_err(sf.interp(pg, bins=bins).cpu().numpy(), ref) <= 1e-5
+        dt = 1e-2
+        new_ref, u1_ref = oracle.rk2_step(cref, pos, dt)
+        rms = np.sqrt((u1_ref ** 2).mean())
+        tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=(8, 8, 8))
+        tr.step(dt)
+        ids = tr.ids.cpu().numpy()
+        assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= dt * 1e-5 * rms + 1e-14
+    finally:
+        ps.ps_tune_set("brick_min_stage", old)
