@@ -40,6 +40,9 @@
  *              elements (nx+3 rounded up to 16 bytes; the tail is written as
  *              zero) so that every row starts on a 16-byte boundary.  Storage
  *              offset of (c, Pz, Py, Px) is ((c*(nz+3) + Pz)*(ny+3) + Py)*rx + Px.
+ *              PS_F32X4: [nz+3][ny+3][nx+3][4] F32, node (Pz, Py, Px) holds
+ *              (u, v, w, 0) at float offset ((Pz*(ny+3) + Py)*(nx+3) + Px)*4.
+ *              (rx = nx+3 nodes.)
  *   scale      [ncomp][nz+3][ny+3] F32, only for BF16/F16 coefficients: the
  *              value of a coefficient is stored * scale of its x-line; scales
  *              are powers of two, so scaling itself is exact.
@@ -68,7 +71,12 @@ typedef enum {
   PS_ERR_DEVICE_STATUS = 6  /* ps_status_read found a device-side anomaly   */
 } ps_status;
 
-typedef enum { PS_F32 = 0, PS_BF16 = 1, PS_F16 = 2, PS_F64 = 3 } ps_dtype;
+/* PS_F32X4 (coefficients only): the three components of a node stored
+ * together as 16 bytes (u, v, w, 0); the array is [nz+3][ny+3][nx+3][4]
+ * float, so one 16-byte load brings a node and a brick's halo is one box of
+ * consecutive rows.  Requires ncomp == 3.  A storage choice, not part of the
+ * method. */
+typedef enum { PS_F32 = 0, PS_BF16 = 1, PS_F16 = 2, PS_F64 = 3, PS_F32X4 = 4 } ps_dtype;
 
 /* device status codes (status[0]) */
 #define PS_DEV_OK 0
@@ -85,7 +93,8 @@ const char* ps_last_error(void);
 /* Library version string. */
 const char* ps_version(void);
 /* Row pitch rx (elements) of a padded coefficient array for nx nodes along x:
- * nx+3 rounded up to a multiple of 16 bytes.  0 for a bad argument.  Part of
+ * nx+3 rounded up to a multiple of 16 bytes (PS_F32X4: nx+3 nodes of 16
+ * bytes).  0 for a bad argument.  Part of
  * the storage layout, not of the method (the paper stores N+3 per line). */
 int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
 
@@ -116,7 +125,8 @@ ps_status ps_status_read(const int32_t* status, int32_t* host_out, void* stream)
 /* x, y and z lines of every component, and store the N+3 padded           */
 /* coefficients per axis.  The result is the exact inverse up to rounding;  */
 /* the order of the three directions is immaterial in exact arithmetic.     */
-/*   field_t: PS_F32 or PS_F64.  coef_t: PS_F32, PS_F64, PS_BF16, PS_F16.   */
+/*   field_t: PS_F32 or PS_F64.  coef_t: PS_F32, PS_F64, PS_BF16, PS_F16,   */
+/*   or PS_F32X4 (ncomp == 3).                                              */
 /*   Arithmetic is FP64 when coef_t is PS_F64, else FP32.                   */
 /*   scale: required for BF16/F16 (per x-line power-of-two scale), else     */
 /*   ignored.  field and coef must not overlap.  ncomp in [1, 16].          */

@@ -18,13 +18,39 @@ from typing import Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import (PS_BF16, PS_F16, PS_F32, PS_F64, PS_OK, PsGrid)
+from ._abi import (PS_BF16, PS_F16, PS_F32, PS_F32X4, PS_F64, PS_OK, PsGrid)
 
 TWO_PI = 2.0 * math.pi
 DEFAULT_L = (TWO_PI, TWO_PI, TWO_PI)
 
 _DT = {torch.float32: PS_F32, torch.float64: PS_F64, torch.bfloat16: PS_BF16,
        torch.float16: PS_F16}
+
+# Coefficient storage with the three components of a node interleaved as 16
+# bytes (u, v, w, 0): a float32 tensor [nz+3][ny+3][nx+3][4] (PS_F32X4).
+F32X4 = "f32x4"
+
+
+def _dt_code(dtype) -> int:
+    return PS_F32X4 if dtype == F32X4 else _DT[dtype]
+
+
+def _is_node4(coef: torch.Tensor) -> bool:
+    # planar rows hold >= 8 elements, so a last extent of 4 is a node array
+    return coef.dtype == torch.float32 and coef.dim() == 4 and coef.shape[-1] == 4
+
+
+def _coef_type(coef: torch.Tensor) -> int:
+    return PS_F32X4 if _is_node4(coef) else _DT[coef.dtype]
+
+
+def coef_kind(coef: torch.Tensor):
+    """The coefficient dtype argument a tensor corresponds to (F32X4 or a torch dtype)."""
+    return F32X4 if _is_node4(coef) else coef.dtype
+
+
+def _ncomp_of(coef: torch.Tensor) -> int:
+    return 3 if _is_node4(coef) else coef.shape[0]
 
 
 class PSError(RuntimeError):
@@ -89,16 +115,25 @@ def _brick_arr(brick):
 def coef_row_pitch(nx: int, dtype: torch.dtype) -> int:
     """Row pitch (elements) of a padded coefficient array: nx+3 rounded up to
     16 bytes (ps_coef_row_pitch)."""
-    return int(_lib().ps_coef_row_pitch(int(nx), _DT[dtype]))
+    return int(_lib().ps_coef_row_pitch(int(nx), _dt_code(dtype)))
 
 
-def coef_shape(n, ncomp: int, dtype: torch.dtype):
-    """Storage shape [ncomp][nz+3][ny+3][pitch] of padded coefficients."""
+def coef_shape(n, ncomp: int, dtype):
+    """Storage shape [ncomp][nz+3][ny+3][pitch] of padded coefficients, or
+    [nz+3][ny+3][nx+3][4] for F32X4 (ncomp 3)."""
+    if dtype == F32X4:
+        if ncomp != 3:
+            raise ValueError("F32X4 coefficients hold three components")
+        return (n[2] + 3, n[1] + 3, n[0] + 3, 4)
     return (ncomp, n[2] + 3, n[1] + 3, coef_row_pitch(n[0], dtype))
 
 
+def _storage_dtype(dtype) -> torch.dtype:
+    return torch.float32 if dtype == F32X4 else dtype
+
+
 def _check_coef_shape(coef: torch.Tensor, n):
-    want = coef_shape(n, coef.shape[0], coef.dtype)
+    want = coef_shape(n, _ncomp_of(coef), coef_kind(coef))
     if tuple(coef.shape) != want:
         raise ValueError(f"coef has shape {tuple(coef.shape)}, grid {tuple(n)} needs {want}")
 
@@ -143,7 +178,8 @@ def ps_status_read(status: torch.Tensor, stream=None, raise_on_error: bool = Fal
 def ps_spline_coeffs_workspace_size(n, ncomp: int, coef_dtype: torch.dtype,
                                     L=DEFAULT_L) -> int:
     g = make_grid(n, L)
-    return int(_lib().ps_spline_coeffs_workspace_size(ctypes.byref(g), ncomp, _DT[coef_dtype]))
+    return int(_lib().ps_spline_coeffs_workspace_size(ctypes.byref(g), ncomp,
+                                                       _dt_code(coef_dtype)))
 
 
 def ps_spline_coeffs(field: torch.Tensor, coef: torch.Tensor, scale: Optional[torch.Tensor] = None,
@@ -159,7 +195,7 @@ def ps_spline_coeffs(field: torch.Tensor, coef: torch.Tensor, scale: Optional[to
     g = make_grid(n, L)
     ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     _check(_lib().ps_spline_coeffs(ctypes.byref(g), ncomp, _DT[field.dtype], _ptr(field),
-                                   _DT[coef.dtype], _ptr(coef), _ptr(scale), _ptr(ws), ws_bytes,
+                                   _coef_type(coef), _ptr(coef), _ptr(scale), _ptr(ws), ws_bytes,
                                    _stream(stream)))
 
 
@@ -196,7 +232,7 @@ def ps_interp(coef: torch.Tensor, n, pos: torch.Tensor, vel: torch.Tensor,
     """Operations 2-3 (Sec. 2.2, Eq. (spline)) at positions pos [3][np] -> vel [ncomp][np].
     n = (nx, ny, nz) of the grid the coefficients belong to."""
     _check_coef_shape(coef, n)
-    ncomp = coef.shape[0]
+    ncomp = _ncomp_of(coef)
     np_ = pos.shape[1]
     _dev(coef, "coef")
     _dev(pos, "pos", torch.float64)
@@ -207,7 +243,7 @@ def ps_interp(coef: torch.Tensor, n, pos: torch.Tensor, vel: torch.Tensor,
     _dev(grad, "grad", torch.float32, ncomp * 3 * np_)
     _dev(status, "status", torch.int32, 4)
     g = make_grid(n, L)
-    _check(_lib().ps_interp(ctypes.byref(g), ncomp, _DT[coef.dtype], _ptr(coef), _ptr(scale), np_,
+    _check(_lib().ps_interp(ctypes.byref(g), ncomp, _coef_type(coef), _ptr(coef), _ptr(scale), np_,
                             _ptr(pos), _ptr(perm), _ptr(bin_offsets), _brick_arr(brick),
                             _ptr(vel), _ptr(grad), _ptr(status), _stream(stream)))
 
@@ -218,7 +254,7 @@ def ps_interp_backward(coef: torch.Tensor, n, pos: torch.Tensor, g_vel: torch.Te
                        L=DEFAULT_L, stream=None):
     """Adjoint of ps_interp and of the coefficient solve."""
     _check_coef_shape(coef, n)
-    ncomp = coef.shape[0]
+    ncomp = _ncomp_of(coef)
     np_ = pos.shape[1]
     _dev(coef, "coef")
     _dev(pos, "pos", torch.float64)
@@ -227,7 +263,7 @@ def ps_interp_backward(coef: torch.Tensor, n, pos: torch.Tensor, g_vel: torch.Te
     _dev(g_field, "g_field", torch.float32, ncomp * n[0] * n[1] * n[2])
     _dev(status, "status", torch.int32, 4)
     g = make_grid(n, L)
-    _check(_lib().ps_interp_backward(ctypes.byref(g), ncomp, _DT[coef.dtype], _ptr(coef),
+    _check(_lib().ps_interp_backward(ctypes.byref(g), ncomp, _coef_type(coef), _ptr(coef),
                                      _ptr(scale), np_, _ptr(pos), _ptr(g_vel), _ptr(g_pos),
                                      _ptr(g_field), None, 0, _ptr(status), _stream(stream)))
 
@@ -256,7 +292,9 @@ def ps_rk2_step(coef_n: torch.Tensor, n, pos: torch.Tensor, dt: float,
     _dev(status, "status", torch.int32, 4)
     g = make_grid(n, L)
     ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
-    _check(_lib().ps_rk2_step(ctypes.byref(g), _DT[coef_n.dtype], _ptr(coef_n), _ptr(coef_np1),
+    if coef_np1 is not None and _coef_type(coef_np1) != _coef_type(coef_n):
+        raise ValueError("coef_np1 must have the storage of coef_n")
+    _check(_lib().ps_rk2_step(ctypes.byref(g), _coef_type(coef_n), _ptr(coef_n), _ptr(coef_np1),
                               _ptr(scale_n), _ptr(scale_np1), np_, _ptr(pos), _ptr(ids),
                               _ptr(vel_out), float(dt), _brick_arr(brick), 1 if rebin else 0,
                               _ptr(bin_offsets), _ptr(ws), ws_bytes, _ptr(status),
@@ -280,11 +318,14 @@ class SplineField:
         self.scale = scale
         self.L = tuple(float(v) for v in L)
         self.n = tuple(int(v) for v in n)
-        self.ncomp = coef.shape[0]
+        self.ncomp = _ncomp_of(coef)
         _check_coef_shape(coef, self.n)
 
     def padded(self) -> torch.Tensor:
-        """[ncomp][nz+3][ny+3][nx+3] view (the row pitch tail dropped)."""
+        """[ncomp][nz+3][ny+3][nx+3] view (the row pitch tail dropped; for F32X4
+        the component-major view of the interleaved nodes)."""
+        if _is_node4(self.coef):
+            return self.coef.permute(3, 0, 1, 2)[:3]
         return self.coef[..., : self.n[0] + 3]
 
     @classmethod
@@ -294,14 +335,14 @@ class SplineField:
         n = grid_of_field(field)
         ncomp = field.shape[0]
         if out is None:
-            coef = torch.empty(coef_shape(n, ncomp, coef_dtype), dtype=coef_dtype,
-                               device=field.device)
+            coef = torch.empty(coef_shape(n, ncomp, coef_dtype),
+                               dtype=_storage_dtype(coef_dtype), device=field.device)
             scale = None
             if coef_dtype in (torch.bfloat16, torch.float16):
                 scale = torch.empty((ncomp, n[2] + 3, n[1] + 3), dtype=torch.float32,
                                     device=field.device)
             out = cls(coef, scale, n, L)
-        need = ps_spline_coeffs_workspace_size(n, ncomp, out.coef.dtype, L)
+        need = ps_spline_coeffs_workspace_size(n, ncomp, coef_kind(out.coef), L)
         if need and (ws is None or ws.numel() < need):
             ws = workspace(need, field.device)
         ps_spline_coeffs(field, out.coef, out.scale, ws if need else None, L=L, stream=stream)
@@ -432,7 +473,7 @@ class BatchPlan:
         self.coef_dtype = coef_dtype
         self._plan = ctypes.c_void_p()
         _check(_lib().ps_batch_plan(self.nfields, arr, ctypes.cast(nps_arr, ctypes.c_void_p),
-                                    _DT[coef_dtype], _brick_arr(brick),
+                                    _dt_code(coef_dtype), _brick_arr(brick),
                                     tune_cache.encode() if tune_cache else None,
                                     ctypes.byref(self._plan)))
         self.np_total = int(_lib().ps_batch_num_particles(self._plan))

@@ -51,6 +51,7 @@ size_t dtype_size(ps_dtype t) {
     case PS_F64: return 8;
     case PS_BF16: return 2;
     case PS_F16: return 2;
+    case PS_F32X4: return 16;
   }
   return 0;
 }
@@ -118,6 +119,11 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
     tuning().brick_min_stage = (int)value;
     return PS_OK;
   }
+  if (!strcmp(key, "node_tma")) {
+    if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "node_tma is 0 or 1");
+    tuning().node_tma = (int)value;
+    return PS_OK;
+  }
   if (!strcmp(key, "brick_ctas_per_sm")) {
     if (value < 1 || value > 8) return fail(PS_ERR_INVALID_ARG, "brick_ctas_per_sm in [1, 8]");
     tuning().brick_ctas_per_sm = (int)value;
@@ -131,6 +137,7 @@ extern "C" int64_t ps_tune_get(const char* key) {
   if (!strcmp(key, "brick_kernel")) return tuning().brick_kernel;
   if (!strcmp(key, "brick_ctas_per_sm")) return tuning().brick_ctas_per_sm;
   if (!strcmp(key, "brick_min_stage")) return tuning().brick_min_stage;
+  if (!strcmp(key, "node_tma")) return tuning().node_tma;
   return -1;
 }
 

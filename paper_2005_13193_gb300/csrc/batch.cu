@@ -77,7 +77,7 @@ void layout(ps_plan* p) {
   p->off_pos = take(3 * np * sizeof(double));
   p->off_ids = take(np * sizeof(int64_t));
   size_t quant = 0;
-  if (p->coef_t == PS_BF16 || p->coef_t == PS_F16)
+  if (p->coef_t == PS_BF16 || p->coef_t == PS_F16 || p->coef_t == PS_F32X4)
     for (int f = 0; f < p->nfields; ++f)
       quant = std::max(quant, ps_spline_coeffs_workspace_size(&p->grids[f], 3, p->coef_t));
   p->off_quant = take(quant);
@@ -98,8 +98,8 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
   *out = nullptr;
   if (nfields < 1 || nfields > 4096 || !grids || !nps)
     return fail(PS_ERR_INVALID_ARG, "need 1..4096 fields with grids and particle counts");
-  if (coef_t != PS_F32 && coef_t != PS_BF16 && coef_t != PS_F16)
-    return fail(PS_ERR_UNSUPPORTED, "batched runs use F32, BF16 or F16 coefficients");
+  if (coef_t != PS_F32 && coef_t != PS_BF16 && coef_t != PS_F16 && coef_t != PS_F32X4)
+    return fail(PS_ERR_UNSUPPORTED, "batched runs use F32, F32X4, BF16 or F16 coefficients");
   ps_plan* p = new ps_plan();
   p->nfields = nfields;
   p->coef_t = coef_t;
@@ -253,9 +253,10 @@ extern "C" ps_status ps_batch_run(ps_plan* p, const ps_batch_field* fields, int 
   if (solve) {
     const size_t qbytes = p->ws_bytes - p->off_quant;
     for (int f = 0; f < p->nfields; ++f) {
+      const bool inter = quant || p->coef_t == PS_F32X4;
       rc = ps_spline_coeffs(&p->grids[f], 3, PS_F32, fields[f].field, p->coef_t, fields[f].coef,
-                            fields[f].scale, quant ? at<char>(ws, p->off_quant) : nullptr,
-                            quant ? qbytes : 0, stream);
+                            fields[f].scale, inter ? at<char>(ws, p->off_quant) : nullptr,
+                            inter ? qbytes : 0, stream);
       if (rc) return rc;
     }
   }

@@ -22,6 +22,11 @@
 #include <cstring>
 #include <type_traits>
 
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -50,11 +55,18 @@ __device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
                                                               const float* scale,
                                                               const GridArgs& g, int c,
                                                               int Pz, int Py, int Px) {
-  const int64_t m1 = g.m[1], m2 = g.m[2];
-  const int64_t row = ((int64_t)c * m2 + Pz) * m1 + Py;
-  typename AccOf<Tc>::type v = CoefLoad<Tc>::ld(coef + row * g.rx + Px);
-  if (IsQuant<Tc>::value) v *= __ldg(scale + row);
-  return v;
+  if constexpr (IsNode4<Tc>::value) {
+    // component c of node (Pz, Py, Px); the node's other components share
+    // the 16-byte segment
+    const int64_t node = ((int64_t)Pz * g.m[1] + Py) * g.rx + Px;
+    return __ldg(reinterpret_cast<const float*>(coef + node) + c);
+  } else {
+    const int64_t m1 = g.m[1], m2 = g.m[2];
+    const int64_t row = ((int64_t)c * m2 + Pz) * m1 + Py;
+    typename AccOf<Tc>::type v = CoefLoad<Tc>::ld(coef + row * g.rx + Px);
+    if (IsQuant<Tc>::value) v *= __ldg(scale + row);
+    return v;
+  }
 }
 
 // The first three lanes of each group of G lanes locate one axis each; the
@@ -330,6 +342,7 @@ struct StagedArgs {
   int PS;       // plane stride in float4 units: >= SX*S[1], = 4 (mod 8)
   int vec;      // 1: halo rows are whole 16-byte vectors inside the array
   int min_stage;  // bricks with fewer particles gather from global memory
+  int tma;        // 1: the node halo is one tensor copy described by tmap
   const void* coef;
   const float* scale;
   const void* coef2;  // second-stage field of an RK2 step; NULL = same as coef
@@ -346,6 +359,7 @@ struct StagedArgs {
   double dt;
   float dtih[3];  // dt * n/L per axis
   int32_t* status;
+  CUtensorMap tmap;  // PS_F32X4 halo box (valid when tma == 1)
 };
 
 // Halo geometry (extents, row and plane strides in float4 units).  KS > 0
@@ -362,8 +376,57 @@ template <> struct HaloGeo<11> {
   static constexpr int Sx = 11, Sy = 11, Sz = 11, SX = 11, PS = 124;
   __device__ __forceinline__ explicit HaloGeo(const StagedArgs&) {}
 };
+// The same halo with 12-point rows: the layout of a tensor copy of a node
+// halo, whose plane of 12 x 11 points is 132 = 4 (mod 8) float4 long.
+template <> struct HaloGeo<12> {
+  static constexpr int Sx = 11, Sy = 11, Sz = 11, SX = 12, PS = 132;
+  __device__ __forceinline__ explicit HaloGeo(const StagedArgs&) {}
+};
 __device__ __forceinline__ bool is_cube11(const StagedArgs& a) {
   return a.S[0] == 11 && a.S[1] == 11 && a.S[2] == 11 && a.SX == 11 && a.PS == 124;
+}
+__device__ __forceinline__ bool is_cube11_rows12(const StagedArgs& a) {
+  return a.S[0] == 11 && a.S[1] == 11 && a.S[2] == 11 && a.SX == 12 && a.PS == 132;
+}
+
+// ------------------------------------------------- tensor-copy staging ----
+// One thread arms an mbarrier with the byte count of the box and issues the
+// tensor copy of the brick's node halo; the copy completes the barrier's
+// phase, after which every thread that waited on it sees the data.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void tma_issue_halo(const CUtensorMap* map, float4* dst,
+                                               unsigned long long* mbar, const int P0[3],
+                                               unsigned bytes) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(0), "r"(P0[0]), "r"(P0[1]), "r"(P0[2]),
+      "r"(smem_u32(mbar))
+      : "memory");
+}
+// Waits for phase 0 of the barrier, giving up after about 2^31 clocks (about a
+// second); returns whether the phase completed.
+__device__ __forceinline__ bool tma_wait(unsigned long long* mbar) {
+  const unsigned a = smem_u32(mbar);
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
 }
 
 // Padded index (any integer) -> interior padded index of the same node.
@@ -407,8 +470,12 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
       for (int c = 0; c < NC; ++c) {
         float x = 0.f;
         if (act[u]) {
-          x = (float)CoefLoad<Tc>::ld(coef + c * cs + row * m0 + Px);
-          if (IsQuant<Tc>::value) x *= __ldg(a.scale + c * m2 * m1 + row);
+          if constexpr (IsNode4<Tc>::value) {
+            x = __ldg(reinterpret_cast<const float*>(coef + row * m0 + Px) + c);
+          } else {
+            x = (float)CoefLoad<Tc>::ld(coef + c * cs + row * m0 + Px);
+            if (IsQuant<Tc>::value) x *= __ldg(a.scale + c * m2 * m1 + row);
+          }
         }
         v[u][c] = x;
       }
@@ -457,9 +524,42 @@ template <typename H> struct Vec16Half {
 template <> struct Vec16<__nv_bfloat16> : Vec16Half<__nv_bfloat16> {};
 template <> struct Vec16<__half> : Vec16Half<__half> {};
 
+template <typename Tc, int NC, int KS>
+__device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
+                                                      const Tc* __restrict__ coef,
+                                                      const int P0[3], float4* halo, bool sync);
+
+// Node coefficients: one 16-byte load and store per halo point, consecutive
+// threads along the rows.
+template <int KS>
+__device__ __forceinline__ void stage_nodes(const StagedArgs& a, const float4* __restrict__ coef,
+                                            const int P0[3], float4* halo) {
+  const HaloGeo<KS> hg(a);
+  const int64_t rx = a.g.rx, m1 = a.g.m[1];
+  const float4* b0 = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
+  const int nrow = hg.Sy * hg.Sz, npts = nrow * hg.Sx;
+  for (int it = threadIdx.x; it < npts; it += blockDim.x) {
+    const int r = it / hg.Sx, x = it - r * hg.Sx;
+    const int lz = r / hg.Sy, ly = r - lz * hg.Sy;
+    halo[lz * hg.PS + ly * hg.SX + x] = __ldg(b0 + ((int64_t)lz * m1 + ly) * rx + x);
+  }
+}
+
 template <typename Tc, int NC, int KS = 0>
 __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __restrict__ coef,
                                                const int P0[3], float4* halo, bool sync = true) {
+  if constexpr (IsNode4<Tc>::value) {
+    stage_nodes<KS>(a, coef, P0, halo);
+    if (sync) __syncthreads();
+  } else {
+    stage_halo_vec_planar<Tc, NC, KS>(a, coef, P0, halo, sync);
+  }
+}
+
+template <typename Tc, int NC, int KS>
+__device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
+                                                      const Tc* __restrict__ coef,
+                                                      const int P0[3], float4* halo, bool sync) {
   constexpr int V = Vec16<Tc>::V;
   constexpr int U = 8 / V;               // rows in flight per thread
   const GridArgs& g = a.g;
@@ -699,8 +799,10 @@ template <typename Tc, int NC, int MODE, int KS = 0>
 __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int end,
                                               const int P0[3], const float4* halo,
                                               const Recs& R, double* pbuf,
-                                              unsigned char* raw_next, int next_bin) {
+                                              unsigned char* raw_next, int next_bin,
+                                              unsigned long long* mbar = nullptr) {
   constexpr bool GRAD = MODE == 1;
+  bool copied = true;  // the halo's tensor copy completed (or there is none)
   const GridArgs& g = a.g;
   const Tc* coef = static_cast<const Tc*>(a.coef);
   const int tid = threadIdx.x, lane = tid & 31;
@@ -737,7 +839,14 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       }
     }
     __syncthreads();
-    if (raw_next && cb == beg) issue_brick<Tc, NC>(a, next_bin, raw_next, pbuf);
+    if constexpr (!IsNode4<Tc>::value)
+      if (raw_next && cb == beg) issue_brick<Tc, NC>(a, next_bin, raw_next, pbuf);
+    // the barrier above also ordered the mbarrier's initialisation before
+    // these waits; a copy that never completes is reported, not waited for
+    if (mbar && cb == beg && !tma_wait(mbar)) {
+      copied = false;
+      if (threadIdx.x == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
+    }
     // phase B: gathers, 8 lanes per particle; the loop is uniform per warp
     // (the butterfly uses full-warp shuffles), idle groups redo record b4
     for (int b4 = warp * 4; b4 < m; b4 += nwarps * 4) {
@@ -824,6 +933,8 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
     __syncthreads();
     }  // MODE == 2
   }
+  // a copy still in flight must land before the block's memory is released
+  if (!copied) tma_wait(mbar);
 }
 
 // ------------------------------------------------ warp-autonomous form ----
@@ -1105,7 +1216,7 @@ __device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4*
 // Phased form of one brick: stage the halo (unless the brick holds fewer than
 // min_stage particles, whose stencils are then read from global memory), then
 // the location / gather / update phases of process_brick.
-template <typename Tc, int NC, int MODE>
+template <typename Tc, int NC, int MODE, bool TMA = false>
 __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float4* smem) {
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   if (beg >= end) return;
@@ -1123,11 +1234,28 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
     process_brick<Tc, NC, MODE>(a, beg, end, far, halo, R, nullptr, nullptr, 0);
     return;
   }
+  if constexpr (TMA && IsNode4<Tc>::value) {
+    // a kernel argument holds the tensor map; the destination must be
+    // 128-byte aligned
+    if (a.tma && is_cube11_rows12(a) && (smem_u32(halo) & 127) == 0) {
+      __shared__ __align__(8) unsigned long long mbar;
+      if (threadIdx.x == 0)
+        tma_issue_halo(&a.tmap, halo, &mbar, P0,
+                       (unsigned)(sizeof(float4) * HaloGeo<12>::PS * HaloGeo<12>::Sz));
+      process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar);
+      return;
+    }
+  }
   // no barrier here: phase A of the first round does not read the halo, and
   // the barrier that follows it also publishes the staged halo
   if (a.vec && is_cube11(a)) {
     stage_halo_vec<Tc, NC, 11>(a, coef, P0, halo, false);
     process_brick<Tc, NC, MODE, 11>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
+    return;
+  }
+  if (a.vec && is_cube11_rows12(a)) {
+    stage_halo_vec<Tc, NC, 12>(a, coef, P0, halo, false);
+    process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
     return;
   }
   if (a.vec)
@@ -1137,17 +1265,20 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
   process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
 }
 
-// MODE 0: vel; 1: vel + grad; 2: fused Heun step.  One CTA per brick.
+// MODE 0: vel; 1: vel + grad; 2: fused Heun step.  One CTA per brick.  The
+// argument block is a grid constant so that its tensor map can be named by
+// the tensor copy.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged(StagedArgs a) {
-  extern __shared__ float4 smem[];
-  brick_phased<Tc, NC, MODE>(a, blockIdx.x, smem);
+__global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4)
+    interp_staged(const __grid_constant__ StagedArgs a) {
+  extern __shared__ __align__(128) float4 smem_a128[];
+  brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128);
 }
 
 // The warp-autonomous form ("brick_kernel" 3): no particle records, no block
 // barrier after the staging.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 4 ? 4 : 3) interp_staged_warp(StagedArgs a) {
+__global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4) interp_staged_warp(StagedArgs a) {
   extern __shared__ float4 smem[];
   brick_body<Tc, NC, MODE>(a, blockIdx.x, smem);
 }
@@ -1542,12 +1673,14 @@ ps_status with_coef_type(ps_dtype t, F&& f) {
     case PS_F64: return f(double{});
     case PS_BF16: return f(__nv_bfloat16{});
     case PS_F16: return f(__half{});
+    case PS_F32X4: return f(float4{});
   }
   return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype %d", (int)t);
 }
 
 ps_status check_coef(ps_dtype coef_t, const void* coef, const float* scale) {
-  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16)
+  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16 &&
+      coef_t != PS_F32X4)
     return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype %d", (int)coef_t);
   if (!coef) return fail(PS_ERR_INVALID_ARG, "coef is NULL");
   if ((coef_t == PS_BF16 || coef_t == PS_F16) && !scale)
@@ -1580,16 +1713,73 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   for (int d = 0; d < 3; ++d) vec = vec && grid->n[d] % a->b.B[d] == 0;
   const int qx = (a->S[0] + V - 1) / (V > 0 ? V : 1);
   vec = vec && qx <= 4 && (a->b.nb[0] - 1) * a->b.B[0] + qx * V <= a->g.rx;
+  if (coef_t == PS_F32X4) {
+    // node rows: any x offset is a whole 16-byte node; the halo stays inside
+    // the padded array when the bricks tile the grid
+    vec = E == 0;
+    for (int d = 0; d < 3; ++d) vec = vec && grid->n[d] % a->b.B[d] == 0;
+    // rows padded so that a plane is 4 (mod 8) nodes long: the layout a
+    // tensor copy of the halo box produces, conflict-free for the gathers
+    for (int sx = a->S[0]; vec && sx < a->S[0] + 8; ++sx)
+      if ((sx * a->S[1]) % 8 == 4) {
+        a->SX = sx;
+        a->PS = sx * a->S[1];
+        break;
+      }
+  }
   a->vec = vec ? 1 : 0;
+  a->tma = 0;
   a->min_stage = tuning().brick_min_stage;
   *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + kRecBytes;
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
 }
 
+// Tensor map of the node halo box (4 floats x SX nodes x S[1] rows x S[2]
+// planes) over the PS_F32X4 array; the driver's encoder is looked up once.
+bool encode_node_halo_map(StagedArgs* a) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static bool looked = false;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!looked) {
+      looked = true;
+      cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+      void* fn = nullptr;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                           &q) == cudaSuccess &&
+          q == cudaDriverEntryPointSuccess)
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+      else
+        cudaGetLastError();
+    }
+  }
+  if (!encode) return false;
+  const GridArgs& g = a->g;
+  const cuuint64_t dims[4] = {4, (cuuint64_t)g.rx, (cuuint64_t)g.m[1], (cuuint64_t)g.m[2]};
+  const cuuint64_t strides[3] = {16, (cuuint64_t)g.rx * 16, (cuuint64_t)g.rx * g.m[1] * 16};
+  const cuuint32_t box[4] = {4, (cuuint32_t)a->SX, (cuuint32_t)a->S[1], (cuuint32_t)a->S[2]};
+  const cuuint32_t unit[4] = {1, 1, 1, 1};
+  return encode(&a->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(a->coef), dims,
+                strides, box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Use a tensor copy for the halo when the coefficients are nodes, the halo
+// rows fit the copy layout and the array is 16-byte aligned.
+void attach_tma(StagedArgs* a, ps_dtype coef_t) {
+  a->tma = 0;
+  if (coef_t != PS_F32X4 || !a->vec || !tuning().node_tma) return;
+  if ((a->SX * a->S[1]) % 8 != 4 || a->SX > 256 || a->S[1] > 256 || a->S[2] > 256) return;
+  if (reinterpret_cast<uintptr_t>(a->coef) & 15) return;
+  a->tma = encode_node_halo_map(a) ? 1 : 0;
+}
+
 template <typename Tc, int NC, int MODE>
 ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
-  if constexpr (sizeof(Tc) != 8) {
+  if constexpr (sizeof(Tc) == 4 || sizeof(Tc) == 2) {
     if (a.vec && tuning().brick_kernel == 1) {
       constexpr int V = 16 / (int)sizeof(Tc);
       const int qx = (a.S[0] + V - 1) / V;
@@ -1749,6 +1939,7 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
   a.scale = s0;
   a.coef2 = c1;
   a.scale2 = s1;
+  attach_tma(&a, coef_t);
   a.np = np;
   a.pos_in = pos_in;
   a.pos_out = pos_out;
@@ -1781,6 +1972,8 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
+  if (coef_t == PS_F32X4 && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "PS_F32X4 coefficients need ncomp == 3");
   if ((rc = check_coef(coef_t, coef, scale))) return rc;
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np == 0) return PS_OK;
@@ -1817,6 +2010,7 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   if ((rc = fill_staged(grid, coef_t, brick, 0, &a, &smem))) return rc;
   a.coef = coef;
   a.scale = scale;
+  attach_tma(&a, coef_t);
   a.np = np;
   a.pos_in = pos;
   a.perm = perm;
@@ -1846,6 +2040,8 @@ extern "C" ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
+  if (coef_t == PS_F32X4 && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "PS_F32X4 coefficients need ncomp == 3");
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np > 0 && (!pos || !g_vel)) return fail(PS_ERR_INVALID_ARG, "pos and g_vel required");
   cudaStream_t st = as_stream(stream);

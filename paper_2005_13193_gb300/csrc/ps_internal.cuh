@@ -74,6 +74,7 @@ struct Tuning {
   int brick_kernel = 0;       // 0: one CTA per brick; 1: persistent, pipelined
   int brick_ctas_per_sm = 3;  // resident CTAs per SM of the persistent form
   int brick_min_stage = 8;    // per-brick kernel: fewer particles skip the halo
+  int node_tma = 1;           // PS_F32X4 halos by tensor copy
 };
 Tuning& tuning();
 int sm_count();
@@ -250,6 +251,9 @@ template <> struct CoefLoadBits<__half> {
 template <typename Tc> struct AccOf { using type = float; };
 template <> struct AccOf<double> { using type = double; };
 template <typename Tc> struct IsQuant { static constexpr bool value = false; };
+// float4 coefficients: one 16-byte node (u, v, w, 0) per grid point (PS_F32X4).
+template <typename Tc> struct IsNode4 { static constexpr bool value = false; };
+template <> struct IsNode4<float4> { static constexpr bool value = true; };
 template <> struct IsQuant<__nv_bfloat16> { static constexpr bool value = true; };
 template <> struct IsQuant<__half> { static constexpr bool value = true; };
 

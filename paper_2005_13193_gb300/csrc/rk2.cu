@@ -42,7 +42,8 @@ extern "C" ps_status ps_rk2_step(const ps_grid* grid, ps_dtype coef_t, const voi
                                  void* ws, size_t ws_bytes, int32_t* status, void* stream) {
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
-  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16)
+  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16 &&
+      coef_t != PS_F32X4)
     return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype");
   if (!coef_n) return fail(PS_ERR_INVALID_ARG, "coef_n is NULL");
   const bool quant = coef_t == PS_BF16 || coef_t == PS_F16;

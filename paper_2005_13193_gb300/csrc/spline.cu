@@ -161,29 +161,14 @@ __device__ __forceinline__ int skew(int e, float inv_L) {
 // without bank conflicts; chunk carries move between lanes by shuffles.
 // padded = 0: dst is an unpadded view.  padded = 1: dst is the padded
 // coefficient array; every line is written to all its periodic images.
-template <typename T, typename Tout, int LMAX, bool QUANT>
-__global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst, View dv,
-                                               float* scale, int nx, int ny, int nz,
-                                               int ncomp, int L, int padded, T z,
-                                               T gain) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
-  T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * (L + 1);
-  const int64_t nrows = (int64_t)ncomp * nz * ny;
-  const int64_t row = (int64_t)blockIdx.x * nwarps + warp;
-  if (row >= nrows) return;  // whole warp; no block-level barrier below
-  const int yy = (int)(row % ny);
-  const int64_t r2 = row / ny;
-  const int zz = (int)(r2 % nz);
-  const int c = (int)(r2 / nz);
+// One periodic line of nx values held by a warp in its skewed shared buffer
+// (element e at e + e/L): the causal and anti-causal recursions with their
+// chunk carries, times the gain.  With QUANT the values are divided by the
+// line's power-of-two scale, which is returned.
+template <typename T, int LMAX, bool QUANT>
+__device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z, T gain) {
   const unsigned FULL = 0xffffffffu;
   const T thr = Thr<T>::v;
-
-  const float inv_L = 1.f / (float)L;
-  const T* sp = src + sv.off + c * sv.sc + zz * sv.sz + yy * sv.sy;
-  for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
-  __syncwarp();
   const int s0 = lane * L;
   int len = nx - s0;
   len = len < 0 ? 0 : (len > L ? L : len);
@@ -268,6 +253,31 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
   for (int i = 0; i < LMAX; ++i)
     if (i < len) mine[i] = gain * v[i] * inv_sc;
   __syncwarp();
+  return sc;
+}
+
+template <typename T, typename Tout, int LMAX, bool QUANT>
+__global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst, View dv,
+                                               float* scale, int nx, int ny, int nz,
+                                               int ncomp, int L, int padded, T z,
+                                               T gain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * (L + 1);
+  const int64_t nrows = (int64_t)ncomp * nz * ny;
+  const int64_t row = (int64_t)blockIdx.x * nwarps + warp;
+  if (row >= nrows) return;  // whole warp; no block-level barrier below
+  const int yy = (int)(row % ny);
+  const int64_t r2 = row / ny;
+  const int zz = (int)(r2 % nz);
+  const int c = (int)(r2 / nz);
+
+  const float inv_L = 1.f / (float)L;
+  const T* sp = src + sv.off + c * sv.sc + zz * sv.sz + yy * sv.sy;
+  for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
+  __syncwarp();
+  const float sc = line_solve<T, LMAX, QUANT>(buf, nx, L, lane, z, gain);
 
   if (!padded) {
     Tout* orow = dst + dv.off + c * dv.sc + zz * dv.sz + yy * dv.sy;
@@ -298,6 +308,47 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
           orow[P] = cvt_out<Tout>((float)val);
       }
       if (QUANT && lane == 0) scale[((int64_t)c * (nz + 3) + Pz) * (ny + 3) + Py] = sc;
+    }
+}
+
+// x pass writing PS_F32X4 nodes: a block of three warps takes one (z, y)
+// line; warp c solves component c in its skewed buffer, then the block writes
+// the padded row and its periodic images as 16-byte nodes (u, v, w, 0).
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, float4* dst, int nx,
+                                                    int ny, int nz, int L, T z, T gain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * (L + 1);
+  const int64_t row = blockIdx.x;
+  const int yy = (int)(row % ny), zz = (int)(row / ny);
+  const float inv_L = 1.f / (float)L;
+  const T* sp = src + sv.off + warp * sv.sc + zz * sv.sz + yy * sv.sy;
+  for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
+  __syncwarp();
+  line_solve<T, LMAX, false>(buf, nx, L, lane, z, gain);
+  __syncthreads();
+  const T* b0 = reinterpret_cast<const T*>(smem_raw);
+  const T* b1 = b0 + 32 * (L + 1);
+  const T* b2 = b1 + 32 * (L + 1);
+  int pys[2], pzs[2];
+  int npy = 1, npz = 1;
+  pys[0] = yy + 1;
+  if (yy == ny - 1) pys[npy++] = 0;
+  else if (yy == 0) pys[npy++] = ny + 1;
+  else if (yy == 1) pys[npy++] = ny + 2;
+  pzs[0] = zz + 1;
+  if (zz == nz - 1) pzs[npz++] = 0;
+  else if (zz == 0) pzs[npz++] = nz + 1;
+  else if (zz == 1) pzs[npz++] = nz + 2;
+  const int64_t mx = nx + 3;
+  for (int iz = 0; iz < npz; ++iz)
+    for (int iy = 0; iy < npy; ++iy) {
+      float4* orow = dst + ((int64_t)pzs[iz] * (ny + 3) + pys[iy]) * mx;
+      for (int P = threadIdx.x; P < nx + 3; P += blockDim.x) {
+        const int e = skew(padded_to_node(P, nx), inv_L);
+        orow[P] = make_float4((float)b0[e], (float)b1[e], (float)b2[e], 0.f);
+      }
     }
 }
 
@@ -399,6 +450,33 @@ ps_status launch_x(const T* src, View sv, Tout* dst, View dv, float* scale, int 
   return fail(PS_ERR_UNSUPPORTED, "FP64 solve supports n <= 1024");
 }
 
+template <int LMAX>
+ps_status launch_x_node4_l(const float* src, View sv, float4* dst, int nx, int ny, int nz,
+                           int L, float z, float gain, cudaStream_t st) {
+  const size_t smem = (size_t)3 * 32 * (L + 1) * sizeof(float);
+  auto kern = solve_x_node4<float, LMAX>;
+  if (smem > 48 * 1024) {
+    ps_status rc = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "solve_x_node4 smem attribute");
+    if (rc) return rc;
+  }
+  const int64_t rows = (int64_t)ny * nz;
+  kern<<<(unsigned)rows, 96, smem, st>>>(src, sv, dst, nx, ny, nz, L, z, gain);
+  return check_launch("solve_x_node4");
+}
+
+ps_status launch_x_node4(const float* src, View sv, float4* dst, int nx, int ny, int nz,
+                         float z, float gain, cudaStream_t st) {
+  const int L = x_chunk(nx);
+  if (L <= 2) return launch_x_node4_l<2>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+  if (L <= 4) return launch_x_node4_l<4>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+  if (L <= 8) return launch_x_node4_l<8>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+  if (L <= 16) return launch_x_node4_l<16>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+  if (L <= 32) return launch_x_node4_l<32>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+  return launch_x_node4_l<64>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+}
+
 View unpadded_view(const ps_grid* g) {
   const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
   return View{0, nx * ny * nz, nx * ny, nx};
@@ -432,6 +510,22 @@ ps_status run_solve(const ps_grid* g, int ncomp, const Tin* field, View fv, T* i
                                   gain, st);
 }
 
+// y and z passes into the unpadded FP32 workspace, then the node x pass.
+template <typename Tin>
+ps_status run_solve_node4(const ps_grid* g, const Tin* field, View fv, float* inter,
+                          float4* out, cudaStream_t st) {
+  const double zd = sqrt(3.0) - 2.0;
+  const float z = (float)zd, gain = (float)(-6.0 * zd);
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  ps_status rc = launch_strided<Tin, float>(field, fv, fv.sz, fv.sy, inter, fv, fv.sz, fv.sy,
+                                            nx, ny, nz, 3, z, gain, st);
+  if (rc) return rc;
+  rc = launch_strided<float, float>(inter, fv, fv.sy, fv.sz, inter, fv, fv.sy, fv.sz, nx, nz, ny,
+                                    3, z, gain, st);
+  if (rc) return rc;
+  return launch_x_node4(inter, fv, out, nx, ny, nz, z, gain, st);
+}
+
 }  // namespace
 
 ps_status solve_unpadded_inplace_f32(const ps_grid* g, int ncomp, float* a,
@@ -447,7 +541,7 @@ using namespace ps;
 extern "C" size_t ps_spline_coeffs_workspace_size(const ps_grid* grid, int ncomp,
                                                   ps_dtype coef_t) {
   if (!grid || ncomp < 1) return 0;
-  if (coef_t == PS_BF16 || coef_t == PS_F16)
+  if (coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_F32X4)
     return align_up((size_t)ncomp * (size_t)grid_volume(grid) * sizeof(float), 256) + 256;
   return 0;
 }
@@ -463,8 +557,10 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
   if (field_t != PS_F32 && field_t != PS_F64)
     return fail(PS_ERR_INVALID_ARG, "field dtype must be F32 or F64");
   const bool quant = coef_t == PS_BF16 || coef_t == PS_F16;
-  if (coef_t != PS_F32 && coef_t != PS_F64 && !quant)
+  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_F32X4 && !quant)
     return fail(PS_ERR_INVALID_ARG, "bad coef dtype");
+  if (coef_t == PS_F32X4 && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "PS_F32X4 coefficients need ncomp == 3");
   if (quant && !scale) return fail(PS_ERR_INVALID_ARG, "scale required for BF16/F16");
   if (coef_t == PS_F64)
     for (int d = 0; d < 3; ++d)
@@ -491,11 +587,16 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
                : run_solve<double, double, double, false>(grid, ncomp, fd, fv, c, iv, c,
                                                           pv, nullptr, 1, st);
   }
-  // quantised output: FP32 intermediate in the workspace
+  // quantised or node output: FP32 intermediate in the workspace
   size_t need = ps_spline_coeffs_workspace_size(grid, ncomp, coef_t);
   if (!ws || ws_bytes < need - 256 || (reinterpret_cast<uintptr_t>(ws) & 255))
     return fail(PS_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need - 256);
   float* inter = static_cast<float*>(ws);
+  if (coef_t == PS_F32X4) {
+    float4* c = static_cast<float4*>(coef);
+    return field_t == PS_F32 ? run_solve_node4<float>(grid, ff, fv, inter, c, st)
+                             : run_solve_node4<double>(grid, fd, fv, inter, c, st);
+  }
   if (coef_t == PS_BF16) {
     __nv_bfloat16* c = static_cast<__nv_bfloat16*>(coef);
     return field_t == PS_F32

@@ -437,3 +437,80 @@ def test_sparse_brick_knob(min_stage):
         assert np.abs(tr.pos.cpu().numpy() - new_ref[:, ids]).max() <= dt * 1e-5 * rms + 1e-14
     finally:
         ps.ps_tune_set("brick_min_stage", old)
+
+
+@pytest.mark.parametrize("n,brick", [((32, 32, 32), (8, 8, 8)), ((40, 24, 16), (8, 8, 8)),
+                                     ((37, 21, 10), (8, 4, 5)), ((64, 48, 40), (16, 8, 4))])
+def test_node4_storage_matches_planar(n, brick):
+    # Interleaved (u, v, w, 0) nodes hold the very values of the planar FP32
+    # coefficients (same passes, same arithmetic), and every kernel reads the
+    # same values from them: all results must agree bit for bit.
+    field, pos, cref = _case(n, 20000, seed=141, spread=1.3)
+    f = torch.from_numpy(field).to(DEV)
+    p32 = ps.SplineField.from_field(f, torch.float32)
+    p4 = ps.SplineField.from_field(f, ps.F32X4)
+    assert p4.coef.shape == (n[2] + 3, n[1] + 3, n[0] + 3, 4)
+    assert torch.equal(p4.padded(), p32.padded())
+    assert torch.count_nonzero(p4.coef[..., 3]) == 0
+    pg = torch.from_numpy(pos).to(DEV)
+    # direct gathers, values and gradients
+    for grad in (False, True):
+        a = p32.interp(pg, grad=grad)
+        b = p4.interp(pg, grad=grad)
+        for x, y in zip(a if grad else (a,), b if grad else (b,)):
+            assert torch.equal(x, y)
+    # staged gathers, every brick kernel
+    bins, sorted_pos = ps.bin_particles(n, brick, pg, want_sorted=True)
+    old = ps.ps_tune_get("brick_kernel")
+    try:
+        for k in (0, 1, 2, 3):
+            ps.ps_tune_set("brick_kernel", k)
+            assert torch.equal(p32.interp(pg, bins=bins), p4.interp(pg, bins=bins))
+            va, ga = p32.interp(pg, grad=True, bins=bins)
+            vb, gb = p4.interp(pg, grad=True, bins=bins)
+            assert torch.equal(va, vb) and torch.equal(ga, gb)
+            outs = []
+            for sf in (p32, p4):
+                tr = ps.Tracker(sf, sorted_pos.clone(), brick=brick)
+                tr.step(1e-2)
+                # by particle label: the order inside a bin is unspecified
+                lab = torch.empty_like(tr.ids)
+                lab[tr.ids] = torch.arange(tr.ids.numel(), device=DEV)
+                outs.append((tr.pos[:, lab], tr.vel[:, lab]))
+            assert all(torch.equal(x, y) for x, y in zip(*outs))
+    finally:
+        ps.ps_tune_set("brick_kernel", old)
+    # unbinned Heun step and the adjoint with respect to positions
+    t32 = ps.Tracker(p32, pg.clone(), brick=None)
+    t4 = ps.Tracker(p4, pg.clone(), brick=None)
+    t32.step(1e-2)
+    t4.step(1e-2)
+    assert torch.equal(t32.pos, t4.pos)
+    w = torch.randn((3, pg.shape[1]), device=DEV, generator=torch.Generator(DEV).manual_seed(3))
+    g32, g4 = torch.empty_like(pg), torch.empty_like(pg)
+    ps.ps_interp_backward(p32.coef, n, pg, w, g_pos=g32)
+    ps.ps_interp_backward(p4.coef, n, pg, w, g_pos=g4)
+    assert torch.equal(g32, g4)
+    # and against the oracle, as for the planar form
+    assert rel_err(p4.interp(pg).cpu().numpy(), oracle.interp(cref, pos)) <= 1e-5
+
+
+def test_node4_tensor_copy_matches_loads():
+    # the halo by tensor copy and by plain loads holds the same values
+    n = (64, 32, 48)
+    field, pos, cref = _case(n, 30000, seed=151, spread=1.1)
+    p4 = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), ps.F32X4)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins = ps.bin_particles(n, (8, 8, 8), pg)
+    old = ps.ps_tune_get("node_tma")
+    try:
+        outs = []
+        for on in (1, 0):
+            ps.ps_tune_set("node_tma", on)
+            st = torch.zeros(4, dtype=torch.int32, device=DEV)
+            outs.append(p4.interp(pg, grad=True, bins=bins, status=st))
+            assert ps.ps_status_read(st)[0] == 0
+        assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    finally:
+        ps.ps_tune_set("node_tma", old)
+    assert rel_err(outs[0][0].cpu().numpy(), oracle.interp(cref, pos)) <= 1e-5
