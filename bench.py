@@ -42,7 +42,7 @@ WORKLOAD = ("mid: 512^3 FP32 u,v,w (k^-5/3, 1<=|k|<=170, unit rms), 16,777,216 u
             "bricks every step")
 # kernels of libps launched per bench step: 3 solve passes + 10 x (5 bin + 1 RK2)
 LAUNCHES_PER_STEP = 3 + RK_STEPS * 6
-DOMINANT = "interp_staged<float,3,RK2> (fused binned Heun step)"
+DOMINANT = "interp_staged<float4,3,RK2> (fused binned Heun step, halo by tensor copy)"
 SOURCE_FOR_TRAFFIC = os.path.join(ROOT, "paper_2005_13193_gb300", "csrc", "interp.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
@@ -188,8 +188,9 @@ def run_ours(args):
     pos_host = synth.uniform_particles(NP, seed=POS_SEED)
     pos0 = torch.from_numpy(pos_host).to(dev)
     n3 = (N, N, N)
-    coef = torch.empty(ps.coef_shape((N, N, N), 3, torch.float32), dtype=torch.float32,
-                       device=dev)
+    # FP32 coefficients stored as interleaved (u, v, w, 0) nodes
+    coef = torch.empty(ps.coef_shape((N, N, N), 3, ps.F32X4), dtype=torch.float32, device=dev)
+    ws_solve = ps.workspace(ps.ps_spline_coeffs_workspace_size((N, N, N), 3, ps.F32X4), dev)
     nb = [-(-N // b) for b in BRICK]
     nbins = nb[0] * nb[1] * nb[2]
     offsets = torch.empty(nbins + 1, dtype=torch.int32, device=dev)
@@ -203,7 +204,7 @@ def run_ours(args):
     def one_step(ev_solve=None, ev_rk=None):
         if ev_solve:
             ev_solve[0].record(stream)
-        ps.ps_spline_coeffs(field, coef)
+        ps.ps_spline_coeffs(field, coef, ws=ws_solve)
         if ev_solve:
             ev_solve[1].record(stream)
         for r in range(RK_STEPS):
@@ -264,13 +265,14 @@ def run_ours(args):
         "data": "synthetic (seeded spectral field, uniform particles)",
         "config": {"workload": WORKLOAD, "grid": N, "particles": NP, "rk2_steps": RK_STEPS,
                    "dt": DT, "brick": list(BRICK), "coef_dtype": "f32",
+                   "coef_storage": "f32x4 nodes (u, v, w, 0)",
                    "positions": "f64", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws_} (independent problems)"},
         "gpu_launches": LAUNCHES_PER_STEP * K,
         "clocks": clk,
         "roofline": {"bound": "hbm", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic_for("rk2_staged_f32"),
+                     "traffic": traffic_for("rk2_staged_f32x4"),
                      "alg_bytes_per_launch": rk_alg_bytes, "avg_launch_ms": rk_avg},
         "breakdown": {"solve_ms": solve_ms,
                       "solve_gbs_min_bytes": solve_min_bytes / (solve_ms * 1e-3) / 1e9,
@@ -287,7 +289,8 @@ def run_ours(args):
         result["coef_forms"] = precision_forms(ps, torch, dev, field, coef, bufs[0], n3)
         result["batched_48_fields"] = batch_extras(ps, torch, dev)
     if not args.no_e2e:
-        result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg)
+        result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_,
+                                    pg)
     if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(field.cpu().numpy(), pos_host)
     if rank == 0:
@@ -337,11 +340,11 @@ def _event_ms(torch, fn, reps, warmup=2):
     return a.elapsed_time(b) / reps
 
 
-def precision_forms(ps, torch, dev, field, coef32, pos_now, n3):
-    """The same solve and binned RK2 step with BF16 and FP16 coefficients
-    (power-of-two scale per x-line) beside FP32: kernel times, and the
-    velocity error of every particle against the FP32 form, relative to the
-    rms velocity."""
+def precision_forms(ps, torch, dev, field, coef_nodes, pos_now, n3):
+    """The same solve and binned RK2 step with FP32 planar, BF16 and FP16
+    coefficients (power-of-two scale per x-line) beside the FP32 node form the
+    benchmark runs: kernel times, and the velocity error of every particle
+    against FP32, relative to the rms velocity."""
     # positions stored in bin order (the staged kernel's precondition)
     bins, pos_binned = ps.bin_particles(n3, BRICK, pos_now, want_sorted=True,
                                         want_perm=False)
@@ -352,9 +355,13 @@ def precision_forms(ps, torch, dev, field, coef32, pos_now, n3):
     pos = torch.empty_like(pos_binned)
     status = torch.zeros(4, dtype=torch.int32, device=dev)
     out = {}
-    for name, dt_ in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
-        if dt_ == torch.float32:
-            c, s, wsq = coef32, None, None
+    for name, dt_ in (("f32x4", ps.F32X4), ("f32", torch.float32), ("bf16", torch.bfloat16),
+                      ("f16", torch.float16)):
+        if dt_ == ps.F32X4:
+            c, s = coef_nodes, None
+            wsq = ps.workspace(ps.ps_spline_coeffs_workspace_size(n3, 3, dt_), dev)
+        elif dt_ == torch.float32:
+            c, s, wsq = torch.empty(ps.coef_shape(n3, 3, dt_), dtype=dt_, device=dev), None, None
         else:
             c = torch.empty(ps.coef_shape(n3, 3, dt_), dtype=dt_, device=dev)
             s = torch.empty((3, N + 3, N + 3), dtype=torch.float32, device=dev)
@@ -382,7 +389,7 @@ def precision_forms(ps, torch, dev, field, coef32, pos_now, n3):
         e = {"solve_ms": t_solve, "rk2_kernel_ms": t_rk,
              "rk2_particles_per_s": 2 * NP / (t_rk * 1e-3),
              "coef_bytes": c.numel() * c.element_size()}
-        if dt_ == torch.float32:
+        if dt_ == ps.F32X4:
             vel32.copy_(vel)
         else:
             d = (vel - vel32).double()
@@ -407,12 +414,12 @@ def batch_extras(ps, torch, dev):
     flds = []
     for i, n in enumerate(sizes):
         f = synth.spectral_field(n, n // 3, seed=3100 + i, device=dev, dtype=torch.float32)
-        flds.append((f, ps.SplineField.from_field(f)))
+        flds.append((f, ps.SplineField.from_field(f, ps.F32X4)))
     pos0 = torch.cat([torch.from_numpy(synth.uniform_particles(v, seed=3200 + i))
                       for i, v in enumerate(nps)], dim=1).to(dev)
     grids = [(n,) * 3 for n in sizes]
-    best, table = autotune.tune_batch(grids, nps, flds, pos0)
-    plan = ps.BatchPlan(grids, nps, brick=best)
+    best, table = autotune.tune_batch(grids, nps, flds, pos0, coef_dtype=ps.F32X4)
+    plan = ps.BatchPlan(grids, nps, coef_dtype=ps.F32X4, brick=best)
     pos = pos0.clone()
     ids = torch.arange(plan.np_total, dtype=torch.int64, device=dev)
     plan.run(flds, pos, nsteps, dt, solve=False, ids=ids, use_graph=True)  # capture
@@ -431,13 +438,14 @@ def batch_extras(ps, torch, dev):
     t_loop = _event_ms(torch, loop, 2, warmup=1)
     units = 2 * nsteps * plan.np_total
     return {"fields": len(sizes), "particles": plan.np_total, "rk2_steps": nsteps,
+            "coef_storage": "f32x4 nodes",
             "autotuned_brick": list(best),
             "autotune_ms_per_step": {"x".join(map(str, k)): v for k, v in table.items()},
             "batched_graph_ms": t_graph, "batched_particles_per_s": units / (t_graph * 1e-3),
             "per_field_loop_ms": t_loop, "loop_particles_per_s": units / (t_loop * 1e-3)}
 
 
-def e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg):
+def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg):
     """The same step through the public API from pinned host buffers: the field
     and positions are copied in, the result positions and velocities out."""
     field_h = field.cpu().pin_memory()
@@ -457,7 +465,7 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, n3, K, ws_, pg):
     def step():
         field_d.copy_(field_h, non_blocking=True)
         pos_d.copy_(pos_h, non_blocking=True)
-        ps.ps_spline_coeffs(field_d, coef)
+        ps.ps_spline_coeffs(field_d, coef, ws=ws_solve)
         for _ in range(RK_STEPS):
             ps.ps_rk2_step(coef, n3, pos_d, DT, ids=ids, vel_out=vel_d, brick=BRICK, rebin=True,
                            bin_offsets=offsets, ws=ws, status=status)

@@ -21,6 +21,7 @@ struct ps_plan {
   std::vector<int64_t> nps, pbase;  // pbase has nfields + 1 entries
   std::vector<int32_t> bin_base;    // nfields + 1 entries
   std::vector<BrickArgs> bricks;
+  std::vector<int32_t> chunk;       // per field: 0 = bricks, else particles per bin
   int64_t np_total = 0, total_bins = 0;
   ps_dtype coef_t = PS_F32;
   int32_t brick[3] = {8, 8, 8};
@@ -111,6 +112,7 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
   p->pbase.assign(nfields + 1, 0);
   p->bin_base.assign(nfields + 1, 0);
   p->bricks.resize(nfields);
+  p->chunk.assign(nfields, 0);
   int64_t bins = 0;
   for (int f = 0; f < nfields; ++f) {
     ps_status rc = validate_grid(&grids[f]);
@@ -121,7 +123,14 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
       return rc;
     }
     p->pbase[f + 1] = p->pbase[f] + nps[f];
-    bins += p->bricks[f].nbins;
+    // a field so sparse that its bricks would hold fewer particles on average
+    // than the staging threshold gathers from global memory anyway: bin it in
+    // runs of particles, a block per run instead of a block per brick
+    const double cells = (double)grids[f].n[0] * grids[f].n[1] * grids[f].n[2];
+    const double per_brick =
+        (double)nps[f] * p->brick[0] * p->brick[1] * p->brick[2] / cells;
+    if (per_brick < tuning().brick_min_stage) p->chunk[f] = kBatchChunk;
+    bins += p->chunk[f] ? (nps[f] + kBatchChunk - 1) / kBatchChunk : p->bricks[f].nbins;
     if (bins >= ((int64_t)1 << 31)) {
       delete p;
       return fail(PS_ERR_INVALID_ARG, "too many bins in the batch");
@@ -144,7 +153,7 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
     size_t s = 0;
     ps_status rc = staged_fill_rk2(&grids[f], coef_t, p->brick, nullptr, nullptr, 0, nullptr,
                                    nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
-                                   probe.data(), &s);
+                                   p->chunk[f] ? 1 : 0, probe.data(), &s);
     if (rc) {
       delete p;
       return rc;
@@ -183,13 +192,15 @@ ps_status build_tables(ps_plan* p, const ps_batch_field* fields, double* pos, in
     ps_status rc = staged_fill_rk2(&p->grids[f], p->coef_t, p->brick, fields[f].coef,
                                    fields[f].scale, p->np_total, pos_s, pos,
                                    offsets + p->bin_base[f], vel, ids ? ids_s : nullptr, ids,
-                                   dt, status, p->h_args.data() + (size_t)f * p->args_size, &s);
+                                   dt, status, p->chunk[f] ? 1 : 0,
+                                   p->h_args.data() + (size_t)f * p->args_size, &s);
     if (rc) return rc;
     BinField& bf = p->h_bintab[f];
     bf.g = make_grid_args(&p->grids[f]);
     bf.b = p->bricks[f];
     bf.pbase = p->pbase[f];
     bf.bin_base = p->bin_base[f];
+    bf.chunk = p->chunk[f];
   }
   return PS_OK;
 }

@@ -187,10 +187,15 @@ __global__ void bin_count_batch_kernel(const BinField* __restrict__ tab, int nfi
         if (tab[mid].pbase <= p) lo = mid;
         else hi = mid;
       }
-      bool ok;
-      key = tab[lo].bin_base +
-            bin_of_position(tab[lo].g, tab[lo].b, pos[p], pos[np + p], pos[2 * np + p], ok);
-      if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+      if (tab[lo].chunk > 0) {
+        // a sparse field: runs of particles in storage order
+        key = tab[lo].bin_base + (int)((p - tab[lo].pbase) / tab[lo].chunk);
+      } else {
+        bool ok;
+        key = tab[lo].bin_base +
+              bin_of_position(tab[lo].g, tab[lo].b, pos[p], pos[np + p], pos[2 * np + p], ok);
+        if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+      }
     }
     const unsigned peers = __match_any_sync(FULL, key);
     const int leader = __ffs(peers) - 1;

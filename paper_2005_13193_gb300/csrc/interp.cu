@@ -343,6 +343,7 @@ struct StagedArgs {
   int vec;      // 1: halo rows are whole 16-byte vectors inside the array
   int min_stage;  // bricks with fewer particles gather from global memory
   int tma;        // 1: the node halo is one tensor copy described by tmap
+  int chunked;    // 1: bins are runs of particles (sparse field): no halo
   const void* coef;
   const float* scale;
   const void* coef2;  // second-stage field of an RK2 step; NULL = same as coef
@@ -1217,7 +1218,8 @@ __device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4*
 // min_stage particles, whose stencils are then read from global memory), then
 // the location / gather / update phases of process_brick.
 template <typename Tc, int NC, int MODE, bool TMA = false>
-__device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float4* smem) {
+__device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float4* smem,
+                                             const CUtensorMap* tmap = nullptr) {
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   if (beg >= end) return;
   const int nbx = a.b.nb[0], nby = a.b.nb[1];
@@ -1228,19 +1230,19 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
   const Tc* coef = static_cast<const Tc*>(a.coef);
   float4* halo = smem;
   const Recs R = carve_recs(smem + a.S[2] * a.PS);
-  if (end - beg < a.min_stage) {
+  if (end - beg < a.min_stage || a.chunked) {
     // an origin far from every cell sends every stencil to global memory
     const int far[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
     process_brick<Tc, NC, MODE>(a, beg, end, far, halo, R, nullptr, nullptr, 0);
     return;
   }
   if constexpr (TMA && IsNode4<Tc>::value) {
-    // a kernel argument holds the tensor map; the destination must be
-    // 128-byte aligned
-    if (a.tma && is_cube11_rows12(a) && (smem_u32(halo) & 127) == 0) {
+    // `tmap` is a kernel argument or lies in global memory; the destination
+    // must be 128-byte aligned
+    if (a.tma && tmap && is_cube11_rows12(a) && (smem_u32(halo) & 127) == 0) {
       __shared__ __align__(8) unsigned long long mbar;
       if (threadIdx.x == 0)
-        tma_issue_halo(&a.tmap, halo, &mbar, P0,
+        tma_issue_halo(tmap, halo, &mbar, P0,
                        (unsigned)(sizeof(float4) * HaloGeo<12>::PS * HaloGeo<12>::Sz));
       process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar);
       return;
@@ -1272,7 +1274,7 @@ template <typename Tc, int NC, int MODE>
 __global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4)
     interp_staged(const __grid_constant__ StagedArgs a) {
   extern __shared__ __align__(128) float4 smem_a128[];
-  brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128);
+  brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128, &a.tmap);
 }
 
 // The warp-autonomous form ("brick_kernel" 3): no particle records, no block
@@ -1289,22 +1291,30 @@ template <typename Tc, int NC, int MODE>
 __global__ void __launch_bounds__(256, 3)
     interp_staged_batch(const StagedArgs* __restrict__ tab, const int* __restrict__ bin_base,
                         int nfields) {
-  extern __shared__ float4 smem[];
+  extern __shared__ __align__(128) float4 smem_b128[];
   __shared__ StagedArgs sa;
-  __shared__ int local_bin;
-  if (threadIdx.x == 0) {
-    const int b = blockIdx.x;
-    int lo = 0, hi = nfields;  // bin_base[lo] <= b < bin_base[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (bin_base[mid] <= b) lo = mid;
-      else hi = mid;
-    }
-    sa = tab[lo];
-    local_bin = b - bin_base[lo];
+  const int b = blockIdx.x;
+  // field 0's offsets are the global offsets: empty bins leave at once
+  const int32_t* goffs = tab[0].offs;
+  if (goffs[b] >= goffs[b + 1]) return;
+  int lo = 0, hi = nfields;  // bin_base[lo] <= b < bin_base[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (bin_base[mid] <= b) lo = mid;
+    else hi = mid;
   }
+  constexpr int kWords = (int)(sizeof(StagedArgs) / sizeof(int4));
+  static_assert(sizeof(StagedArgs) % sizeof(int4) == 0, "argument block copied in 16 bytes");
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<int4*>(&sa)[i] = reinterpret_cast<const int4*>(tab + lo)[i];
+  // the field's tensor map stays in the global table (a tensor copy cannot
+  // name one in shared memory); order its upload before the copy proxy
+  if (threadIdx.x == 0 && IsNode4<Tc>::value && tab[lo].tma)
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<unsigned long long>(&tab[lo].tmap))
+                 : "memory");
   __syncthreads();
-  brick_phased<Tc, NC, MODE>(sa, local_bin, smem);
+  brick_phased<Tc, NC, MODE, true>(sa, b - bin_base[lo], smem_b128, &tab[lo].tmap);
 }
 
 // ------------------------------------------------- thread per particle ----
@@ -1773,7 +1783,7 @@ void attach_tma(StagedArgs* a, ps_dtype coef_t) {
   a->tma = 0;
   if (coef_t != PS_F32X4 || !a->vec || !tuning().node_tma) return;
   if ((a->SX * a->S[1]) % 8 != 4 || a->SX > 256 || a->S[1] > 256 || a->S[2] > 256) return;
-  if (reinterpret_cast<uintptr_t>(a->coef) & 15) return;
+  if (!a->coef || (reinterpret_cast<uintptr_t>(a->coef) & 15)) return;
   a->tma = encode_node_halo_map(a) ? 1 : 0;
 }
 
@@ -1856,13 +1866,14 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
                           const void* coef, const float* scale, int64_t np_total,
                           const double* pos_in, double* pos_out, const int32_t* offs,
                           float* vel, const int64_t* ids_in, int64_t* ids_out, double dt,
-                          int32_t* status, void* out, size_t* smem) {
+                          int32_t* status, int chunked, void* out, size_t* smem) {
   if (coef_t == PS_F64) return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
   StagedArgs a{};
   ps_status rc = fill_staged(grid, coef_t, brick, 0, &a, smem);
   if (rc) return rc;
   a.coef = coef;
   a.scale = scale;
+  attach_tma(&a, coef_t);
   a.np = np_total;
   a.pos_in = pos_in;
   a.pos_out = pos_out;
@@ -1876,6 +1887,7 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
   a.dtih[1] = d.y;
   a.dtih[2] = d.z;
   a.status = status;
+  a.chunked = chunked;
   memcpy(out, &a, sizeof(a));
   return PS_OK;
 }

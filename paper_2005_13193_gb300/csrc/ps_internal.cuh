@@ -102,6 +102,7 @@ struct BinField {
   BrickArgs b;
   int64_t pbase;     // first particle of the field in the concatenated arrays
   int32_t bin_base;  // first global bin of the field
+  int32_t chunk;     // > 0: bins are runs of `chunk` particles, not bricks
 };
 ps_status bin_run_batch(const BinField* d_tab, int nfields, int64_t total_bins, int64_t np,
                         const double* pos, int32_t* bin_of, int32_t* bin_offsets,
@@ -115,7 +116,9 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
                           const void* coef, const float* scale, int64_t np_total,
                           const double* pos_in, double* pos_out, const int32_t* offs,
                           float* vel, const int64_t* ids_in, int64_t* ids_out, double dt,
-                          int32_t* status, void* out, size_t* smem);
+                          int32_t* status, int chunked, void* out, size_t* smem);
+// Particles per bin of a field binned in runs of particles instead of bricks.
+constexpr int kBatchChunk = 128;
 ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
                               int nfields, int64_t total_bins, size_t smem, bool prepare,
                               cudaStream_t st);

@@ -39,10 +39,12 @@ def _by_label(x, ids):
     return out
 
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, ps.F32X4])
 def test_batch_equals_per_field_runs(dtype):
-    sizes = [16, 24, 32, 48, 32]
-    nps = [1000, 50000, 3000, 20000, 0]
+    # the last field is sparse (about 4 particles per 8^3 brick): the plan
+    # bins it in runs of particles and gathers from global memory
+    sizes = [16, 24, 32, 48, 32, 64]
+    nps = [1000, 50000, 3000, 20000, 0, 2000]
     dt, nsteps = 4e-3, 3
     flds = _fields(sizes, 300, dtype)
     pos0 = _positions(nps, 400)
