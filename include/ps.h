@@ -76,7 +76,20 @@ typedef enum {
  * float, so one 16-byte load brings a node and a brick's halo is one box of
  * consecutive rows.  Requires ncomp == 3.  A storage choice, not part of the
  * method. */
-typedef enum { PS_F32 = 0, PS_BF16 = 1, PS_F16 = 2, PS_F64 = 3, PS_F32X4 = 4 } ps_dtype;
+/* PS_BF16X4 / PS_F16X4 (coefficients only): the same node layout with 16-bit
+ * values (8 bytes per node, rows padded to an even node count), each scaled
+ * by the power-of-two scale of its component's x-line; the scale array is
+ * [nz+3][ny+3][4] F32 (s_u, s_v, s_w, 1).  The stored values are those of
+ * PS_BF16 / PS_F16.  Requires ncomp == 3. */
+typedef enum {
+  PS_F32 = 0,
+  PS_BF16 = 1,
+  PS_F16 = 2,
+  PS_F64 = 3,
+  PS_F32X4 = 4,
+  PS_BF16X4 = 5,
+  PS_F16X4 = 6
+} ps_dtype;
 
 /* device status codes (status[0]) */
 #define PS_DEV_OK 0
@@ -126,7 +139,7 @@ ps_status ps_status_read(const int32_t* status, int32_t* host_out, void* stream)
 /* coefficients per axis.  The result is the exact inverse up to rounding;  */
 /* the order of the three directions is immaterial in exact arithmetic.     */
 /*   field_t: PS_F32 or PS_F64.  coef_t: PS_F32, PS_F64, PS_BF16, PS_F16,   */
-/*   or PS_F32X4 (ncomp == 3).                                              */
+/*   or the node forms PS_F32X4, PS_BF16X4, PS_F16X4 (ncomp == 3).          */
 /*   Arithmetic is FP64 when coef_t is PS_F64, else FP32.                   */
 /*   scale: required for BF16/F16 (per x-line power-of-two scale), else     */
 /*   ignored.  field and coef must not overlap.  ncomp in [1, 16].          */

@@ -18,7 +18,8 @@ from typing import Optional, Sequence
 import torch
 
 from . import _abi
-from ._abi import (PS_BF16, PS_F16, PS_F32, PS_F32X4, PS_F64, PS_OK, PsGrid)
+from ._abi import (PS_BF16, PS_BF16X4, PS_F16, PS_F16X4, PS_F32, PS_F32X4, PS_F64, PS_OK,
+                   PsGrid)
 
 TWO_PI = 2.0 * math.pi
 DEFAULT_L = (TWO_PI, TWO_PI, TWO_PI)
@@ -26,27 +27,38 @@ DEFAULT_L = (TWO_PI, TWO_PI, TWO_PI)
 _DT = {torch.float32: PS_F32, torch.float64: PS_F64, torch.bfloat16: PS_BF16,
        torch.float16: PS_F16}
 
-# Coefficient storage with the three components of a node interleaved as 16
-# bytes (u, v, w, 0): a float32 tensor [nz+3][ny+3][nx+3][4] (PS_F32X4).
+# Coefficient storage with the three components of a node interleaved
+# (u, v, w, 0): a tensor [nz+3][ny+3][pitch][4], float32 (PS_F32X4) or 16-bit
+# values scaled per component and x-line (PS_BF16X4, PS_F16X4; the scales are
+# a float32 tensor [nz+3][ny+3][4]).
 F32X4 = "f32x4"
+BF16X4 = "bf16x4"
+F16X4 = "f16x4"
+_NODE = {F32X4: (PS_F32X4, torch.float32), BF16X4: (PS_BF16X4, torch.bfloat16),
+         F16X4: (PS_F16X4, torch.float16)}
+_NODE_OF = {v[1]: k for k, v in _NODE.items()}
+
+
+def _is_token(dtype) -> bool:
+    return isinstance(dtype, str)
 
 
 def _dt_code(dtype) -> int:
-    return PS_F32X4 if dtype == F32X4 else _DT[dtype]
+    return _NODE[dtype][0] if _is_token(dtype) else _DT[dtype]
 
 
 def _is_node4(coef: torch.Tensor) -> bool:
     # planar rows hold >= 8 elements, so a last extent of 4 is a node array
-    return coef.dtype == torch.float32 and coef.dim() == 4 and coef.shape[-1] == 4
+    return coef.dtype in _NODE_OF and coef.dim() == 4 and coef.shape[-1] == 4
 
 
 def _coef_type(coef: torch.Tensor) -> int:
-    return PS_F32X4 if _is_node4(coef) else _DT[coef.dtype]
+    return _dt_code(coef_kind(coef))
 
 
 def coef_kind(coef: torch.Tensor):
-    """The coefficient dtype argument a tensor corresponds to (F32X4 or a torch dtype)."""
-    return F32X4 if _is_node4(coef) else coef.dtype
+    """The coefficient dtype argument a tensor corresponds to (a node token or a torch dtype)."""
+    return _NODE_OF[coef.dtype] if _is_node4(coef) else coef.dtype
 
 
 def _ncomp_of(coef: torch.Tensor) -> int:
@@ -121,15 +133,24 @@ def coef_row_pitch(nx: int, dtype: torch.dtype) -> int:
 def coef_shape(n, ncomp: int, dtype):
     """Storage shape [ncomp][nz+3][ny+3][pitch] of padded coefficients, or
     [nz+3][ny+3][nx+3][4] for F32X4 (ncomp 3)."""
-    if dtype == F32X4:
+    if _is_token(dtype):
         if ncomp != 3:
-            raise ValueError("F32X4 coefficients hold three components")
-        return (n[2] + 3, n[1] + 3, n[0] + 3, 4)
+            raise ValueError("node coefficients hold three components")
+        return (n[2] + 3, n[1] + 3, coef_row_pitch(n[0], dtype), 4)
     return (ncomp, n[2] + 3, n[1] + 3, coef_row_pitch(n[0], dtype))
 
 
+def scale_shape(n, ncomp: int, dtype):
+    """Shape of the per-x-line scales of 16-bit coefficients (None otherwise)."""
+    if dtype in (BF16X4, F16X4):
+        return (n[2] + 3, n[1] + 3, 4)
+    if dtype in (torch.bfloat16, torch.float16):
+        return (ncomp, n[2] + 3, n[1] + 3)
+    return None
+
+
 def _storage_dtype(dtype) -> torch.dtype:
-    return torch.float32 if dtype == F32X4 else dtype
+    return _NODE[dtype][1] if _is_token(dtype) else dtype
 
 
 def _check_coef_shape(coef: torch.Tensor, n):
@@ -325,7 +346,7 @@ class SplineField:
         """[ncomp][nz+3][ny+3][nx+3] view (the row pitch tail dropped; for F32X4
         the component-major view of the interleaved nodes)."""
         if _is_node4(self.coef):
-            return self.coef.permute(3, 0, 1, 2)[:3]
+            return self.coef.permute(3, 0, 1, 2)[:3, ..., : self.n[0] + 3]
         return self.coef[..., : self.n[0] + 3]
 
     @classmethod
@@ -337,10 +358,9 @@ class SplineField:
         if out is None:
             coef = torch.empty(coef_shape(n, ncomp, coef_dtype),
                                dtype=_storage_dtype(coef_dtype), device=field.device)
-            scale = None
-            if coef_dtype in (torch.bfloat16, torch.float16):
-                scale = torch.empty((ncomp, n[2] + 3, n[1] + 3), dtype=torch.float32,
-                                    device=field.device)
+            shp = scale_shape(n, ncomp, coef_dtype)
+            scale = (torch.empty(shp, dtype=torch.float32, device=field.device)
+                     if shp is not None else None)
             out = cls(coef, scale, n, L)
         need = ps_spline_coeffs_workspace_size(n, ncomp, coef_kind(out.coef), L)
         if need and (ws is None or ws.numel() < need):

@@ -16,7 +16,7 @@ PS_ERR_UNSUPPORTED = 4
 PS_ERR_TIMEOUT = 5
 PS_ERR_DEVICE_STATUS = 6
 
-PS_F32, PS_BF16, PS_F16, PS_F64, PS_F32X4 = 0, 1, 2, 3, 4
+PS_F32, PS_BF16, PS_F16, PS_F64, PS_F32X4, PS_BF16X4, PS_F16X4 = 0, 1, 2, 3, 4, 5, 6
 
 PS_DEV_OK = 0
 PS_DEV_NONFINITE_POS = 1

@@ -52,6 +52,8 @@ size_t dtype_size(ps_dtype t) {
     case PS_BF16: return 2;
     case PS_F16: return 2;
     case PS_F32X4: return 16;
+    case PS_BF16X4: return 8;
+    case PS_F16X4: return 8;
   }
   return 0;
 }

@@ -78,7 +78,7 @@ void layout(ps_plan* p) {
   p->off_pos = take(3 * np * sizeof(double));
   p->off_ids = take(np * sizeof(int64_t));
   size_t quant = 0;
-  if (p->coef_t == PS_BF16 || p->coef_t == PS_F16 || p->coef_t == PS_F32X4)
+  if (ps_spline_coeffs_workspace_size(&p->grids[0], 3, p->coef_t) > 0)
     for (int f = 0; f < p->nfields; ++f)
       quant = std::max(quant, ps_spline_coeffs_workspace_size(&p->grids[f], 3, p->coef_t));
   p->off_quant = take(quant);
@@ -99,8 +99,9 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
   *out = nullptr;
   if (nfields < 1 || nfields > 4096 || !grids || !nps)
     return fail(PS_ERR_INVALID_ARG, "need 1..4096 fields with grids and particle counts");
-  if (coef_t != PS_F32 && coef_t != PS_BF16 && coef_t != PS_F16 && coef_t != PS_F32X4)
-    return fail(PS_ERR_UNSUPPORTED, "batched runs use F32, F32X4, BF16 or F16 coefficients");
+  if (coef_t != PS_F32 && coef_t != PS_BF16 && coef_t != PS_F16 && coef_t != PS_F32X4 &&
+      coef_t != PS_BF16X4 && coef_t != PS_F16X4)
+    return fail(PS_ERR_UNSUPPORTED, "batched runs need F32, BF16 or F16 coefficients");
   ps_plan* p = new ps_plan();
   p->nfields = nfields;
   p->coef_t = coef_t;
@@ -253,7 +254,8 @@ extern "C" ps_status ps_batch_run(ps_plan* p, const ps_batch_field* fields, int 
   if (p->np_total > 0 && !pos) return fail(PS_ERR_INVALID_ARG, "pos is NULL");
   if (!ws || ws_bytes < p->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255))
     return fail(PS_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", p->ws_bytes);
-  const bool quant = p->coef_t == PS_BF16 || p->coef_t == PS_F16;
+  const bool quant = p->coef_t == PS_BF16 || p->coef_t == PS_F16 || p->coef_t == PS_BF16X4 ||
+                     p->coef_t == PS_F16X4;
   for (int f = 0; f < p->nfields; ++f) {
     if (!fields[f].coef) return fail(PS_ERR_INVALID_ARG, "field %d: coef is NULL", f);
     if (quant && !fields[f].scale) return fail(PS_ERR_INVALID_ARG, "field %d: scale is NULL", f);
@@ -264,7 +266,7 @@ extern "C" ps_status ps_batch_run(ps_plan* p, const ps_batch_field* fields, int 
   if (solve) {
     const size_t qbytes = p->ws_bytes - p->off_quant;
     for (int f = 0; f < p->nfields; ++f) {
-      const bool inter = quant || p->coef_t == PS_F32X4;
+      const bool inter = ps_spline_coeffs_workspace_size(&p->grids[f], 3, p->coef_t) > 0;
       rc = ps_spline_coeffs(&p->grids[f], 3, PS_F32, fields[f].field, p->coef_t, fields[f].coef,
                             fields[f].scale, inter ? at<char>(ws, p->off_quant) : nullptr,
                             inter ? qbytes : 0, stream);

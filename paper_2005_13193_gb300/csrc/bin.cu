@@ -29,34 +29,65 @@ __device__ __forceinline__ int bin_of_position(const GridArgs& g, const BrickArg
   return (bz * b.nb[1] + by) * b.nb[0] + bx;
 }
 
+// Ranks inside runs of equal keys in consecutive lanes: the run's first lane,
+// the lane's offset in the run and the run's length.  Particles stored in the
+// previous step's bin order form long runs, so one atomic serves many lanes;
+// equal keys in separate runs simply take separate atomics.
+__device__ __forceinline__ void run_ranks(int key, int lane, int& first, int& within, int& len) {
+  const unsigned FULL = 0xffffffffu;
+  const int prev = __shfl_up_sync(FULL, key, 1);
+  const unsigned starts = __ballot_sync(FULL, lane == 0 || prev != key);
+  const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
+  first = 31 - __clz(starts & upto);
+  within = lane - first;
+  const unsigned after = starts & ~upto;
+  len = (after ? __ffs(after) - 1 : 32) - first;
+}
+
+// Each warp takes kCountUnroll consecutive groups of 32 particles per trip and
+// issues all their position loads before any index arithmetic.
+constexpr int kCountUnroll = 4;
+
 __global__ void bin_count_kernel(GridArgs g, BrickArgs b, int64_t np,
                                  const double* __restrict__ pos, int32_t* __restrict__ bin_of,
                                  int32_t* __restrict__ rank, int32_t* __restrict__ counts,
                                  int32_t* status) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   // uniform trip count per warp so that every lane reaches the warp intrinsics
-  const int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t warp_start = start - lane;
-  for (int64_t base = warp_start; base < np; base += stride) {
-    const int64_t p = base + lane;
-    const bool valid = p < np;
-    int key = -1 - lane;  // unique per lane when invalid
-    if (valid) {
-      bool ok;
-      key = bin_of_position(g, b, pos[p], pos[np + p], pos[2 * np + p], ok);
-      if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+  for (int64_t base = wid * 32 * kCountUnroll; base < np; base += warps * 32 * kCountUnroll) {
+    double x[kCountUnroll], y[kCountUnroll], z[kCountUnroll];
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      x[u] = y[u] = z[u] = 0.0;
+      if (p < np) {
+        x[u] = pos[p];
+        y[u] = pos[np + p];
+        z[u] = pos[2 * np + p];
+      }
     }
-    const unsigned peers = __match_any_sync(FULL, key);
-    const int leader = __ffs(peers) - 1;
-    const int within = __popc(peers & ((1u << lane) - 1));
-    int basev = 0;
-    if (valid && lane == leader) basev = atomicAdd(&counts[key], __popc(peers));
-    basev = __shfl_sync(peers, basev, leader);
-    if (valid) {
-      bin_of[p] = key;
-      rank[p] = basev + within;
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      const bool valid = p < np;
+      int key = -1 - lane;  // unique per lane when invalid
+      if (valid) {
+        bool ok;
+        key = bin_of_position(g, b, x[u], y[u], z[u], ok);
+        if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+      }
+      int first, within, len;
+      run_ranks(key, lane, first, within, len);
+      int basev = 0;
+      if (valid && lane == first) basev = atomicAdd(&counts[key], len);
+      basev = __shfl_sync(FULL, basev, first);
+      if (valid) {
+        bin_of[p] = key;
+        rank[p] = basev + within;
+      }
     }
   }
 }
@@ -152,16 +183,29 @@ __global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
                                    double* __restrict__ pos_sorted,
                                    const int64_t* __restrict__ ids,
                                    int64_t* __restrict__ ids_sorted) {
+  // kCountUnroll particles per thread and trip: the dependent loads (bin,
+  // offset, then the payload) of several particles are in flight together
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += stride) {
-    const int64_t slot = (int64_t)offsets[bin_of[p]] + rank[p];
-    if (perm) perm[slot] = p;
-    if (pos_sorted) {
-      pos_sorted[slot] = pos[p];
-      pos_sorted[np + slot] = pos[np + p];
-      pos_sorted[2 * np + slot] = pos[2 * np + p];
+  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < np;
+       p0 += stride * kCountUnroll) {
+    int64_t slot[kCountUnroll];
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int64_t p = p0 + u * stride;
+      slot[u] = p < np ? (int64_t)offsets[bin_of[p]] + rank[p] : -1;
     }
-    if (ids_sorted) ids_sorted[slot] = ids[p];
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int64_t p = p0 + u * stride;
+      if (slot[u] < 0) continue;
+      if (perm) perm[slot[u]] = p;
+      if (pos_sorted) {
+        pos_sorted[slot[u]] = pos[p];
+        pos_sorted[np + slot[u]] = pos[np + p];
+        pos_sorted[2 * np + slot[u]] = pos[2 * np + p];
+      }
+      if (ids_sorted) ids_sorted[slot[u]] = ids[p];
+    }
   }
 }
 

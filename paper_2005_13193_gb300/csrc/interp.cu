@@ -55,7 +55,11 @@ __device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
                                                               const float* scale,
                                                               const GridArgs& g, int c,
                                                               int Pz, int Py, int Px) {
-  if constexpr (IsNode4<Tc>::value) {
+  if constexpr (IsNode16<Tc>::value) {
+    // component c of a 16-bit node, times its line's scale
+    const int64_t row = (int64_t)Pz * g.m[1] + Py;
+    return node16_value(coef[row * g.rx + Px].v[c]) * __ldg(scale + row * 4 + c);
+  } else if constexpr (IsNode4<Tc>::value) {
     // component c of node (Pz, Py, Px); the node's other components share
     // the 16-byte segment
     const int64_t node = ((int64_t)Pz * g.m[1] + Py) * g.rx + Px;
@@ -360,7 +364,8 @@ struct StagedArgs {
   double dt;
   float dtih[3];  // dt * n/L per axis
   int32_t* status;
-  CUtensorMap tmap;  // PS_F32X4 halo box (valid when tma == 1)
+  CUtensorMap tmap;   // node halo box (valid when tma == 1)
+  CUtensorMap tmap2;  // 16-bit nodes: the box of the halo rows' scales
 };
 
 // Halo geometry (extents, row and plane strides in float4 units).  KS > 0
@@ -412,6 +417,41 @@ __device__ __forceinline__ void tma_issue_halo(const CUtensorMap* map, float4* d
       "r"(smem_u32(mbar))
       : "memory");
 }
+// 16-bit node halos: the raw nodes and the rows' scales land after the
+// records (128-byte aligned), then every thread converts them to the float4
+// halo.  Offsets in bytes from the start of the dynamic shared memory.
+__host__ __device__ __forceinline__ size_t align128(size_t v) { return (v + 127) & ~size_t(127); }
+__host__ __device__ __forceinline__ size_t node16_raw_offset(int Sz, int PS, size_t rec_bytes) {
+  return align128((size_t)Sz * PS * 16 + rec_bytes);
+}
+__host__ __device__ __forceinline__ size_t node16_scale_offset(int Sz, int PS, int Sy, int SX,
+                                                               size_t rec_bytes) {
+  return align128(node16_raw_offset(Sz, PS, rec_bytes) + (size_t)Sz * Sy * SX * 8);
+}
+__device__ __forceinline__ void tma_issue_node16(const CUtensorMap* nodes,
+                                                 const CUtensorMap* scales, void* raw,
+                                                 void* sraw, unsigned long long* mbar,
+                                                 const int P0[3], unsigned bytes) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+  // node pairs are the 16-byte inner unit: x coordinate P0[0] / 2
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(raw)),
+      "l"(reinterpret_cast<unsigned long long>(nodes)), "r"(0), "r"(P0[0] >> 1), "r"(P0[1]),
+      "r"(P0[2]), "r"(smem_u32(mbar))
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sraw)),
+      "l"(reinterpret_cast<unsigned long long>(scales)), "r"(0), "r"(P0[1]), "r"(P0[2]),
+      "r"(smem_u32(mbar))
+      : "memory");
+}
+
 // Waits for phase 0 of the barrier, giving up after about 2^31 clocks (about a
 // second); returns whether the phase completed.
 __device__ __forceinline__ bool tma_wait(unsigned long long* mbar) {
@@ -471,7 +511,9 @@ __device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __rest
       for (int c = 0; c < NC; ++c) {
         float x = 0.f;
         if (act[u]) {
-          if constexpr (IsNode4<Tc>::value) {
+          if constexpr (IsNode16<Tc>::value) {
+            x = node16_value(coef[row * m0 + Px].v[c]) * __ldg(a.scale + row * 4 + c);
+          } else if constexpr (IsNode4<Tc>::value) {
             x = __ldg(reinterpret_cast<const float*>(coef + row * m0 + Px) + c);
           } else {
             x = (float)CoefLoad<Tc>::ld(coef + c * cs + row * m0 + Px);
@@ -532,17 +574,27 @@ __device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
 
 // Node coefficients: one 16-byte load and store per halo point, consecutive
 // threads along the rows.
-template <int KS>
-__device__ __forceinline__ void stage_nodes(const StagedArgs& a, const float4* __restrict__ coef,
+template <typename Tc, int KS>
+__device__ __forceinline__ void stage_nodes(const StagedArgs& a, const Tc* __restrict__ coef,
                                             const int P0[3], float4* halo) {
   const HaloGeo<KS> hg(a);
   const int64_t rx = a.g.rx, m1 = a.g.m[1];
-  const float4* b0 = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
+  const Tc* b0 = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
   const int nrow = hg.Sy * hg.Sz, npts = nrow * hg.Sx;
   for (int it = threadIdx.x; it < npts; it += blockDim.x) {
     const int r = it / hg.Sx, x = it - r * hg.Sx;
     const int lz = r / hg.Sy, ly = r - lz * hg.Sy;
-    halo[lz * hg.PS + ly * hg.SX + x] = __ldg(b0 + ((int64_t)lz * m1 + ly) * rx + x);
+    const int64_t roff = (int64_t)lz * m1 + ly;
+    if constexpr (IsNode16<Tc>::value) {
+      const Tc n = b0[roff * rx + x];
+      const float4 sc = __ldg(reinterpret_cast<const float4*>(a.scale) +
+                              ((int64_t)P0[2] * m1 + P0[1]) + roff);
+      halo[lz * hg.PS + ly * hg.SX + x] =
+          make_float4(node16_value(n.v[0]) * sc.x, node16_value(n.v[1]) * sc.y,
+                      node16_value(n.v[2]) * sc.z, 0.f);
+    } else {
+      halo[lz * hg.PS + ly * hg.SX + x] = __ldg(b0 + roff * rx + x);
+    }
   }
 }
 
@@ -550,7 +602,7 @@ template <typename Tc, int NC, int KS = 0>
 __device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __restrict__ coef,
                                                const int P0[3], float4* halo, bool sync = true) {
   if constexpr (IsNode4<Tc>::value) {
-    stage_nodes<KS>(a, coef, P0, halo);
+    stage_nodes<Tc, KS>(a, coef, P0, halo);
     if (sync) __syncthreads();
   } else {
     stage_halo_vec_planar<Tc, NC, KS>(a, coef, P0, halo, sync);
@@ -801,7 +853,8 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
                                               const int P0[3], const float4* halo,
                                               const Recs& R, double* pbuf,
                                               unsigned char* raw_next, int next_bin,
-                                              unsigned long long* mbar = nullptr) {
+                                              unsigned long long* mbar = nullptr,
+                                              const unsigned char* raw16 = nullptr) {
   constexpr bool GRAD = MODE == 1;
   bool copied = true;  // the halo's tensor copy completed (or there is none)
   const GridArgs& g = a.g;
@@ -847,6 +900,25 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
     if (mbar && cb == beg && !tma_wait(mbar)) {
       copied = false;
       if (threadIdx.x == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
+    }
+    if constexpr (IsNode16<Tc>::value) {
+      if (raw16 && cb == beg) {
+        // the copied 16-bit nodes and their rows' scales -> float4 halo; the
+        // copy's rows are SX nodes long, the halo's rows too (dense planes)
+        const Tc* nodes = reinterpret_cast<const Tc*>(raw16);
+        const float4* scl = reinterpret_cast<const float4*>(
+            raw16 + (node16_scale_offset(hg.Sz, hg.PS, hg.Sy, hg.SX, kRecBytes) -
+                     node16_raw_offset(hg.Sz, hg.PS, kRecBytes)));
+        float4* h = const_cast<float4*>(halo);
+        const int npts = hg.Sz * hg.Sy * hg.SX;
+        for (int it = threadIdx.x; it < npts; it += blockDim.x) {
+          const Tc n = nodes[it];
+          const float4 sc = scl[it / hg.SX];
+          h[it] = make_float4(node16_value(n.v[0]) * sc.x, node16_value(n.v[1]) * sc.y,
+                              node16_value(n.v[2]) * sc.z, 0.f);
+        }
+        __syncthreads();
+      }
     }
     // phase B: gathers, 8 lanes per particle; the loop is uniform per warp
     // (the butterfly uses full-warp shuffles), idle groups redo record b4
@@ -1219,7 +1291,7 @@ __device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4*
 // the location / gather / update phases of process_brick.
 template <typename Tc, int NC, int MODE, bool TMA = false>
 __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float4* smem,
-                                             const CUtensorMap* tmap = nullptr) {
+                                             const StagedArgs* maps = nullptr) {
   const int beg = a.offs[bin], end = a.offs[bin + 1];
   if (beg >= end) return;
   const int nbx = a.b.nb[0], nby = a.b.nb[1];
@@ -1237,14 +1309,26 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
     return;
   }
   if constexpr (TMA && IsNode4<Tc>::value) {
-    // `tmap` is a kernel argument or lies in global memory; the destination
-    // must be 128-byte aligned
-    if (a.tma && tmap && is_cube11_rows12(a) && (smem_u32(halo) & 127) == 0) {
+    // `maps` (with the tensor maps) is the kernel argument block or lies in
+    // global memory; the destinations must be 128-byte aligned
+    if (a.tma && maps && is_cube11_rows12(a) && (smem_u32(halo) & 127) == 0) {
       __shared__ __align__(8) unsigned long long mbar;
-      if (threadIdx.x == 0)
-        tma_issue_halo(tmap, halo, &mbar, P0,
-                       (unsigned)(sizeof(float4) * HaloGeo<12>::PS * HaloGeo<12>::Sz));
-      process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar);
+      using G = HaloGeo<12>;
+      if constexpr (IsNode16<Tc>::value) {
+        unsigned char* base = reinterpret_cast<unsigned char*>(smem);
+        unsigned char* raw = base + node16_raw_offset(G::Sz, G::PS, kRecBytes);
+        unsigned char* sraw = base + node16_scale_offset(G::Sz, G::PS, G::Sy, G::SX, kRecBytes);
+        if (threadIdx.x == 0)
+          tma_issue_node16(&maps->tmap, &maps->tmap2, raw, sraw, &mbar, P0,
+                           (unsigned)(G::Sz * G::Sy * (G::SX * 8 + 16)));
+        process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar,
+                                        raw);
+      } else {
+        if (threadIdx.x == 0)
+          tma_issue_halo(&maps->tmap, halo, &mbar, P0,
+                         (unsigned)(sizeof(float4) * G::PS * G::Sz));
+        process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar);
+      }
       return;
     }
   }
@@ -1274,7 +1358,7 @@ template <typename Tc, int NC, int MODE>
 __global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4)
     interp_staged(const __grid_constant__ StagedArgs a) {
   extern __shared__ __align__(128) float4 smem_a128[];
-  brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128, &a.tmap);
+  brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128, &a);
 }
 
 // The warp-autonomous form ("brick_kernel" 3): no particle records, no block
@@ -1309,12 +1393,17 @@ __global__ void __launch_bounds__(256, 3)
     reinterpret_cast<int4*>(&sa)[i] = reinterpret_cast<const int4*>(tab + lo)[i];
   // the field's tensor map stays in the global table (a tensor copy cannot
   // name one in shared memory); order its upload before the copy proxy
-  if (threadIdx.x == 0 && IsNode4<Tc>::value && tab[lo].tma)
+  if (threadIdx.x == 0 && IsNode4<Tc>::value && tab[lo].tma) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
                      reinterpret_cast<unsigned long long>(&tab[lo].tmap))
                  : "memory");
+    if (IsNode16<Tc>::value)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                       reinterpret_cast<unsigned long long>(&tab[lo].tmap2))
+                   : "memory");
+  }
   __syncthreads();
-  brick_phased<Tc, NC, MODE, true>(sa, b - bin_base[lo], smem_b128, &tab[lo].tmap);
+  brick_phased<Tc, NC, MODE, true>(sa, b - bin_base[lo], smem_b128, tab + lo);
 }
 
 // ------------------------------------------------- thread per particle ----
@@ -1684,16 +1773,19 @@ ps_status with_coef_type(ps_dtype t, F&& f) {
     case PS_BF16: return f(__nv_bfloat16{});
     case PS_F16: return f(__half{});
     case PS_F32X4: return f(float4{});
+    case PS_BF16X4: return f(bf16x4{});
+    case PS_F16X4: return f(f16x4{});
   }
   return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype %d", (int)t);
 }
 
 ps_status check_coef(ps_dtype coef_t, const void* coef, const float* scale) {
   if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16 &&
-      coef_t != PS_F32X4)
+      coef_t != PS_F32X4 && coef_t != PS_BF16X4 && coef_t != PS_F16X4)
     return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype %d", (int)coef_t);
   if (!coef) return fail(PS_ERR_INVALID_ARG, "coef is NULL");
-  if ((coef_t == PS_BF16 || coef_t == PS_F16) && !scale)
+  if ((coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_BF16X4 || coef_t == PS_F16X4) &&
+      !scale)
     return fail(PS_ERR_INVALID_ARG, "scale required for BF16/F16 coefficients");
   return PS_OK;
 }
@@ -1723,8 +1815,8 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   for (int d = 0; d < 3; ++d) vec = vec && grid->n[d] % a->b.B[d] == 0;
   const int qx = (a->S[0] + V - 1) / (V > 0 ? V : 1);
   vec = vec && qx <= 4 && (a->b.nb[0] - 1) * a->b.B[0] + qx * V <= a->g.rx;
-  if (coef_t == PS_F32X4) {
-    // node rows: any x offset is a whole 16-byte node; the halo stays inside
+  if (coef_t == PS_F32X4 || coef_t == PS_BF16X4 || coef_t == PS_F16X4) {
+    // node rows: any x offset is a whole node; the halo stays inside
     // the padded array when the bricks tile the grid
     vec = E == 0;
     for (int d = 0; d < 3; ++d) vec = vec && grid->n[d] % a->b.B[d] == 0;
@@ -1739,15 +1831,20 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   }
   a->vec = vec ? 1 : 0;
   a->tma = 0;
+  const bool n16 = coef_t == PS_BF16X4 || coef_t == PS_F16X4;
   a->min_stage = tuning().brick_min_stage;
   *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + kRecBytes;
+  // room for a tensor copy of 16-bit nodes and their rows' scales
+  if (n16 && vec)
+    *smem = node16_scale_offset(a->S[2], a->PS, a->S[1], a->SX, kRecBytes) +
+            (size_t)a->S[2] * a->S[1] * 16;
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
 }
 
 // Tensor map of the node halo box (4 floats x SX nodes x S[1] rows x S[2]
 // planes) over the PS_F32X4 array; the driver's encoder is looked up once.
-bool encode_node_halo_map(StagedArgs* a) {
+bool encode_node_halo_map(StagedArgs* a, ps_dtype coef_t) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static bool looked = false;
   static std::mutex mu;
@@ -1767,13 +1864,35 @@ bool encode_node_halo_map(StagedArgs* a) {
   }
   if (!encode) return false;
   const GridArgs& g = a->g;
-  const cuuint64_t dims[4] = {4, (cuuint64_t)g.rx, (cuuint64_t)g.m[1], (cuuint64_t)g.m[2]};
-  const cuuint64_t strides[3] = {16, (cuuint64_t)g.rx * 16, (cuuint64_t)g.rx * g.m[1] * 16};
-  const cuuint32_t box[4] = {4, (cuuint32_t)a->SX, (cuuint32_t)a->S[1], (cuuint32_t)a->S[2]};
   const cuuint32_t unit[4] = {1, 1, 1, 1};
-  return encode(&a->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(a->coef), dims,
-                strides, box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  const cuuint64_t m1 = (cuuint64_t)g.m[1], m2 = (cuuint64_t)g.m[2], rx = (cuuint64_t)g.rx;
+  if (coef_t == PS_F32X4) {
+    const cuuint64_t dims[4] = {4, rx, m1, m2};
+    const cuuint64_t strides[3] = {16, rx * 16, rx * m1 * 16};
+    const cuuint32_t box[4] = {4, (cuuint32_t)a->SX, (cuuint32_t)a->S[1], (cuuint32_t)a->S[2]};
+    return encode(&a->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(a->coef),
+                  dims, strides, box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  // 16-bit nodes: pairs of nodes (16 bytes) are the inner unit; rx is even
+  const cuuint64_t dims[4] = {8, rx / 2, m1, m2};
+  const cuuint64_t strides[3] = {16, rx * 8, rx * m1 * 8};
+  const cuuint32_t box[4] = {8, (cuuint32_t)a->SX / 2, (cuuint32_t)a->S[1],
+                             (cuuint32_t)a->S[2]};
+  const CUtensorMapDataType t =
+      coef_t == PS_BF16X4 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  if (encode(&a->tmap, t, 4, const_cast<void*>(a->coef), dims, strides, box, unit,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  // the rows' scales (s_u, s_v, s_w, 1): [m2][m1][4] floats
+  const cuuint64_t sdims[3] = {4, m1, m2};
+  const cuuint64_t sstrides[2] = {16, m1 * 16};
+  const cuuint32_t sbox[3] = {4, (cuuint32_t)a->S[1], (cuuint32_t)a->S[2]};
+  return encode(&a->tmap2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(a->scale),
+                sdims, sstrides, sbox, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1781,10 +1900,14 @@ bool encode_node_halo_map(StagedArgs* a) {
 // rows fit the copy layout and the array is 16-byte aligned.
 void attach_tma(StagedArgs* a, ps_dtype coef_t) {
   a->tma = 0;
-  if (coef_t != PS_F32X4 || !a->vec || !tuning().node_tma) return;
+  const bool n16 = coef_t == PS_BF16X4 || coef_t == PS_F16X4;
+  if ((coef_t != PS_F32X4 && !n16) || !a->vec || !tuning().node_tma) return;
   if ((a->SX * a->S[1]) % 8 != 4 || a->SX > 256 || a->S[1] > 256 || a->S[2] > 256) return;
   if (!a->coef || (reinterpret_cast<uintptr_t>(a->coef) & 15)) return;
-  a->tma = encode_node_halo_map(a) ? 1 : 0;
+  if (n16 && ((a->SX & 1) || (a->b.B[0] & 1) || (a->g.rx & 1) || !a->scale ||
+              (reinterpret_cast<uintptr_t>(a->scale) & 15)))
+    return;
+  a->tma = encode_node_halo_map(a, coef_t) ? 1 : 0;
 }
 
 template <typename Tc, int NC, int MODE>
@@ -1900,7 +2023,7 @@ ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_b
                               cudaStream_t st) {
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
-    if constexpr (sizeof(Tc) == 8) {
+    if constexpr (std::is_same<Tc, double>::value) {
       return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
     } else {
       auto kern = interp_staged_batch<Tc, 3, 2>;
@@ -1967,7 +2090,7 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
   a.status = status;
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
-    if constexpr (sizeof(Tc) == 8) return PS_ERR_UNSUPPORTED;
+    if constexpr (std::is_same<Tc, double>::value) return PS_ERR_UNSUPPORTED;
     else return launch_staged<Tc, 3, 2>(a, smem, st);
   });
 }
@@ -1984,8 +2107,8 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
-  if (coef_t == PS_F32X4 && ncomp != 3)
-    return fail(PS_ERR_INVALID_ARG, "PS_F32X4 coefficients need ncomp == 3");
+  if ((coef_t == PS_F32X4 || coef_t == PS_BF16X4 || coef_t == PS_F16X4) && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "node coefficients need ncomp == 3");
   if ((rc = check_coef(coef_t, coef, scale))) return rc;
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np == 0) return PS_OK;
@@ -2032,7 +2155,7 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   a.status = status;
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
-    if constexpr (sizeof(Tc) == 8) {
+    if constexpr (std::is_same<Tc, double>::value) {
       return PS_ERR_UNSUPPORTED;
     } else {
       if (ncomp == 3)
@@ -2052,8 +2175,8 @@ extern "C" ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
-  if (coef_t == PS_F32X4 && ncomp != 3)
-    return fail(PS_ERR_INVALID_ARG, "PS_F32X4 coefficients need ncomp == 3");
+  if ((coef_t == PS_F32X4 || coef_t == PS_BF16X4 || coef_t == PS_F16X4) && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "node coefficients need ncomp == 3");
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np > 0 && (!pos || !g_vel)) return fail(PS_ERR_INVALID_ARG, "pos and g_vel required");
   cudaStream_t st = as_stream(stream);

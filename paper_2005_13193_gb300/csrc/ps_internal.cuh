@@ -257,6 +257,22 @@ template <typename Tc> struct IsQuant { static constexpr bool value = false; };
 // float4 coefficients: one 16-byte node (u, v, w, 0) per grid point (PS_F32X4).
 template <typename Tc> struct IsNode4 { static constexpr bool value = false; };
 template <> struct IsNode4<float4> { static constexpr bool value = true; };
+// 16-bit nodes (PS_BF16X4, PS_F16X4): four values in 8 bytes, scaled per
+// component and x-line.
+template <typename H> struct alignas(8) Node16 {
+  H v[4];
+};
+using bf16x4 = Node16<__nv_bfloat16>;
+using f16x4 = Node16<__half>;
+template <> struct IsNode4<bf16x4> { static constexpr bool value = true; };
+template <> struct IsNode4<f16x4> { static constexpr bool value = true; };
+template <> struct IsQuant<bf16x4> { static constexpr bool value = true; };
+template <> struct IsQuant<f16x4> { static constexpr bool value = true; };
+template <typename Tc> struct IsNode16 { static constexpr bool value = false; };
+template <> struct IsNode16<bf16x4> { static constexpr bool value = true; };
+template <> struct IsNode16<f16x4> { static constexpr bool value = true; };
+__device__ __forceinline__ float node16_value(__nv_bfloat16 h) { return __bfloat162float(h); }
+__device__ __forceinline__ float node16_value(__half h) { return __half2float(h); }
 template <> struct IsQuant<__nv_bfloat16> { static constexpr bool value = true; };
 template <> struct IsQuant<__half> { static constexpr bool value = true; };
 

@@ -43,10 +43,11 @@ extern "C" ps_status ps_rk2_step(const ps_grid* grid, ps_dtype coef_t, const voi
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_BF16 && coef_t != PS_F16 &&
-      coef_t != PS_F32X4)
+      coef_t != PS_F32X4 && coef_t != PS_BF16X4 && coef_t != PS_F16X4)
     return fail(PS_ERR_INVALID_ARG, "bad coefficient dtype");
   if (!coef_n) return fail(PS_ERR_INVALID_ARG, "coef_n is NULL");
-  const bool quant = coef_t == PS_BF16 || coef_t == PS_F16;
+  const bool quant = coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_BF16X4 ||
+                     coef_t == PS_F16X4;
   if (quant && (!scale_n || (coef_np1 && !scale_np1)))
     return fail(PS_ERR_INVALID_ARG, "scales required for BF16/F16 coefficients");
   if (np < 0 || np >= ((int64_t)1 << 31)) return fail(PS_ERR_INVALID_ARG, "np out of range");

@@ -311,13 +311,35 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
     }
 }
 
-// x pass writing PS_F32X4 nodes: a block of three warps takes one (z, y)
+// x pass writing node coefficients: a block of three warps takes one (z, y)
 // line; warp c solves component c in its skewed buffer, then the block writes
-// the padded row and its periodic images as 16-byte nodes (u, v, w, 0).
-template <typename T, int LMAX>
-__global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, float4* dst, int nx,
-                                                    int ny, int nz, int L, T z, T gain) {
+// the padded row (rx nodes, the tail zero) and its periodic images as nodes
+// (u, v, w, 0): float4, or 16-bit values divided by the power-of-two scale of
+// their component's line, the scales stored as (s_u, s_v, s_w, 1) per row.
+template <typename NodeT> struct NodeOut;
+template <> struct NodeOut<float4> {
+  static __device__ __forceinline__ float4 make(float a, float b, float c) {
+    return make_float4(a, b, c, 0.f);
+  }
+};
+template <typename H> struct NodeOut<Node16<H>> {
+  static __device__ __forceinline__ Node16<H> make(float a, float b, float c) {
+    Node16<H> n;
+    n.v[0] = cvt_out<H>(a);
+    n.v[1] = cvt_out<H>(b);
+    n.v[2] = cvt_out<H>(c);
+    n.v[3] = cvt_out<H>(0.f);
+    return n;
+  }
+};
+
+template <typename T, int LMAX, typename NodeT>
+__global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, NodeT* dst,
+                                                    float* scale4, int64_t rx, int nx, int ny,
+                                                    int nz, int L, T z, T gain) {
+  constexpr bool Q = IsNode16<NodeT>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float line_scale[3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * (L + 1);
   const int64_t row = blockIdx.x;
@@ -326,7 +348,8 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, float
   const T* sp = src + sv.off + warp * sv.sc + zz * sv.sz + yy * sv.sy;
   for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
   __syncwarp();
-  line_solve<T, LMAX, false>(buf, nx, L, lane, z, gain);
+  const float sc = line_solve<T, LMAX, Q>(buf, nx, L, lane, z, gain);
+  if (lane == 0) line_scale[warp] = sc;
   __syncthreads();
   const T* b0 = reinterpret_cast<const T*>(smem_raw);
   const T* b1 = b0 + 32 * (L + 1);
@@ -341,14 +364,22 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, float
   if (zz == nz - 1) pzs[npz++] = 0;
   else if (zz == 0) pzs[npz++] = nz + 1;
   else if (zz == 1) pzs[npz++] = nz + 2;
-  const int64_t mx = nx + 3;
   for (int iz = 0; iz < npz; ++iz)
     for (int iy = 0; iy < npy; ++iy) {
-      float4* orow = dst + ((int64_t)pzs[iz] * (ny + 3) + pys[iy]) * mx;
-      for (int P = threadIdx.x; P < nx + 3; P += blockDim.x) {
-        const int e = skew(padded_to_node(P, nx), inv_L);
-        orow[P] = make_float4((float)b0[e], (float)b1[e], (float)b2[e], 0.f);
+      const int64_t r = (int64_t)pzs[iz] * (ny + 3) + pys[iy];
+      NodeT* orow = dst + r * rx;
+      for (int P = threadIdx.x; P < rx; P += blockDim.x) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        if (P < nx + 3) {
+          const int e = skew(padded_to_node(P, nx), inv_L);
+          a = (float)b0[e];
+          b = (float)b1[e];
+          c = (float)b2[e];
+        }
+        orow[P] = NodeOut<NodeT>::make(a, b, c);
       }
+      if (Q && threadIdx.x < 4)
+        scale4[r * 4 + threadIdx.x] = threadIdx.x < 3 ? line_scale[threadIdx.x] : 1.f;
     }
 }
 
@@ -450,11 +481,11 @@ ps_status launch_x(const T* src, View sv, Tout* dst, View dv, float* scale, int 
   return fail(PS_ERR_UNSUPPORTED, "FP64 solve supports n <= 1024");
 }
 
-template <int LMAX>
-ps_status launch_x_node4_l(const float* src, View sv, float4* dst, int nx, int ny, int nz,
-                           int L, float z, float gain, cudaStream_t st) {
+template <int LMAX, typename NodeT>
+ps_status launch_x_node4_l(const float* src, View sv, NodeT* dst, float* scale4, int64_t rx,
+                           int nx, int ny, int nz, int L, float z, float gain, cudaStream_t st) {
   const size_t smem = (size_t)3 * 32 * (L + 1) * sizeof(float);
-  auto kern = solve_x_node4<float, LMAX>;
+  auto kern = solve_x_node4<float, LMAX, NodeT>;
   if (smem > 48 * 1024) {
     ps_status rc = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -462,19 +493,22 @@ ps_status launch_x_node4_l(const float* src, View sv, float4* dst, int nx, int n
     if (rc) return rc;
   }
   const int64_t rows = (int64_t)ny * nz;
-  kern<<<(unsigned)rows, 96, smem, st>>>(src, sv, dst, nx, ny, nz, L, z, gain);
+  kern<<<(unsigned)rows, 96, smem, st>>>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain);
   return check_launch("solve_x_node4");
 }
 
-ps_status launch_x_node4(const float* src, View sv, float4* dst, int nx, int ny, int nz,
-                         float z, float gain, cudaStream_t st) {
+template <typename NodeT>
+ps_status launch_x_node4(const float* src, View sv, NodeT* dst, float* scale4, int64_t rx,
+                         int nx, int ny, int nz, float z, float gain, cudaStream_t st) {
   const int L = x_chunk(nx);
-  if (L <= 2) return launch_x_node4_l<2>(src, sv, dst, nx, ny, nz, L, z, gain, st);
-  if (L <= 4) return launch_x_node4_l<4>(src, sv, dst, nx, ny, nz, L, z, gain, st);
-  if (L <= 8) return launch_x_node4_l<8>(src, sv, dst, nx, ny, nz, L, z, gain, st);
-  if (L <= 16) return launch_x_node4_l<16>(src, sv, dst, nx, ny, nz, L, z, gain, st);
-  if (L <= 32) return launch_x_node4_l<32>(src, sv, dst, nx, ny, nz, L, z, gain, st);
-  return launch_x_node4_l<64>(src, sv, dst, nx, ny, nz, L, z, gain, st);
+  if (L <= 2) return launch_x_node4_l<2>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
+  if (L <= 4) return launch_x_node4_l<4>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
+  if (L <= 8) return launch_x_node4_l<8>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
+  if (L <= 16)
+    return launch_x_node4_l<16>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
+  if (L <= 32)
+    return launch_x_node4_l<32>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
+  return launch_x_node4_l<64>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
 }
 
 View unpadded_view(const ps_grid* g) {
@@ -511,9 +545,9 @@ ps_status run_solve(const ps_grid* g, int ncomp, const Tin* field, View fv, T* i
 }
 
 // y and z passes into the unpadded FP32 workspace, then the node x pass.
-template <typename Tin>
+template <typename Tin, typename NodeT>
 ps_status run_solve_node4(const ps_grid* g, const Tin* field, View fv, float* inter,
-                          float4* out, cudaStream_t st) {
+                          NodeT* out, float* scale4, int64_t rx, cudaStream_t st) {
   const double zd = sqrt(3.0) - 2.0;
   const float z = (float)zd, gain = (float)(-6.0 * zd);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
@@ -523,7 +557,7 @@ ps_status run_solve_node4(const ps_grid* g, const Tin* field, View fv, float* in
   rc = launch_strided<float, float>(inter, fv, fv.sy, fv.sz, inter, fv, fv.sy, fv.sz, nx, nz, ny,
                                     3, z, gain, st);
   if (rc) return rc;
-  return launch_x_node4(inter, fv, out, nx, ny, nz, z, gain, st);
+  return launch_x_node4(inter, fv, out, scale4, rx, nx, ny, nz, z, gain, st);
 }
 
 }  // namespace
@@ -541,7 +575,8 @@ using namespace ps;
 extern "C" size_t ps_spline_coeffs_workspace_size(const ps_grid* grid, int ncomp,
                                                   ps_dtype coef_t) {
   if (!grid || ncomp < 1) return 0;
-  if (coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_F32X4)
+  if (coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_F32X4 || coef_t == PS_BF16X4 ||
+      coef_t == PS_F16X4)
     return align_up((size_t)ncomp * (size_t)grid_volume(grid) * sizeof(float), 256) + 256;
   return 0;
 }
@@ -556,11 +591,13 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
   if (!field || !coef) return fail(PS_ERR_INVALID_ARG, "field and coef must be non-NULL");
   if (field_t != PS_F32 && field_t != PS_F64)
     return fail(PS_ERR_INVALID_ARG, "field dtype must be F32 or F64");
-  const bool quant = coef_t == PS_BF16 || coef_t == PS_F16;
-  if (coef_t != PS_F32 && coef_t != PS_F64 && coef_t != PS_F32X4 && !quant)
+  const bool node = coef_t == PS_F32X4 || coef_t == PS_BF16X4 || coef_t == PS_F16X4;
+  const bool quant = coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_BF16X4 ||
+                     coef_t == PS_F16X4;
+  if (coef_t != PS_F32 && coef_t != PS_F64 && !node && !quant)
     return fail(PS_ERR_INVALID_ARG, "bad coef dtype");
-  if (coef_t == PS_F32X4 && ncomp != 3)
-    return fail(PS_ERR_INVALID_ARG, "PS_F32X4 coefficients need ncomp == 3");
+  if (node && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "node coefficients need ncomp == 3");
   if (quant && !scale) return fail(PS_ERR_INVALID_ARG, "scale required for BF16/F16");
   if (coef_t == PS_F64)
     for (int d = 0; d < 3; ++d)
@@ -594,8 +631,18 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
   float* inter = static_cast<float*>(ws);
   if (coef_t == PS_F32X4) {
     float4* c = static_cast<float4*>(coef);
-    return field_t == PS_F32 ? run_solve_node4<float>(grid, ff, fv, inter, c, st)
-                             : run_solve_node4<double>(grid, fd, fv, inter, c, st);
+    return field_t == PS_F32 ? run_solve_node4<float>(grid, ff, fv, inter, c, nullptr, rx, st)
+                             : run_solve_node4<double>(grid, fd, fv, inter, c, nullptr, rx, st);
+  }
+  if (coef_t == PS_BF16X4) {
+    bf16x4* c = static_cast<bf16x4*>(coef);
+    return field_t == PS_F32 ? run_solve_node4<float>(grid, ff, fv, inter, c, scale, rx, st)
+                             : run_solve_node4<double>(grid, fd, fv, inter, c, scale, rx, st);
+  }
+  if (coef_t == PS_F16X4) {
+    f16x4* c = static_cast<f16x4*>(coef);
+    return field_t == PS_F32 ? run_solve_node4<float>(grid, ff, fv, inter, c, scale, rx, st)
+                             : run_solve_node4<double>(grid, fd, fv, inter, c, scale, rx, st);
   }
   if (coef_t == PS_BF16) {
     __nv_bfloat16* c = static_cast<__nv_bfloat16*>(coef);

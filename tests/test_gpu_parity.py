@@ -514,3 +514,43 @@ def test_node4_tensor_copy_matches_loads():
     finally:
         ps.ps_tune_set("node_tma", old)
     assert rel_err(outs[0][0].cpu().numpy(), oracle.interp(cref, pos)) <= 1e-5
+
+
+@pytest.mark.parametrize("planar,node", [(torch.bfloat16, "bf16x4"), (torch.float16, "f16x4")])
+@pytest.mark.parametrize("n", [(64, 32, 48), (37, 21, 10)])
+def test_node16_storage_matches_planar(planar, node, n):
+    # 16-bit nodes hold the planar 16-bit values and per-line scales: every
+    # path (direct, staged by tensor copy or by loads, Heun steps) agrees with
+    # the planar form bit for bit, and both stay within the rounding bound.
+    field, pos, cref = _case(n, 20000, seed=161, spread=1.2)
+    f = torch.from_numpy(field).to(DEV)
+    pp = ps.SplineField.from_field(f, planar)
+    pn = ps.SplineField.from_field(f, node)
+    assert pn.coef.dtype == planar and pn.coef.shape[-1] == 4
+    assert torch.equal(pn.padded(), pp.padded())
+    assert torch.equal(pn.scale[..., :3].permute(2, 0, 1), pp.scale)
+    assert torch.count_nonzero(pn.coef[..., 3].float()) == 0
+    pg = torch.from_numpy(pos).to(DEV)
+    va, ga = pp.interp(pg, grad=True)
+    vb, gb = pn.interp(pg, grad=True)
+    assert torch.equal(va, vb) and torch.equal(ga, gb)
+    bins, sorted_pos = ps.bin_particles(n, (8, 8, 8), pg, want_sorted=True)
+    old = ps.ps_tune_get("node_tma")
+    try:
+        for on in (1, 0):
+            ps.ps_tune_set("node_tma", on)
+            st = torch.zeros(4, dtype=torch.int32, device=DEV)
+            assert torch.equal(pp.interp(pg, bins=bins), pn.interp(pg, bins=bins, status=st))
+            assert ps.ps_status_read(st)[0] == 0
+            outs = []
+            for sf in (pp, pn):
+                tr = ps.Tracker(sf, sorted_pos.clone(), brick=(8, 8, 8))
+                tr.step(1e-2)
+                lab = torch.empty_like(tr.ids)
+                lab[tr.ids] = torch.arange(tr.ids.numel(), device=DEV)
+                outs.append((tr.pos[:, lab], tr.vel[:, lab]))
+            assert all(torch.equal(x, y) for x, y in zip(*outs))
+    finally:
+        ps.ps_tune_set("node_tma", old)
+    ulp = 2.0 ** -8 if planar == torch.bfloat16 else 2.0 ** -10
+    assert abs_err(vb.cpu().numpy(), oracle.interp(cref, pos)) <= ulp * np.abs(cref).max()
