@@ -112,7 +112,7 @@ extern "C" const char* ps_last_error(void) { return g_err; }
 extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
   if (!key) return fail(PS_ERR_INVALID_ARG, "key is NULL");
   if (!strcmp(key, "brick_kernel")) {
-    if (value < 0 || value > 3) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0, 1, 2 or 3");
+    if (value < 0 || value > 4) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0 to 4");
     tuning().brick_kernel = (int)value;
     return PS_OK;
   }

@@ -402,6 +402,25 @@ __device__ __forceinline__ bool is_cube11_rows12(const StagedArgs& a) {
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void tma_init_barrier(unsigned long long* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Arms the barrier's current phase with the box's byte count and issues the
+// copy (the barrier was initialised before).
+__device__ __forceinline__ void tma_copy_halo(const CUtensorMap* map, float4* dst,
+                                              unsigned long long* mbar, const int P0[3],
+                                              unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(0), "r"(P0[0]), "r"(P0[1]), "r"(P0[2]),
+      "r"(smem_u32(mbar))
+      : "memory");
+}
 __device__ __forceinline__ void tma_issue_halo(const CUtensorMap* map, float4* dst,
                                                unsigned long long* mbar, const int P0[3],
                                                unsigned bytes) {
@@ -452,18 +471,18 @@ __device__ __forceinline__ void tma_issue_node16(const CUtensorMap* nodes,
       : "memory");
 }
 
-// Waits for phase 0 of the barrier, giving up after about 2^31 clocks (about a
-// second); returns whether the phase completed.
-__device__ __forceinline__ bool tma_wait(unsigned long long* mbar) {
+// Waits for the barrier's phase of the given parity, giving up after about
+// 2^31 clocks (about a second); returns whether the phase completed.
+__device__ __forceinline__ bool tma_wait(unsigned long long* mbar, unsigned parity = 0) {
   const unsigned a = smem_u32(mbar);
   const long long t0 = clock64();
   while (true) {
     unsigned done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a)
+        : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > (1ll << 31)) return false;
@@ -699,8 +718,8 @@ __device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
 //   loc[d][i]  int     brick-local stencil start along d, -1 = outside halo
 //   cell[d][i] int     global cell along d, -1 = position not finite
 //   u[i]       float4  (u, v, w, ok) result of the last gather
-constexpr int kRecords = 128;  // particles per round
-constexpr int kThreads = 256;  // threads per brick CTA
+constexpr int kRecords = 64;   // particles per round
+constexpr int kThreads = 128;  // threads per brick CTA
 
 struct Recs {
   float4* f;  // b[3], db[3], u: 7 * kRecords float4
@@ -854,7 +873,8 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
                                               const Recs& R, double* pbuf,
                                               unsigned char* raw_next, int next_bin,
                                               unsigned long long* mbar = nullptr,
-                                              const unsigned char* raw16 = nullptr) {
+                                              const unsigned char* raw16 = nullptr,
+                                              unsigned parity = 0) {
   constexpr bool GRAD = MODE == 1;
   bool copied = true;  // the halo's tensor copy completed (or there is none)
   const GridArgs& g = a.g;
@@ -897,7 +917,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       if (raw_next && cb == beg) issue_brick<Tc, NC>(a, next_bin, raw_next, pbuf);
     // the barrier above also ordered the mbarrier's initialisation before
     // these waits; a copy that never completes is reported, not waited for
-    if (mbar && cb == beg && !tma_wait(mbar)) {
+    if (mbar && cb == beg && !tma_wait(mbar, parity)) {
       copied = false;
       if (threadIdx.x == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
     }
@@ -1007,7 +1027,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
     }  // MODE == 2
   }
   // a copy still in flight must land before the block's memory is released
-  if (!copied) tma_wait(mbar);
+  if (!copied) tma_wait(mbar, parity);
 }
 
 // ------------------------------------------------ warp-autonomous form ----
@@ -1355,7 +1375,7 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
 // argument block is a grid constant so that its tensor map can be named by
 // the tensor copy.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, sizeof(Tc) == 2 ? 6 : 7)
     interp_staged(const __grid_constant__ StagedArgs a) {
   extern __shared__ __align__(128) float4 smem_a128[];
   brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128, &a);
@@ -1364,15 +1384,77 @@ __global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4)
 // The warp-autonomous form ("brick_kernel" 3): no particle records, no block
 // barrier after the staging.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(Tc) == 2 ? 3 : 4) interp_staged_warp(StagedArgs a) {
+__global__ void __launch_bounds__(kThreads, sizeof(Tc) == 2 ? 6 : 7) interp_staged_warp(StagedArgs a) {
   extern __shared__ float4 smem[];
   brick_body<Tc, NC, MODE>(a, blockIdx.x, smem);
+}
+
+__device__ __forceinline__ int next_busy(const StagedArgs& a, int bin);
+__device__ __forceinline__ void brick_origin(const StagedArgs& a, int bin, int P0[3]);
+
+// Persistent pipelined form for node coefficients ("brick_kernel" 4): each
+// block walks bricks blockIdx.x, + gridDim.x, ...; while it processes one,
+// the tensor copy of its next non-empty brick's halo fills the other of two
+// halo buffers, each with its own mbarrier whose phase parity alternates.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(kThreads, 6) interp_staged_pipe(const __grid_constant__ StagedArgs a) {
+  using G = HaloGeo<12>;
+  constexpr int HS = G::Sz * G::PS;        // float4 per halo
+  constexpr int HSP = (HS + 7) / 8 * 8;    // buffers 128-byte aligned
+  constexpr unsigned kBytes = (unsigned)(sizeof(float4) * HS);
+  extern __shared__ __align__(128) float4 smem_p[];
+  __shared__ __align__(8) unsigned long long mbar[2];
+  if constexpr (IsNode4<Tc>::value && !IsNode16<Tc>::value) {
+    float4* H[2] = {smem_p, smem_p + HSP};
+    const Recs R = carve_recs(smem_p + 2 * HSP);
+    const int nb = (int)a.b.nbins;
+    int bin = next_busy(a, blockIdx.x);
+    if (bin >= nb) return;
+    if (smem_u32(smem_p) & 127) {
+      // a tensor copy needs 128-byte aligned destinations: plain loads instead
+      for (; bin < nb; bin = next_busy(a, bin + gridDim.x)) {
+        int P0[3];
+        brick_origin(a, bin, P0);
+        stage_halo_vec<Tc, NC, 12>(a, static_cast<const Tc*>(a.coef), P0, H[0], false);
+        process_brick<Tc, NC, MODE, 12>(a, a.offs[bin], a.offs[bin + 1], P0, H[0], R, nullptr,
+                                        nullptr, 0);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) {
+      tma_init_barrier(&mbar[0]);
+      tma_init_barrier(&mbar[1]);
+      int P0[3];
+      brick_origin(a, bin, P0);
+      tma_copy_halo(&a.tmap, H[0], &mbar[0], P0, kBytes);
+    }
+    __syncthreads();  // the barriers' initialisation before any wait
+    unsigned parity[2] = {0u, 0u};
+    int c = 0;
+    while (bin < nb) {
+      const int next = next_busy(a, bin + gridDim.x);
+      // the other buffer's last reader was the previous brick, which ended with
+      // a block barrier
+      if (threadIdx.x == 0 && next < nb) {
+        int Pn[3];
+        brick_origin(a, next, Pn);
+        tma_copy_halo(&a.tmap, H[c ^ 1], &mbar[c ^ 1], Pn, kBytes);
+      }
+      int P0[3];
+      brick_origin(a, bin, P0);
+      process_brick<Tc, NC, MODE, 12>(a, a.offs[bin], a.offs[bin + 1], P0, H[c], R, nullptr,
+                                      nullptr, 0, &mbar[c], nullptr, parity[c]);
+      parity[c] ^= 1u;
+      c ^= 1;
+      bin = next;
+    }
+  }
 }
 
 // Many fields in one launch: block b handles global brick b; the field is the
 // last f with bin_base[f] <= b, and its parameters are copied to shared memory.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(kThreads, 5)
     interp_staged_batch(const StagedArgs* __restrict__ tab, const int* __restrict__ bin_base,
                         int nfields) {
   extern __shared__ __align__(128) float4 smem_b128[];
@@ -1945,6 +2027,22 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
     }
     tk<<<(unsigned)a.b.nbins, 64, hs, st>>>(a);
     return check_launch("interp_thread");
+  }
+  if constexpr (IsNode4<Tc>::value && !IsNode16<Tc>::value) {
+    if (tuning().brick_kernel == 4 && a.tma && a.E == 0 && a.S[0] == 11 && a.S[1] == 11 &&
+        a.S[2] == 11 && a.SX == 12 && a.PS == 132) {
+      auto pk = interp_staged_pipe<Tc, NC, MODE>;
+      const size_t sm = (size_t)2 * ((a.S[2] * a.PS + 7) / 8 * 8) * sizeof(float4) + kRecBytes;
+      if (sm > 48 * 1024) {
+        ps_status rc = check_cuda(
+            cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+            "pipelined smem attribute");
+        if (rc) return rc;
+      }
+      const int64_t grid = std::min<int64_t>(a.b.nbins, (int64_t)sm_count() * 4);
+      pk<<<(unsigned)grid, kThreads, sm, st>>>(a);
+      return check_launch("interp_staged_pipe");
+    }
   }
   if (tuning().brick_kernel == 3) {
     auto wk = interp_staged_warp<Tc, NC, MODE>;

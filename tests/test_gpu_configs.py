@@ -142,7 +142,8 @@ def test_precision_config_full_size():
     # 1536^3 FP32 field (k^-5/3, 1 <= |k| <= 512), 300,000,000 particles: one
     # coefficient solve, interpolation and one RK2 step (dt = 1e-3) with FP32,
     # BF16 and FP16 coefficients (BF16/FP16 with a power-of-two scale per
-    # x-line).  FP32 is checked against the windowed FP64 oracle on 4096
+    # x-line), planar and as interleaved nodes (identical values, so identical
+    # results).  FP32 is checked against the windowed FP64 oracle on 4096
     # particles with the bars above; BF16/FP16 against the FP32 result on a
     # seeded 1,000,000-particle subsample and against the oracle on the 4096,
     # at most 1e-2 (BF16) and 1e-3 (FP16) of the rms velocity, and within the
@@ -161,7 +162,7 @@ def test_precision_config_full_size():
     sub = torch.from_numpy(sub_h).to(DEV)
     bins = ps.bin_particles((N,) * 3, brick, pos)
     got, cmax = {}, None
-    for dtype in (torch.float32, torch.bfloat16, torch.float16):
+    for dtype in (torch.float32, torch.bfloat16, torch.float16, ps.F32X4, ps.BF16X4, ps.F16X4):
         sf = ps.SplineField.from_field(field, dtype)
         if dtype == torch.float32:
             cmax = max(float(sf.coef[c].abs().max()) for c in range(3))
@@ -187,6 +188,11 @@ def test_precision_config_full_size():
     u2 = oracle.interp_windowed(f_h, xk + dt * u1)
     x1 = xk + 0.5 * dt * (u1 + u2)
     rms = np.sqrt((u1 ** 2).mean())
+    # node storage holds the planar values: identical results
+    for planar, node in ((torch.float32, ps.F32X4), (torch.bfloat16, ps.BF16X4),
+                         (torch.float16, ps.F16X4)):
+        assert np.array_equal(got[planar][0], got[node][0])
+        assert np.array_equal(got[planar][1], got[node][1])
     u32, x32 = got[torch.float32]
     rms32 = np.sqrt((u32.astype(np.float64) ** 2).mean())
     report = {"rms_u": rms, "max_abs_c": cmax}

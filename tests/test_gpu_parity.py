@@ -463,7 +463,7 @@ def test_node4_storage_matches_planar(n, brick):
     bins, sorted_pos = ps.bin_particles(n, brick, pg, want_sorted=True)
     old = ps.ps_tune_get("brick_kernel")
     try:
-        for k in (0, 1, 2, 3):
+        for k in (0, 1, 2, 3, 4):
             ps.ps_tune_set("brick_kernel", k)
             assert torch.equal(p32.interp(pg, bins=bins), p4.interp(pg, bins=bins))
             va, ga = p32.interp(pg, grad=True, bins=bins)
