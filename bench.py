@@ -73,6 +73,17 @@ def parse():
     return args
 
 
+# Shared-memory wavefronts (128 B) per particle of the binned Heun step: two
+# 64-point float4 gathers (16) plus the particle records, as counted by ncu
+# (l1tex__data_pipe_lsu_wavefronts_mem_shared_op_{ld,st}) for the node form.
+SMEM_WAVEFRONTS = 24.2
+
+
+def smem_bound_ms(np_: int, sms: int = 152, clock_ghz: float = 2.07) -> float:
+    """Time the shared-memory pipe needs for the Heun step's wavefronts."""
+    return SMEM_WAVEFRONTS * np_ / (sms * clock_ghz * 1e9) * 1e3
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -273,7 +284,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic_for("rk2_staged_f32x4"),
-                     "alg_bytes_per_launch": rk_alg_bytes, "avg_launch_ms": rk_avg},
+                     "alg_bytes_per_launch": rk_alg_bytes, "avg_launch_ms": rk_avg,
+                     # the shared-memory pipe: one 128-byte wavefront per clock per SM;
+                     # SMEM_WAVEFRONTS per particle from the ncu summary in profiles/
+                     "smem_bound_ms": smem_bound_ms(NP),
+                     "frac_of_smem_bound": smem_bound_ms(NP) / rk_avg},
         "breakdown": {"solve_ms": solve_ms,
                       "solve_gbs_min_bytes": solve_min_bytes / (solve_ms * 1e-3) / 1e9,
                       "solve_gbs_pass_bytes": solve_pass_bytes / (solve_ms * 1e-3) / 1e9,

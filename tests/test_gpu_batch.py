@@ -39,7 +39,7 @@ def _by_label(x, ids):
     return out
 
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, ps.F32X4])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, ps.F32X4, ps.BF16X4])
 def test_batch_equals_per_field_runs(dtype):
     # the last field is sparse (about 4 particles per 8^3 brick): the plan
     # bins it in runs of particles and gathers from global memory
