@@ -66,6 +66,8 @@ def _load():
             lib.ora_interp_backward.argtypes = [P, P, i32, P, i64, P, P, P, P]
             lib.ora_rk2_step.argtypes = [P, P, P, P, i64, P, d, P]
             lib.ora_interp_windowed.argtypes = [P, P, P, i64, P, P]
+            lib.ora_interp_hessian.argtypes = [P, P, i32, P, i64, P, P]
+            lib.ora_lagrangian_accel.argtypes = [P, P, P, P, d, i64, P, P]
             lib.ora_basis.argtypes = [d, P, P]
             lib.ora_basis.restype = None
             lib.ora_locate.argtypes = [d, d, i32, P, P]
@@ -140,6 +142,34 @@ def interp(coef, pos, L=(2 * np.pi,) * 3, grad=False, allow_nonfinite=False):
                             _p(vel), _p(g) if grad else None)
     _check(rc, allow_nonfinite)
     return (vel, g) if grad else vel
+
+
+def interp_hessian(coef, pos, L=(2 * np.pi,) * 3, allow_nonfinite=False):
+    """Second derivatives of Eq. (spline): hess [ncomp][6][np] (xx, yy, zz, xy, xz, yz)."""
+    coef = _f64(coef)
+    pos = _f64(pos)
+    ncomp = coef.shape[0]
+    n_arr, L_arr = _grid([coef.shape[3] - 3, coef.shape[2] - 3, coef.shape[1] - 3], L)
+    npart = pos.shape[1]
+    hess = np.empty((ncomp, 6, npart), dtype=np.float64)
+    _check(_load().ora_interp_hessian(_p(n_arr), _p(L_arr), ncomp, _p(coef), npart, _p(pos),
+                                      _p(hess)), allow_nonfinite)
+    return hess
+
+
+def lagrangian_accel(coef_n, pos, coef_np1=None, dt_field=1.0, L=(2 * np.pi,) * 3):
+    """a = du/dt + (u . grad) u at the particles ([3][np]); du/dt by the two-field
+    difference when coef_np1 is given."""
+    coef_n = _f64(coef_n)
+    pos = _f64(pos)
+    n_arr, L_arr = _grid([coef_n.shape[3] - 3, coef_n.shape[2] - 3, coef_n.shape[1] - 3], L)
+    npart = pos.shape[1]
+    acc = np.empty((3, npart), dtype=np.float64)
+    c1 = _f64(coef_np1) if coef_np1 is not None else None
+    _check(_load().ora_lagrangian_accel(_p(n_arr), _p(L_arr), _p(coef_n),
+                                        _p(c1) if c1 is not None else None, float(dt_field),
+                                        npart, _p(pos), _p(acc)))
+    return acc
 
 
 def bin_particles(n, brick, pos, L=(2 * np.pi,) * 3):

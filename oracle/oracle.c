@@ -326,6 +326,98 @@ int ora_interp(const int32_t n[3], const double L[3], int ncomp,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Second derivatives of the interpolant (the spline is twice continuously  */
+/* differentiable, Sec. 2.2): d2 b_i / dt2 = (1-t), 3t-2, 1-3t, t for       */
+/* i = 0..3, and each derivative along axis d brings a factor n_d/L_d.      */
+/*   hess: [ncomp][6][np] in the order xx, yy, zz, xy, xz, yz.              */
+/* ------------------------------------------------------------------------ */
+static void ddbasis(double t, double d2[4]) {
+  d2[0] = 1.0 - t;
+  d2[1] = 3.0 * t - 2.0;
+  d2[2] = 1.0 - 3.0 * t;
+  d2[3] = t;
+}
+
+int ora_interp_hessian(const int32_t n[3], const double L[3], int ncomp,
+                       const double* coef, int64_t np, const double* pos, double* hess) {
+  if (ncomp < 1 || ncomp > 8) return ORA_ERR_ARG;
+  double inv_h[3];
+  inv_spacing(n, L, inv_h);
+  const int64_t mx = n[0] + 3, my = n[1] + 3, mz = n[2] + 3;
+  int err = ORA_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < np; ++p) {
+    int64_t cell[3];
+    double t[3], b[3][4], db[3][4], d2[3][4];
+    int bad = 0;
+    for (int d = 0; d < 3; ++d) {
+      if (locate(pos[d * np + p], inv_h[d], n[d], &cell[d], &t[d])) bad = 1;
+      basis(t[d], b[d]);
+      dbasis(t[d], db[d]);
+      ddbasis(t[d], d2[d]);
+    }
+    for (int c = 0; c < ncomp; ++c) {
+      double h[6] = {0, 0, 0, 0, 0, 0};
+      if (!bad) {
+        const double* C = coef + (int64_t)c * mx * my * mz;
+        for (int k = 0; k < 4; ++k)
+          for (int j = 0; j < 4; ++j)
+            for (int i = 0; i < 4; ++i) {
+              const double s = C[((cell[2] + k) * my + cell[1] + j) * mx + cell[0] + i];
+              h[0] += d2[0][i] * b[1][j] * b[2][k] * s;
+              h[1] += b[0][i] * d2[1][j] * b[2][k] * s;
+              h[2] += b[0][i] * b[1][j] * d2[2][k] * s;
+              h[3] += db[0][i] * db[1][j] * b[2][k] * s;
+              h[4] += db[0][i] * b[1][j] * db[2][k] * s;
+              h[5] += b[0][i] * db[1][j] * db[2][k] * s;
+            }
+        h[0] *= inv_h[0] * inv_h[0];
+        h[1] *= inv_h[1] * inv_h[1];
+        h[2] *= inv_h[2] * inv_h[2];
+        h[3] *= inv_h[0] * inv_h[1];
+        h[4] *= inv_h[0] * inv_h[2];
+        h[5] *= inv_h[1] * inv_h[2];
+      }
+      for (int e = 0; e < 6; ++e) hess[((int64_t)c * 6 + e) * np + p] = bad ? NAN : h[e];
+    }
+    if (bad) {
+#pragma omp atomic write
+      err = ORA_ERR_NONFINITE;
+    }
+  }
+  return err;
+}
+
+/* Lagrangian acceleration of fluid particles (Sec. 2.1: particles move with */
+/* the local fluid velocity): a = du/dt + (u . grad) u, the time derivative */
+/* taken as (u(x, t+dt) - u(x, t)) / dt from two fields when coef_np1 is    */
+/* given (else zero), the convective term from the field at t.  acc [3][np]. */
+int ora_lagrangian_accel(const int32_t n[3], const double L[3], const double* coef_n,
+                         const double* coef_np1, double dt_field, int64_t np,
+                         const double* pos, double* acc) {
+  double inv_h[3];
+  inv_spacing(n, L, inv_h);
+  int err = ORA_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < np; ++p) {
+    double x[3] = {pos[p], pos[np + p], pos[2 * np + p]};
+    double u[8], du[8][3], u1[8];
+    int rc = interp_one(n, inv_h, 3, coef_n, x, u, du);
+    if (!rc && coef_np1) rc = interp_one(n, inv_h, 3, coef_np1, x, u1, NULL);
+    for (int c = 0; c < 3; ++c) {
+      double a = du[c][0] * u[0] + du[c][1] * u[1] + du[c][2] * u[2];
+      if (coef_np1) a += (u1[c] - u[c]) / dt_field;
+      acc[(int64_t)c * np + p] = rc ? NAN : a;
+    }
+    if (rc) {
+#pragma omp atomic write
+      err = rc;
+    }
+  }
+  return err;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Binning: the single-device reading of the dynamic particle-to-process    */
 /* mapping by instantaneous position (Sec. 3).  Bricks of B cells per axis, */
 /* bin = (bz*nBy + by)*nBx + bx; stable counting sort.                      */

@@ -374,3 +374,109 @@ def test_nonfinite_position_is_reported():
     assert np.isnan(vel[:, 2]).all() and np.isfinite(vel[:, [0, 1, 3]]).all()
     with pytest.raises(oracle.OracleError):
         oracle.interp(coef, pos)
+
+
+# ----------------------------------------------------- second derivatives ----
+
+def test_hessian_matches_central_differences_of_the_gradient():
+    # d2u/dxa dxb from central differences (h = 1e-5) of the oracle's gradient,
+    # which is computed by a different sum (b' instead of b'')
+    n = (10, 12, 9)
+    coef = oracle.spline_coeffs(synth.random_field(n, ncomp=3, seed=18))
+    pos = synth.uniform_particles(512, seed=19)
+    hess = oracle.interp_hessian(coef, pos)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    hfd = 1e-5
+    for e, (a, b) in enumerate(pairs):
+        p1, p0 = pos.copy(), pos.copy()
+        p1[b] += hfd
+        p0[b] -= hfd
+        _, g1 = oracle.interp(coef, p1, grad=True)
+        _, g0 = oracle.interp(coef, p0, grad=True)
+        fd = (g1[:, a] - g0[:, a]) / (2 * hfd)
+        np.testing.assert_allclose(hess[:, e], fd, rtol=0, atol=1e-7 * np.abs(hess).max())
+
+
+def test_hessian_mixed_partials_commute():
+    # d/dy (du/dx) and d/dx (du/dy) from differences agree with the one stored
+    n = 12
+    coef = oracle.spline_coeffs(synth.random_field(n, ncomp=1, seed=20))
+    pos = synth.uniform_particles(256, seed=21)
+    hess = oracle.interp_hessian(coef, pos)
+    hfd = 1e-5
+    for e, (a, b) in ((3, (0, 1)), (4, (0, 2)), (5, (1, 2))):
+        outs = []
+        for da, db in ((a, b), (b, a)):
+            p1, p0 = pos.copy(), pos.copy()
+            p1[db] += hfd
+            p0[db] -= hfd
+            _, g1 = oracle.interp(coef, p1, grad=True)
+            _, g0 = oracle.interp(coef, p0, grad=True)
+            outs.append((g1[0, da] - g0[0, da]) / (2 * hfd))
+        np.testing.assert_allclose(outs[0], outs[1], rtol=0, atol=1e-7 * np.abs(hess).max())
+        np.testing.assert_allclose(hess[0, e], outs[0], rtol=0, atol=1e-7 * np.abs(hess).max())
+
+
+def test_hessian_is_linear_inside_a_cell():
+    # the cubic B-spline's second derivative is piecewise linear: along x
+    # inside one cell d2u/dx2 at the midpoint is the mean of the two ends
+    n = 8
+    coef = oracle.spline_coeffs(synth.random_field(n, ncomp=1, seed=22))
+    h = TWO_PI / n
+    rng = np.random.default_rng(3)
+    base = rng.uniform(0, TWO_PI, size=(3, 100))
+    cell = np.floor(base[0] / h)
+    lo, mid, hi = base.copy(), base.copy(), base.copy()
+    lo[0] = (cell + 0.1) * h
+    mid[0] = (cell + 0.5) * h
+    hi[0] = (cell + 0.9) * h
+    hl, hm, hh = (oracle.interp_hessian(coef, p)[0, 0] for p in (lo, mid, hi))
+    np.testing.assert_allclose(hm, 0.5 * (hl + hh), rtol=0, atol=1e-10 * np.abs(hm).max())
+
+
+def test_hessian_convergence():
+    # second derivatives of the interpolant of a smooth field converge at
+    # least at second order in h (d2/dx2 shows third order, the mixed one
+    # second, at random points); a wrong basis or scale does not converge
+    pos = synth.uniform_particles(400, seed=23)
+    x, y, z = pos
+    exact = -np.sin(x) * np.cos(2 * y) * np.sin(z + 0.4)          # d2u/dx2
+    exact_xy = -2 * np.cos(x) * np.sin(2 * y) * np.sin(z + 0.4)   # d2u/dxdy
+    errs, errs_xy = [], []
+    for n in (16, 32, 64):
+        hess = oracle.interp_hessian(oracle.spline_coeffs(_analytic_field(n)), pos)
+        errs.append(np.abs(hess[0, 0] - exact).max())
+        errs_xy.append(np.abs(hess[0, 3] - exact_xy).max())
+    for e in (errs, errs_xy):
+        r1, r2 = e[0] / e[1], e[1] / e[2]
+        assert r1 > 3.0 and r2 > 3.0, e  # first order would give 2
+        assert e[2] < 1e-3, e
+
+
+def test_lagrangian_accel_closed_forms():
+    n = 16
+    pos = synth.uniform_particles(300, seed=24)
+    # a spatially constant field changing in time: a = (u1 - u0) / dt exactly
+    f0 = np.ones((3, n, n, n)) * np.array([1.0, -2.0, 0.5])[:, None, None, None]
+    f1 = f0 * 1.5
+    acc = oracle.lagrangian_accel(oracle.spline_coeffs(f0), pos, oracle.spline_coeffs(f1), 0.25)
+    np.testing.assert_allclose(acc, (0.5 / 0.25) * f0[:, 0, 0, 0][:, None] * np.ones_like(acc),
+                               rtol=0, atol=1e-12)
+    # a steady shear flow u = (sin y, 0, 0) has no convective acceleration
+    h = TWO_PI / n
+    z, y, x = np.meshgrid(np.arange(n) * h, np.arange(n) * h, np.arange(n) * h, indexing="ij")
+    f = np.stack([np.sin(y), np.zeros_like(y), np.zeros_like(y)])
+    acc = oracle.lagrangian_accel(oracle.spline_coeffs(f), pos)
+    assert np.abs(acc).max() < 1e-12
+    # u = (sin y, sin z, 0): (u . grad) u = (sin z cos y, 0, 0), third order in h
+    errs = []
+    for n in (16, 32, 64):
+        h = TWO_PI / n
+        z, y, x = np.meshgrid(np.arange(n) * h, np.arange(n) * h, np.arange(n) * h,
+                              indexing="ij")
+        f = np.stack([np.sin(y), np.sin(z), np.zeros_like(y)])
+        acc = oracle.lagrangian_accel(oracle.spline_coeffs(f), pos)
+        ex = np.sin(pos[2]) * np.cos(pos[1])
+        errs.append(max(np.abs(acc[0] - ex).max(), np.abs(acc[1:]).max()))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 6 < r1 < 11 and 6.5 < r2 < 10, errs
