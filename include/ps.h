@@ -239,6 +239,34 @@ ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype coef_t,
                              size_t ws_bytes, int32_t* status, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Second derivatives of the interpolant (the cubic spline is twice         */
+/* continuously differentiable, Sec. 2.2): the 64-term sum of Eq. (spline)  */
+/* with d2b/dt2 = (1-t, 3t-2, 1-3t, t) along one axis (or db/dt along two), */
+/* times n_a n_b / (L_a L_b).  Direct gathers, any particle order.          */
+/*   hess: [ncomp][6][np] F32 in the order xx, yy, zz, xy, xz, yz.          */
+/*   Non-finite positions give NaN and set the status word.                 */
+/* ------------------------------------------------------------------------ */
+ps_status ps_interp_hessian(const ps_grid* grid, int ncomp, ps_dtype coef_t,
+                            const void* coef, const float* scale, int64_t np,
+                            const double* pos, float* hess, int32_t* status,
+                            void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Lagrangian acceleration of fluid particles (Sec. 2.1: they move with the */
+/* local velocity), a = du/dt + (u . grad) u, three components: the         */
+/* convective term from the field at t (coef_n), du/dt as                   */
+/* (u(coef_np1) - u(coef_n)) / dt_field when coef_np1 is given, else 0.     */
+/*   acc: [3][np] F32; vel (optional): [3][np] F32, u from coef_n.          */
+/*   dt_field > 0 when coef_np1 is given.  Direct gathers.                  */
+/* ------------------------------------------------------------------------ */
+ps_status ps_lagrangian_accel(const ps_grid* grid, ps_dtype coef_t,
+                              const void* coef_n, const float* scale_n,
+                              const void* coef_np1, const float* scale_np1,
+                              double dt_field, int64_t np, const double* pos,
+                              float* acc, float* vel, int32_t* status,
+                              void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* One second-order Runge-Kutta step (Sec. 2.1; Sec. 4.3), Heun's form:     */
 /*   u1 = u(x^n; coef_n);  x* = x^n + dt u1;  u2 = u(x*; coef_np1);         */
 /*   x^{n+1} = x^n + (dt/2)(u1 + u2)                                        */

@@ -289,6 +289,48 @@ def ps_interp_backward(coef: torch.Tensor, n, pos: torch.Tensor, g_vel: torch.Te
                                      _ptr(g_field), None, 0, _ptr(status), _stream(stream)))
 
 
+def ps_interp_hessian(coef: torch.Tensor, n, pos: torch.Tensor, hess: torch.Tensor,
+                      scale: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                      L=DEFAULT_L, stream=None):
+    """Second derivatives of Eq. (spline): hess [ncomp][6][np] (xx, yy, zz, xy, xz, yz)."""
+    _check_coef_shape(coef, n)
+    ncomp = _ncomp_of(coef)
+    np_ = pos.shape[1]
+    _dev(coef, "coef")
+    _dev(pos, "pos", torch.float64)
+    _dev(hess, "hess", torch.float32, ncomp * 6 * np_)
+    _dev(scale, "scale", torch.float32)
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    _check(_lib().ps_interp_hessian(ctypes.byref(g), ncomp, _coef_type(coef), _ptr(coef),
+                                    _ptr(scale), np_, _ptr(pos), _ptr(hess), _ptr(status),
+                                    _stream(stream)))
+
+
+def ps_lagrangian_accel(coef_n: torch.Tensor, n, pos: torch.Tensor, acc: torch.Tensor,
+                        coef_np1: Optional[torch.Tensor] = None, dt_field: float = 1.0,
+                        scale_n: Optional[torch.Tensor] = None,
+                        scale_np1: Optional[torch.Tensor] = None,
+                        vel: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
+                        L=DEFAULT_L, stream=None):
+    """a = du/dt + (u . grad) u at pos [3][np] -> acc [3][np] (du/dt from two fields)."""
+    _check_coef_shape(coef_n, n)
+    np_ = pos.shape[1]
+    _dev(coef_n, "coef_n")
+    _dev(coef_np1, "coef_np1", coef_n.dtype)
+    if coef_np1 is not None and _coef_type(coef_np1) != _coef_type(coef_n):
+        raise ValueError("coef_np1 must have the storage of coef_n")
+    _dev(pos, "pos", torch.float64)
+    _dev(acc, "acc", torch.float32, 3 * np_)
+    _dev(vel, "vel", torch.float32, 3 * np_)
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    _check(_lib().ps_lagrangian_accel(ctypes.byref(g), _coef_type(coef_n), _ptr(coef_n),
+                                      _ptr(scale_n), _ptr(coef_np1), _ptr(scale_np1),
+                                      float(dt_field), np_, _ptr(pos), _ptr(acc), _ptr(vel),
+                                      _ptr(status), _stream(stream)))
+
+
 def ps_rk2_workspace_size(n, brick, np_: int, L=DEFAULT_L) -> int:
     g = make_grid(n, L)
     return int(_lib().ps_rk2_workspace_size(ctypes.byref(g), _brick_arr(brick), int(np_)))
@@ -367,6 +409,27 @@ class SplineField:
             ws = workspace(need, field.device)
         ps_spline_coeffs(field, out.coef, out.scale, ws if need else None, L=L, stream=stream)
         return out
+
+    def hessian(self, pos: torch.Tensor, status: Optional[torch.Tensor] = None,
+                stream=None) -> torch.Tensor:
+        """Second derivatives at pos: [ncomp][6][np] (xx, yy, zz, xy, xz, yz)."""
+        h = torch.empty((self.ncomp, 6, pos.shape[1]), dtype=torch.float32, device=pos.device)
+        ps_interp_hessian(self.coef, self.n, pos, h, scale=self.scale, status=status, L=self.L,
+                          stream=stream)
+        return h
+
+    def acceleration(self, pos: torch.Tensor, later: Optional["SplineField"] = None,
+                     dt_field: float = 1.0, status: Optional[torch.Tensor] = None,
+                     stream=None) -> torch.Tensor:
+        """Lagrangian acceleration du/dt + (u . grad) u at pos ([3][np]); du/dt from
+        `later` (the field dt_field later) when given."""
+        a = torch.empty((3, pos.shape[1]), dtype=torch.float32, device=pos.device)
+        ps_lagrangian_accel(self.coef, self.n, pos, a,
+                            coef_np1=later.coef if later is not None else None,
+                            dt_field=dt_field, scale_n=self.scale,
+                            scale_np1=later.scale if later is not None else None,
+                            status=status, L=self.L, stream=stream)
+        return a
 
     def interp(self, pos: torch.Tensor, grad: bool = False, bins: Optional["Bins"] = None,
                status: Optional[torch.Tensor] = None, stream=None):

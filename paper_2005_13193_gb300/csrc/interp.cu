@@ -276,6 +276,122 @@ __global__ void __launch_bounds__(256) scatter_field(GridArgs g, int64_t np,
   }
 }
 
+// Second derivatives of Eq. (spline) by a quad of lanes per particle (lane q
+// owns stencil column a_x + q): six sums per component over the 16 (j, k)
+// rows with the y and z factors of each derivative, the x factor applied per
+// lane before the quad reduction.  hess [ncomp][6][np]: xx, yy, zz, xy, xz, yz.
+template <typename Tc, int NC>
+__global__ void __launch_bounds__(256) interp_hessian_direct(GridArgs g,
+                                                             const Tc* __restrict__ coef,
+                                                             const float* __restrict__ scale,
+                                                             int64_t np,
+                                                             const double* __restrict__ pos,
+                                                             float* __restrict__ hess,
+                                                             int32_t* status) {
+  using A = typename AccOf<Tc>::type;
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const bool valid = p0 < np;
+  const int64_t p = valid ? p0 : 0;
+  int cell[3];
+  A t[3];
+  double xd;
+  const bool ok = locate_group<4, A>(g, pos, valid ? np : 0, p, lane, cell, t, xd) || !valid;
+  A b[3][4], db[3][4], d2[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    bspline<A>(t[d], b[d]);
+    dbspline<A>(t[d], db[d]);
+    ddbspline<A>(t[d], d2[d]);
+  }
+  A s0[NC], sy[NC], sz[NC], syy[NC], szz[NC], syz[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) s0[c] = sy[c] = sz[c] = syy[c] = szz[c] = syz[c] = A(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const A v = load_coef<Tc>(coef, scale, g, c, cell[2] + k, cell[1] + j, cell[0] + q);
+        s0[c] += b[1][j] * b[2][k] * v;
+        sy[c] += db[1][j] * b[2][k] * v;
+        sz[c] += b[1][j] * db[2][k] * v;
+        syy[c] += d2[1][j] * b[2][k] * v;
+        szz[c] += b[1][j] * d2[2][k] * v;
+        syz[c] += db[1][j] * db[2][k] * v;
+      }
+    }
+  const A bq = pick4(b[0], q), dbq = pick4(db[0], q), d2q = pick4(d2[0], q);
+  const A hx = (A)g.inv_h[0], hy = (A)g.inv_h[1], hz = (A)g.inv_h[2];
+  A h[NC][6];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    h[c][0] = group_sum<4>(d2q * s0[c]) * (hx * hx);
+    h[c][1] = group_sum<4>(bq * syy[c]) * (hy * hy);
+    h[c][2] = group_sum<4>(bq * szz[c]) * (hz * hz);
+    h[c][3] = group_sum<4>(dbq * sy[c]) * (hx * hy);
+    h[c][4] = group_sum<4>(dbq * sz[c]) * (hx * hz);
+    h[c][5] = group_sum<4>(bq * syz[c]) * (hy * hz);
+  }
+  if (!valid || q != 0) return;
+  if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+  const float nanf_ = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) hess[((int64_t)c * 6 + e) * np + p] = ok ? (float)h[c][e] : nanf_;
+}
+
+// Lagrangian acceleration a = du/dt + (u . grad) u by a quad per particle:
+// u and its gradient from c0, u from c1 (if given) for the time difference.
+template <typename Tc>
+__global__ void __launch_bounds__(256) lagrangian_accel_direct(
+    GridArgs g, const Tc* __restrict__ c0, const float* __restrict__ s0,
+    const Tc* __restrict__ c1, const float* __restrict__ s1, double inv_dt, int64_t np,
+    const double* __restrict__ pos, float* __restrict__ acc, float* __restrict__ vel,
+    int32_t* status) {
+  using A = typename AccOf<Tc>::type;
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const bool valid = p0 < np;
+  const int64_t p = valid ? p0 : 0;
+  int cell[3];
+  A t[3];
+  double xd;
+  const bool ok = locate_group<4, A>(g, pos, valid ? np : 0, p, lane, cell, t, xd) || !valid;
+  Basis<A, true> B;
+  B.set(cell, t);
+  A a0[3], ay[3], az[3];
+  quad_rows<Tc, 3, true, A>(g, c0, s0, B, q, a0, ay, az);
+  const A bq = pick4(B.b[0], q), dbq = pick4(B.db[0], q);
+  A u[3], gx[3], gy[3], gz[3], u1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u[c] = group_sum<4>(bq * a0[c]);
+    gx[c] = group_sum<4>(dbq * a0[c]) * (A)g.inv_h[0];
+    gy[c] = group_sum<4>(bq * ay[c]) * (A)g.inv_h[1];
+    gz[c] = group_sum<4>(bq * az[c]) * (A)g.inv_h[2];
+    u1[c] = u[c];
+  }
+  if (c1) {
+    Basis<A, false> B1;
+    B1.set(cell, t);
+    quad_rows<Tc, 3, false, A>(g, c1, s1, B1, q, a0, ay, az);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u1[c] = group_sum<4>(bq * a0[c]);
+  }
+  if (!valid || q != 0) return;
+  if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+  const float nanf_ = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const A a = gx[c] * u[0] + gy[c] * u[1] + gz[c] * u[2] + (u1[c] - u[c]) * (A)inv_dt;
+    acc[(int64_t)c * np + p] = ok ? (float)a : nanf_;
+    if (vel) vel[(int64_t)c * np + p] = ok ? (float)u[c] : nanf_;
+  }
+}
+
 // Fused Heun step with direct gathers (any particle order).
 template <typename Tc>
 __global__ void __launch_bounds__(256) rk2_direct(GridArgs g, const Tc* __restrict__ c0,
@@ -2310,4 +2426,59 @@ extern "C" ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype
     if (rc) return rc;
   }
   return PS_OK;
+}
+
+extern "C" ps_status ps_interp_hessian(const ps_grid* grid, int ncomp, ps_dtype coef_t,
+                                       const void* coef, const float* scale, int64_t np,
+                                       const double* pos, float* hess, int32_t* status,
+                                       void* stream) {
+  ps_status rc = validate_grid(grid);
+  if (rc) return rc;
+  if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
+  if ((coef_t == PS_F32X4 || coef_t == PS_BF16X4 || coef_t == PS_F16X4) && ncomp != 3)
+    return fail(PS_ERR_INVALID_ARG, "node coefficients need ncomp == 3");
+  if ((rc = check_coef(coef_t, coef, scale))) return rc;
+  if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
+  if (np == 0) return PS_OK;
+  if (!pos || !hess) return fail(PS_ERR_INVALID_ARG, "pos and hess are required");
+  cudaStream_t st = as_stream(stream);
+  GridArgs g = make_grid_args(grid, coef_t);
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    const Tc* c = static_cast<const Tc*>(coef);
+    if (ncomp == 3)
+      interp_hessian_direct<Tc, 3><<<quad_blocks(np), 256, 0, st>>>(g, c, scale, np, pos, hess,
+                                                                     status);
+    else
+      interp_hessian_direct<Tc, 1><<<quad_blocks(np), 256, 0, st>>>(g, c, scale, np, pos, hess,
+                                                                     status);
+    return check_launch("interp_hessian_direct");
+  });
+}
+
+extern "C" ps_status ps_lagrangian_accel(const ps_grid* grid, ps_dtype coef_t,
+                                         const void* coef_n, const float* scale_n,
+                                         const void* coef_np1, const float* scale_np1,
+                                         double dt_field, int64_t np, const double* pos,
+                                         float* acc, float* vel, int32_t* status,
+                                         void* stream) {
+  ps_status rc = validate_grid(grid);
+  if (rc) return rc;
+  if ((rc = check_coef(coef_t, coef_n, scale_n))) return rc;
+  if (coef_np1 && (rc = check_coef(coef_t, coef_np1, scale_np1))) return rc;
+  if (coef_np1 && !(dt_field > 0.0 && std::isfinite(dt_field)))
+    return fail(PS_ERR_INVALID_ARG, "dt_field must be finite and > 0");
+  if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
+  if (np == 0) return PS_OK;
+  if (!pos || !acc) return fail(PS_ERR_INVALID_ARG, "pos and acc are required");
+  cudaStream_t st = as_stream(stream);
+  GridArgs g = make_grid_args(grid, coef_t);
+  const double inv_dt = coef_np1 ? 1.0 / dt_field : 0.0;
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    lagrangian_accel_direct<Tc><<<quad_blocks(np), 256, 0, st>>>(
+        g, static_cast<const Tc*>(coef_n), scale_n, static_cast<const Tc*>(coef_np1), scale_np1,
+        inv_dt, np, pos, acc, vel, status);
+    return check_launch("lagrangian_accel_direct");
+  });
 }

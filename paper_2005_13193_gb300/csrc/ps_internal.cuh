@@ -219,6 +219,16 @@ __device__ __forceinline__ void dbspline(T t, T d[4]) {
   d[3] = t * t * half;
 }
 
+// d2 b / dt2: piecewise linear (the spline is twice continuously
+// differentiable, Sec. 2.2).
+template <typename T>
+__device__ __forceinline__ void ddbspline(T t, T d[4]) {
+  d[0] = T(1) - t;
+  d[1] = T(3) * t - T(2);
+  d[2] = T(1) - T(3) * t;
+  d[3] = t;
+}
+
 // Coefficient element -> arithmetic type.
 template <typename Tc> struct CoefLoad;
 template <> struct CoefLoad<float> {

@@ -554,3 +554,67 @@ def test_node16_storage_matches_planar(planar, node, n):
         ps.ps_tune_set("node_tma", old)
     ulp = 2.0 ** -8 if planar == torch.bfloat16 else 2.0 ** -10
     assert abs_err(vb.cpu().numpy(), oracle.interp(cref, pos)) <= ulp * np.abs(cref).max()
+
+
+# ---------------------------------------------------- second derivatives ----
+
+@pytest.mark.parametrize("n,L", [((32, 32, 32), (TWO_PI,) * 3), ((37, 21, 10), (TWO_PI, 4.0, 2.5))])
+def test_hessian_matches_oracle(n, L):
+    # bar: 1e-5 relative rounding on weights summing (in absolute value) to at
+    # most 4 per second-derivative axis and 1 per first-derivative axis
+    field, pos, cref = _case(n, 5000, seed=171, L=L, spread=1.3)
+    ref = oracle.interp_hessian(cref, pos, L=L)
+    ih = np.array(n) / np.array(L)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    scale = np.array([ih[a] * ih[b] for a, b in pairs])[None, :, None]
+    cmax = np.abs(cref).max()
+    f = torch.from_numpy(field).to(DEV)
+    pg = torch.from_numpy(pos).to(DEV)
+    out = {}
+    for dt, bar in ((torch.float32, 4e-5), (torch.float64, 1e-9), (ps.F32X4, 4e-5),
+                    (torch.bfloat16, 4 * 2.0 ** -8), (ps.BF16X4, 4 * 2.0 ** -8)):
+        sf = ps.SplineField.from_field(f, dt, L=L)
+        st = torch.zeros(4, dtype=torch.int32, device=DEV)
+        h = sf.hessian(pg, status=st).cpu().numpy()
+        assert ps.ps_status_read(st)[0] == 0
+        # plus the rounding of the FP32 output itself
+        assert np.all(np.abs(h - ref) <= bar * scale * cmax + 2.0 ** -23 * np.abs(ref)), dt
+        out[dt] = h
+    np.testing.assert_array_equal(out[ps.F32X4], out[torch.float32])
+    np.testing.assert_array_equal(out[ps.BF16X4], out[torch.bfloat16])
+
+
+def test_hessian_nonfinite_flagged():
+    n = (16, 16, 16)
+    field, pos, _ = _case(n, 64, seed=173)
+    pos[1, 5] = np.nan
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    st = torch.zeros(4, dtype=torch.int32, device=DEV)
+    h = sf.hessian(torch.from_numpy(pos).to(DEV), status=st).cpu().numpy()
+    assert np.isnan(h[:, :, 5]).all() and np.isfinite(np.delete(h, 5, axis=2)).all()
+    assert ps.ps_status_read(st)[0] == 1
+
+
+@pytest.mark.parametrize("two_fields", [False, True])
+def test_lagrangian_accel_matches_oracle(two_fields):
+    n = (24, 20, 28)
+    field, pos, cref = _case(n, 6000, seed=175, spread=1.2)
+    f2 = synth.random_field(n, ncomp=3, seed=176).astype(np.float32)
+    cref2 = oracle.spline_coeffs(f2.astype(np.float64))
+    dt = 0.05
+    ref = oracle.lagrangian_accel(cref, pos, cref2 if two_fields else None, dt)
+    u, G = oracle.interp(cref, pos, grad=True)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    sf2 = ps.SplineField.from_field(torch.from_numpy(f2).to(DEV), torch.float32)
+    a = sf.acceleration(torch.from_numpy(pos).to(DEV), later=sf2 if two_fields else None,
+                        dt_field=dt).cpu().numpy()
+    # sum over three axes of (gradient bar 1e-5 * 3 * n/L * max|c|) * |u|
+    # + |grad u| * (velocity bar 1e-5 rms), plus both fields' velocity bars
+    # over dt
+    ih = max(n) / TWO_PI
+    cmax = max(np.abs(cref).max(), np.abs(cref2).max())
+    rms = np.sqrt((u ** 2).mean())
+    tol = 3 * (1e-5 * 3 * ih * cmax * np.abs(u).max() + np.abs(G).max() * 1e-5 * rms)
+    if two_fields:
+        tol += 2 * 1e-5 * 3 * rms / dt
+    assert np.abs(a - ref).max() <= tol
