@@ -22,6 +22,8 @@
 // (one warp per row, staged through shared memory), which writes the padded
 // N+3 layout with periodic ghosts and, for BF16/FP16, a power-of-two scale per
 // x-line.
+#include <mutex>
+
 #include "ps_internal.cuh"
 
 namespace ps {
@@ -50,6 +52,72 @@ template <typename To> __device__ __forceinline__ To cvt_out_d(double v) { retur
 // pencil.  grid = (ceil(nx/XW), n_other, ncomp).  src and dst may alias
 // exactly (in place): each thread reads all its elements before any write and
 // owns them.
+// z^k for k = 0..64 (the recursions' pole), in both precisions; filled once
+// per device from the host's FP64 value of z.
+__constant__ float c_zpow_f[65];
+__constant__ double c_zpow_d[65];
+template <typename T> __device__ __forceinline__ T zpow(int k);
+template <> __device__ __forceinline__ float zpow<float>(int k) { return c_zpow_f[k]; }
+template <> __device__ __forceinline__ double zpow<double>(int k) { return c_zpow_d[k]; }
+
+// One chunk of a pencil held in registers, len <= LMAX values: the causal
+// recursion from a zero state (returns its end state), the causal fix-up
+// v_i += c z^(i+1), the anti-causal recursion (returns its start state) and
+// its fix-up v_i += c z^(len-i).  Full chunks (len == LMAX) run without
+// predicates and take the powers of z from the constant table.
+template <typename T, int LMAX>
+__device__ __forceinline__ T chunk_causal(T v[LMAX], int len, T z) {
+  T y = T(0);
+  if (len == LMAX) {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) v[i] = y = v[i] + z * y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) v[i] = y = v[i] + z * y;
+  }
+  return y;
+}
+template <typename T, int LMAX>
+__device__ __forceinline__ void chunk_causal_fix(T v[LMAX], int len, T c) {
+#pragma unroll
+  for (int i = 0; i < LMAX; ++i)
+    if (len == LMAX || i < len) v[i] += c * zpow<T>(i + 1);
+}
+template <typename T, int LMAX>
+__device__ __forceinline__ T chunk_anticausal(T v[LMAX], int len, T z) {
+  T w = T(0);
+  if (len == LMAX) {
+#pragma unroll
+    for (int i = LMAX - 1; i >= 0; --i) v[i] = w = v[i] + z * w;
+  } else {
+#pragma unroll
+    for (int i = LMAX - 1; i >= 0; --i)
+      if (i < len) v[i] = w = v[i] + z * w;
+  }
+  return w;
+}
+template <typename T, int LMAX>
+__device__ __forceinline__ void chunk_anticausal_fix(T v[LMAX], int len, T c, T z) {
+  if (len == LMAX) {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) v[i] += c * zpow<T>(LMAX - i);
+  } else {
+    T pw = z * c;
+#pragma unroll
+    for (int i = LMAX - 1; i >= 0; --i)
+      if (i < len) {
+        v[i] += pw;
+        pw *= z;
+      }
+  }
+}
+// z^len of a chunk.
+template <typename T>
+__device__ __forceinline__ T chunk_zlen(int len) {
+  return len <= 64 ? zpow<T>(len) : T(0);
+}
+
 template <typename Tin, typename T, int LMAX>
 __global__ void __launch_bounds__(1024) solve_strided(
     const Tin* src, int64_t s_off, int64_t s_sc, int64_t s_so, int64_t s_si,
@@ -67,26 +135,19 @@ __global__ void __launch_bounds__(1024) solve_strided(
   int len = n - s0;
   len = len < 0 ? 0 : (len > L ? L : len);
   if (x >= nx) len = 0;
-  const int64_t sbase = s_off + c * s_sc + o * s_so + x;
-  const int64_t dbase = d_off + c * d_sc + o * d_so + x;
+  const Tin* sp = src + s_off + c * s_sc + o * s_so + x + (int64_t)s0 * s_si;
+  T* dp = dst + d_off + c * d_sc + o * d_so + x + (int64_t)s0 * d_si;
   const T thr = Thr<T>::v;
 
   T v[LMAX];
 #pragma unroll
   for (int i = 0; i < LMAX; ++i)
-    if (i < len) v[i] = (T)src[sbase + (int64_t)(s0 + i) * s_si];
+    if (i < len) v[i] = (T)sp[(int64_t)i * s_si];
 
-  // causal sweep from a zero state
-  T y = T(0), a = T(1);
-#pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) {
-      y = v[i] + z * y;
-      v[i] = y;
-      a *= z;
-    }
+  // causal sweep from a zero state; chunk carries by a geometric sum
+  const T y = chunk_causal<T, LMAX>(v, len, z);
   const int me = m * XW + tx;
-  sa[me] = a;
+  sa[me] = chunk_zlen<T>(len);
   se[me] = y;
   __syncthreads();
   T carry = T(0), fac = T(1);
@@ -100,24 +161,11 @@ __global__ void __launch_bounds__(1024) solve_strided(
     if (fabs(fac) < thr) break;
   }
   if (j > M) carry = carry / (T(1) - fac);
-  T pw = z * carry;
-#pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) {
-      v[i] += pw;
-      pw *= z;
-    }
+  chunk_causal_fix<T, LMAX>(v, len, carry);
   __syncthreads();
 
   // anti-causal sweep from a zero state
-  T w = T(0);
-#pragma unroll
-  for (int i = LMAX - 1; i >= 0; --i)
-    if (i < len) {
-      w = v[i] + z * w;
-      v[i] = w;
-    }
-  se[me] = w;
+  se[me] = chunk_anticausal<T, LMAX>(v, len, z);
   __syncthreads();
   carry = T(0);
   fac = T(1);
@@ -130,16 +178,10 @@ __global__ void __launch_bounds__(1024) solve_strided(
     if (fabs(fac) < thr) break;
   }
   if (j > M) carry = carry / (T(1) - fac);
-  pw = z * carry;
-#pragma unroll
-  for (int i = LMAX - 1; i >= 0; --i)
-    if (i < len) {
-      v[i] += pw;
-      pw *= z;
-    }
+  chunk_anticausal_fix<T, LMAX>(v, len, carry, z);
 #pragma unroll
   for (int i = 0; i < LMAX; ++i)
-    if (i < len) dst[dbase + (int64_t)(s0 + i) * d_si] = gain * v[i];
+    if (i < len) dp[(int64_t)i * d_si] = gain * v[i];
 }
 
 __device__ __forceinline__ float pow2_at_least(float mx) {
@@ -178,14 +220,8 @@ __device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z
   for (int i = 0; i < LMAX; ++i)
     if (i < len) v[i] = mine[i];
 
-  T y = T(0), a = T(1);
-#pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) {
-      y = v[i] + z * y;
-      v[i] = y;
-      a *= z;
-    }
+  const T y = chunk_causal<T, LMAX>(v, len, z);
+  const T a = chunk_zlen<T>(len);
   T carry = T(0), fac = T(1);
   bool wrapped = true;
   for (int j = 1; j <= 32; ++j) {
@@ -200,21 +236,9 @@ __device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z
     }
   }
   if (wrapped) carry = carry / (T(1) - fac);
-  T pw = z * carry;
-#pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) {
-      v[i] += pw;
-      pw *= z;
-    }
+  chunk_causal_fix<T, LMAX>(v, len, carry);
 
-  T w = T(0);
-#pragma unroll
-  for (int i = LMAX - 1; i >= 0; --i)
-    if (i < len) {
-      w = v[i] + z * w;
-      v[i] = w;
-    }
+  const T w = chunk_anticausal<T, LMAX>(v, len, z);
   carry = T(0);
   fac = T(1);
   wrapped = true;
@@ -230,13 +254,7 @@ __device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z
     }
   }
   if (wrapped) carry = carry / (T(1) - fac);
-  pw = z * carry;
-#pragma unroll
-  for (int i = LMAX - 1; i >= 0; --i)
-    if (i < len) {
-      v[i] += pw;
-      pw *= z;
-    }
+  chunk_anticausal_fix<T, LMAX>(v, len, carry, z);
 
   float sc = 1.f;
   if (QUANT) {
@@ -511,6 +529,27 @@ ps_status launch_x_node4(const float* src, View sv, NodeT* dst, float* scale4, i
   return launch_x_node4_l<64>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
 }
 
+// Fill the constant tables of z^k once per device (the host's FP64 z).
+ps_status upload_zpow(double zd) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  ps_status rc = check_cuda(cudaGetDevice(&dev), "get device");
+  if (rc) return rc;
+  if (dev < 0 || dev >= 64) return fail(PS_ERR_UNSUPPORTED, "device index %d", dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return PS_OK;
+  double pd[65];
+  float pf[65];
+  pd[0] = 1.0;
+  for (int k = 1; k <= 64; ++k) pd[k] = pd[k - 1] * zd;
+  for (int k = 0; k <= 64; ++k) pf[k] = (float)pd[k];
+  if ((rc = check_cuda(cudaMemcpyToSymbol(c_zpow_d, pd, sizeof(pd)), "z powers (FP64)"))) return rc;
+  if ((rc = check_cuda(cudaMemcpyToSymbol(c_zpow_f, pf, sizeof(pf)), "z powers (FP32)"))) return rc;
+  done[dev] = true;
+  return PS_OK;
+}
+
 View unpadded_view(const ps_grid* g) {
   const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
   return View{0, nx * ny * nz, nx * ny, nx};
@@ -532,6 +571,7 @@ ps_status run_solve(const ps_grid* g, int ncomp, const Tin* field, View fv, T* i
                     View iv, Tout* out, View ov, float* scale, int padded,
                     cudaStream_t st) {
   const double zd = sqrt(3.0) - 2.0;
+  if (ps_status zrc = upload_zpow(zd)) return zrc;
   const T z = (T)zd, gain = (T)(-6.0 * zd);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   ps_status rc = launch_strided<Tin, T>(field, fv, fv.sz, fv.sy, inter, iv, iv.sz, iv.sy,
@@ -549,6 +589,7 @@ template <typename Tin, typename NodeT>
 ps_status run_solve_node4(const ps_grid* g, const Tin* field, View fv, float* inter,
                           NodeT* out, float* scale4, int64_t rx, cudaStream_t st) {
   const double zd = sqrt(3.0) - 2.0;
+  if (ps_status zrc = upload_zpow(zd)) return zrc;
   const float z = (float)zd, gain = (float)(-6.0 * zd);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   ps_status rc = launch_strided<Tin, float>(field, fv, fv.sz, fv.sy, inter, fv, fv.sz, fv.sy,
