@@ -116,12 +116,16 @@ int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
  * 1 = persistent CTAs that prefetch the next brick's halo while processing the
  * current one, 2 = one CTA per brick, one thread per particle, 3 = one CTA per
  * brick, every warp walking its own particles with no barrier after the
- * staging; "brick_ctas_per_sm" in [1, 8] (default 3,
+ * staging, 4 = persistent CTAs with two node-halo buffers, the next brick's
+ * tensor copy in flight (node coefficients only; otherwise 0 runs);
+ * "brick_ctas_per_sm" in [1, 8] (default 3,
  * persistent form only); "brick_min_stage" in [0, 2^20] (default 8): in the
  * one-CTA-per-brick kernel, bricks holding fewer particles skip the halo
- * staging and gather their stencils from global memory.  Process-wide; set
- * them before capturing work in a graph.  ps_tune_get returns -1 for an
- * unknown key. */
+ * staging and gather their stencils from global memory; "node_tma" 0 or 1
+ * (default 1): halos of node coefficients by tensor copy; "solve_xw" 0, 8, 16
+ * or 32 (0 = default 16): x extent of a block of the strided spline passes.
+ * Process-wide; set them before capturing work in a graph.  ps_tune_get
+ * returns -1 for an unknown key. */
 ps_status ps_tune_set(const char* key, int64_t value);
 int64_t ps_tune_get(const char* key);
 

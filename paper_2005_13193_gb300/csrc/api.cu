@@ -121,6 +121,12 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
     tuning().brick_min_stage = (int)value;
     return PS_OK;
   }
+  if (!strcmp(key, "solve_xw")) {
+    if (value != 0 && value != 8 && value != 16 && value != 32)
+      return fail(PS_ERR_INVALID_ARG, "solve_xw is 0, 8, 16 or 32");
+    tuning().solve_xw = (int)value;
+    return PS_OK;
+  }
   if (!strcmp(key, "node_tma")) {
     if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "node_tma is 0 or 1");
     tuning().node_tma = (int)value;
@@ -140,6 +146,7 @@ extern "C" int64_t ps_tune_get(const char* key) {
   if (!strcmp(key, "brick_ctas_per_sm")) return tuning().brick_ctas_per_sm;
   if (!strcmp(key, "brick_min_stage")) return tuning().brick_min_stage;
   if (!strcmp(key, "node_tma")) return tuning().node_tma;
+  if (!strcmp(key, "solve_xw")) return tuning().solve_xw;
   return -1;
 }
 

@@ -75,6 +75,7 @@ struct Tuning {
   int brick_ctas_per_sm = 3;  // resident CTAs per SM of the persistent form
   int brick_min_stage = 8;    // per-brick kernel: fewer particles skip the halo
   int node_tma = 1;           // PS_F32X4 halos by tensor copy
+  int solve_xw = 0;           // x extent of a strided-pass block (0: default)
 };
 Tuning& tuning();
 int sm_count();
