@@ -316,12 +316,16 @@ def run_ours(args):
 
 
 def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
-    """Config-2 comparison: one interpolation of all particles, unsorted (random
-    storage order, direct gathers) vs sorted (bin order, staged halos)."""
+    """One interpolation of all particles, unsorted (random storage order, direct
+    gathers) vs sorted (bin order, staged halos); then, on the sorted order, the
+    velocity gradient, the second derivatives and the Lagrangian acceleration."""
     g = torch.Generator(device="cpu").manual_seed(5)
     perm = torch.randperm(NP, generator=g).to(dev)
     pos_rand = pos_sorted_by_bin[:, perm].contiguous()
     vel = torch.empty((3, NP), dtype=torch.float32, device=dev)
+    grad = torch.empty((3, 3, NP), dtype=torch.float32, device=dev)
+    hess = torch.empty((3, 6, NP), dtype=torch.float32, device=dev)
+    acc = torch.empty((3, NP), dtype=torch.float32, device=dev)
     # physically sorted copy
     bins2, pos_sorted = ps.bin_particles(n3, BRICK, pos_sorted_by_bin, want_sorted=True)
     out = {}
@@ -329,7 +333,16 @@ def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
             ("unsorted_direct", lambda: ps.ps_interp(coef, n3, pos_rand, vel)),
             ("sorted_direct", lambda: ps.ps_interp(coef, n3, pos_sorted, vel)),
             ("sorted_staged", lambda: ps.ps_interp(coef, n3, pos_sorted, vel,
-                                                   bin_offsets=bins2.offsets, brick=BRICK))):
+                                                   bin_offsets=bins2.offsets, brick=BRICK)),
+            ("sorted_staged_grad", lambda: ps.ps_interp(coef, n3, pos_sorted, vel, grad=grad,
+                                                        bin_offsets=bins2.offsets,
+                                                        brick=BRICK)),
+            # second derivatives: direct quad-per-particle gathers
+            ("sorted_hessian_direct", lambda: ps.ps_interp_hessian(coef, n3, pos_sorted, hess)),
+            # du/dt + (u . grad) u with a second field: 2 + 9 sums per particle
+            ("sorted_accel_direct", lambda: ps.ps_lagrangian_accel(coef, n3, pos_sorted, acc,
+                                                                   coef_np1=coef,
+                                                                   dt_field=1.0))):
         for _ in range(3):
             fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -340,6 +353,7 @@ def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
         torch.cuda.synchronize()
         t = a.elapsed_time(b) / 5
         out[name] = {"ms": t, "particles_per_s": NP / (t * 1e-3)}
+    del grad, hess, acc
     return out
 
 
