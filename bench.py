@@ -40,8 +40,9 @@ POS_SEED = 2001
 WORKLOAD = ("mid: 512^3 FP32 u,v,w (k^-5/3, 1<=|k|<=170, unit rms), 16,777,216 uniform FP64 "
             "particles; spline solve + 10 Heun RK2 steps (dt 1e-3) with re-binning into 8^3 "
             "bricks every step")
-# kernels of libps launched per bench step: 3 solve passes + 10 x (5 bin + 1 RK2)
-LAUNCHES_PER_STEP = 3 + RK_STEPS * 6
+# kernels of libps launched per bench step: 3 solve passes + 10 x (3 scan passes, 1 scatter
+# and the RK2 step, which also counts the next sort's bins)
+LAUNCHES_PER_STEP = 3 + RK_STEPS * 5
 DOMINANT = "interp_staged<float4,3,RK2> (fused binned Heun step, halo by tensor copy)"
 SOURCE_FOR_TRAFFIC = os.path.join(ROOT, "paper_2005_13193_gb300", "csrc", "interp.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -67,7 +68,7 @@ def parse():
         NP = args.particles or NP
         RK_STEPS = args.rk_steps or RK_STEPS
         KMAX = N // 3
-        LAUNCHES_PER_STEP = 3 + RK_STEPS * 6
+        LAUNCHES_PER_STEP = 3 + RK_STEPS * 5
         WORKLOAD = (f"reduced case: {N}^3 FP32 u,v,w (k^-5/3, 1<=|k|<={KMAX}), {NP} particles, "
                     f"solve + {RK_STEPS} RK2 steps, 8^3 bricks")
     return args
@@ -205,12 +206,13 @@ def run_ours(args):
     nb = [-(-N // b) for b in BRICK]
     nbins = nb[0] * nb[1] * nb[2]
     offsets = torch.empty(nbins + 1, dtype=torch.int32, device=dev)
-    bin_of = torch.empty(NP, dtype=torch.int32, device=dev)
-    ws_bin = ps.workspace(ps.ps_bin_workspace_size(n3, BRICK, NP), dev)
+    ws_rk = ps.workspace(ps.ps_rk2_workspace_size(n3, BRICK, NP), dev)
     status = torch.zeros(4, dtype=torch.int32, device=dev)
     vel = torch.empty((3, NP), dtype=torch.float32, device=dev)
     bufs = [pos0.clone(), torch.empty_like(pos0)]
     stream = torch.cuda.current_stream(dev)
+
+    counted = [False]  # ws holds the counts of bufs[0]'s positions
 
     def one_step(ev_solve=None, ev_rk=None):
         if ev_solve:
@@ -220,13 +222,17 @@ def run_ours(args):
             ev_solve[1].record(stream)
         for r in range(RK_STEPS):
             src, dst = bufs[0], bufs[1]
-            ps.ps_bin_particles(n3, BRICK, src, bin_of, offsets, None, dst, ws_bin, status)
+            # sort (from the counts the previous step's kernel took), then the
+            # fused Heun step, which counts the bins of the positions it writes
+            ps.ps_rk2_sort(n3, BRICK, src, dst, offsets, ws_rk, counted=counted[0],
+                           status=status)
             if ev_rk:
                 ev_rk[r][0].record(stream)
-            ps.ps_rk2_step(coef, n3, dst, DT, vel_out=vel, brick=BRICK, rebin=False,
-                           bin_offsets=offsets, status=status)
+            ps.ps_rk2_step(coef, n3, dst, DT, vel_out=vel, brick=BRICK, rebin=0,
+                           bin_offsets=offsets, ws=ws_rk, status=status)
             if ev_rk:
                 ev_rk[r][1].record(stream)
+            counted[0] = True
             bufs[0], bufs[1] = dst, src
 
     for _ in range(args.warmup):
@@ -262,7 +268,9 @@ def run_ours(args):
     rk_avg = statistics.mean(rk_ms)
     peak, peak_kind = measured_peaks()
     coef_bytes = 3 * 4 * (N + 3) ** 3
-    rk_alg_bytes = NP * (24 + 24 + 12) + coef_bytes
+    # positions in and out, u1 out, the next sort's bin and rank out; the
+    # coefficients once
+    rk_alg_bytes = NP * (24 + 24 + 12 + 8) + coef_bytes
     solve_min_bytes = 3 * 4 * N ** 3 + coef_bytes
     solve_pass_bytes = 3 * 4 * N ** 3 * 5 + coef_bytes
     achieved = rk_alg_bytes / (rk_avg * 1e-3) / 1e9
@@ -507,9 +515,12 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg)
         st.wait_event(ev_in[b])
         ids[b].copy_(ids0)
         ps.ps_spline_coeffs(field_d[b], coef, ws=ws_solve, stream=st)
-        for _ in range(RK_STEPS):
+        for r in range(RK_STEPS):
+            # the first step sorts the uploaded positions; each step's kernel
+            # counts the bins of the positions it writes for the next sort
             ps.ps_rk2_step(coef, n3, pos_d[b], DT, ids=ids[b], vel_out=vel_d[b], brick=BRICK,
-                           rebin=True, bin_offsets=offsets, ws=ws, status=status, stream=st)
+                           rebin=2 if r == 0 else 3, bin_offsets=offsets, ws=ws,
+                           status=status, stream=st)
         ev_done[b].record(st)
 
     def readback(b):
@@ -546,8 +557,8 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg)
             "steps": steps,
             "h2d_bytes_per_step": field_h.numel() * 4 + pos_h.numel() * 8,
             "d2h_bytes_per_step": pos_out_h.numel() * 8 + vel_h.numel() * 4,
-            "api": "ps_spline_coeffs + ps_rk2_step(rebin=1, ids); inputs double-buffered on a "
-                   "copy stream"}
+            "api": "ps_spline_coeffs + ps_rk2_step(rebin=2, then 3, ids); inputs "
+                   "double-buffered on a copy stream"}
 
 
 # ------------------------------------------------------------- the oracle ----

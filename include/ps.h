@@ -95,6 +95,8 @@ typedef enum {
 #define PS_DEV_OK 0
 #define PS_DEV_NONFINITE_POS 1 /* position NaN/Inf or |x * n/L| >= 2^50 */
 #define PS_DEV_TIMEOUT 2
+#define PS_DEV_BAD_BINS 3 /* ps_rk2_step(rebin = 3) without the counts of a  */
+                          /* preceding rebin = 2 or 3 step on the same ws   */
 
 typedef struct {
   int32_t n[3]; /* nodes per axis: x, y, z */
@@ -283,7 +285,23 @@ ps_status ps_lagrangian_accel(const ps_grid* grid, ps_dtype coef_t,
 /*                   (optional, [nbins+1]) receives the new bin bounds;     */
 /*                   stage 1 reads the staged brick halo in shared memory.  */
 /*   brick, rebin=0  particles are taken to be in bin order already with    */
-/*                   the given bin_offsets (required).                      */
+/*                   the given bin_offsets (required).  ws is optional:     */
+/*                   when given, the step also counts the bins of the       */
+/*                   positions it writes into ws, for a following           */
+/*                   ps_rk2_sort(counted = 1) or ps_rk2_step(rebin = 3).    */
+/*   brick, rebin=2  as rebin=1, and while it stores x^{n+1} the step       */
+/*                   counts each particle's new bin into ws (bin, rank and  */
+/*                   bin counters), the way the paper identifies departing  */
+/*                   particles during the position update (Sec. 4.3).       */
+/*   brick, rebin=3  as rebin=2, but the sort by x^n starts from the counts */
+/*                   the previous rebin=2 or 3 call left in ws: that call   */
+/*                   must have used the same grid, brick, np and ws, and    */
+/*                   pos (and ids) must be as it left them.  The sort then  */
+/*                   reads the positions once, not twice.  Counts that are  */
+/*                   not those of pos are caught by range checks (each      */
+/*                   write stays inside the arrays) and set PS_DEV_BAD_BINS */
+/*                   in the status word.  Results equal rebin=1's, up to    */
+/*                   the order of particles inside a bin.                   */
 /*   vel_out: optional [3][np], receives u1 in the final particle order.    */
 /*   ids: optional int64 [np] particle labels, permuted with the particles. */
 /* ------------------------------------------------------------------------ */
@@ -295,6 +313,25 @@ ps_status ps_rk2_step(const ps_grid* grid, ps_dtype coef_t, const void* coef_n,
                       int64_t* ids, float* vel_out, double dt,
                       const int32_t brick[3], int rebin, int32_t* bin_offsets,
                       void* ws, size_t ws_bytes, int32_t* status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* The sort of a binned Heun step on its own (ps_rk2_step with rebin = 1    */
+/* or 3 is this sort followed by the rebin = 0 step): particles pos [3][np] */
+/* (and ids, optional int64 [np]) are copied in bin order to pos_sorted     */
+/* (and ids_sorted; neither may alias its input) and bin_offsets           */
+/* [nbins+1] receives the bin bounds.                                       */
+/*   counted = 0: bins are counted from pos (as ps_bin_particles does);     */
+/*   counted = 1: from the counts that the last ps_rk2_step on this ws      */
+/*                (rebin = 0 with ws, 2 or 3) took of the positions it      */
+/*                wrote, which pos must still hold; counts that are not     */
+/*                pos's are caught by range checks and set PS_DEV_BAD_BINS. */
+/* ws: ps_rk2_workspace_size(grid, brick, np) bytes, 256-byte aligned.      */
+/* ------------------------------------------------------------------------ */
+ps_status ps_rk2_sort(const ps_grid* grid, const int32_t brick[3], int64_t np,
+                      const double* pos, const int64_t* ids, int counted,
+                      double* pos_sorted, int64_t* ids_sorted,
+                      int32_t* bin_offsets, void* ws, size_t ws_bytes,
+                      int32_t* status, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Many fields at once (no counterpart in the paper: a way of running many  */

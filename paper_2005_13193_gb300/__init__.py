@@ -339,11 +339,17 @@ def ps_rk2_workspace_size(n, brick, np_: int, L=DEFAULT_L) -> int:
 def ps_rk2_step(coef_n: torch.Tensor, n, pos: torch.Tensor, dt: float,
                 coef_np1: Optional[torch.Tensor] = None, scale_n: Optional[torch.Tensor] = None,
                 scale_np1: Optional[torch.Tensor] = None, ids: Optional[torch.Tensor] = None,
-                vel_out: Optional[torch.Tensor] = None, brick=None, rebin: bool = True,
+                vel_out: Optional[torch.Tensor] = None, brick=None, rebin: int = 1,
                 bin_offsets: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
                 status: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
-    """One Heun RK2 step (Sec. 2.1 / 4.3) of positions pos [3][np] in place."""
+    """One Heun RK2 step (Sec. 2.1 / 4.3) of positions pos [3][np] in place.
+    rebin: 0/False (bins given), 1/True (sort first), 2 (sort, and count the new
+    positions' bins into ws), 3 (sort from the counts a previous 2 or 3 step
+    left in ws)."""
     _check_coef_shape(coef_n, n)
+    rebin = int(rebin)
+    if rebin not in (0, 1, 2, 3):
+        raise ValueError("rebin is 0, 1, 2 or 3")
     np_ = pos.shape[1]
     _dev(coef_n, "coef_n")
     _dev(coef_np1, "coef_np1", coef_n.dtype)
@@ -359,9 +365,31 @@ def ps_rk2_step(coef_n: torch.Tensor, n, pos: torch.Tensor, dt: float,
         raise ValueError("coef_np1 must have the storage of coef_n")
     _check(_lib().ps_rk2_step(ctypes.byref(g), _coef_type(coef_n), _ptr(coef_n), _ptr(coef_np1),
                               _ptr(scale_n), _ptr(scale_np1), np_, _ptr(pos), _ptr(ids),
-                              _ptr(vel_out), float(dt), _brick_arr(brick), 1 if rebin else 0,
+                              _ptr(vel_out), float(dt), _brick_arr(brick), rebin,
                               _ptr(bin_offsets), _ptr(ws), ws_bytes, _ptr(status),
                               _stream(stream)))
+
+
+def ps_rk2_sort(n, brick, pos: torch.Tensor, pos_sorted: torch.Tensor,
+                bin_offsets: torch.Tensor, ws: torch.Tensor, ids: Optional[torch.Tensor] = None,
+                ids_sorted: Optional[torch.Tensor] = None, counted: bool = False,
+                status: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
+    """The sort of a binned Heun step: pos [3][np] (and ids) copied in bin order to
+    pos_sorted (and ids_sorted), bounds to bin_offsets.  counted=True starts from
+    the counts the last ps_rk2_step on ws took of the positions it wrote."""
+    np_ = pos.shape[1]
+    _dev(pos, "pos", torch.float64)
+    _dev(pos_sorted, "pos_sorted", torch.float64, 3 * np_)
+    _dev(ids, "ids", torch.int64, np_)
+    _dev(ids_sorted, "ids_sorted", torch.int64, np_)
+    _dev(bin_offsets, "bin_offsets", torch.int32)
+    _dev(ws, "ws")
+    _dev(status, "status", torch.int32, 4)
+    g = make_grid(n, L)
+    _check(_lib().ps_rk2_sort(ctypes.byref(g), _brick_arr(brick), np_, _ptr(pos), _ptr(ids),
+                              1 if counted else 0, _ptr(pos_sorted), _ptr(ids_sorted),
+                              _ptr(bin_offsets), _ptr(ws), ws.numel() * ws.element_size(),
+                              _ptr(status), _stream(stream)))
 
 
 # ------------------------------------------------------------------ helpers ----
@@ -474,12 +502,20 @@ def bin_particles(n, brick, pos: torch.Tensor, L=DEFAULT_L, want_perm=True,
 
 class Tracker:
     """Particles advanced by Heun RK2 through a (frozen or time-dependent)
-    spline field, bin-sorted into bricks every step."""
+    spline field, bin-sorted into bricks every step.  With incremental=True
+    each step's kernel counts the bins of the positions it writes, and the
+    next step's sort starts from those counts (ps_rk2_step rebin 2, then 3).
+    Positions changed between steps keep results exact (a particle outside
+    its brick's halo reads its stencil from global memory); call reset_bins()
+    after such a change to sort them afresh."""
 
     def __init__(self, field: SplineField, pos: torch.Tensor, brick=(8, 8, 8),
-                 ids: Optional[torch.Tensor] = None, keep_velocity: bool = True):
+                 ids: Optional[torch.Tensor] = None, keep_velocity: bool = True,
+                 incremental: bool = True):
         self.field = field
         self.pos = pos
+        self.incremental = incremental
+        self._counted = False  # ws holds the counts of the current positions
         self.brick = brick if brick is None or not isinstance(brick, int) else (brick,) * 3
         np_ = pos.shape[1]
         self.ids = ids if ids is not None else torch.arange(np_, dtype=torch.int64,
@@ -496,14 +532,23 @@ class Tracker:
             self.ws = workspace(ps_rk2_workspace_size(field.n, self.brick, np_, field.L),
                                 pos.device)
 
+    def reset_bins(self) -> None:
+        """Forget the counts left by the last step (the next step sorts from the
+        positions themselves)."""
+        self._counted = False
+
     def step(self, dt: float, field_np1: Optional[SplineField] = None, rebin: bool = True,
              stream=None):
         f1 = field_np1
+        mode = 0
+        if rebin:
+            mode = (3 if self._counted else 2) if self.incremental else 1
         ps_rk2_step(self.field.coef, self.field.n, self.pos, dt,
                     coef_np1=f1.coef if f1 is not None else None, scale_n=self.field.scale,
                     scale_np1=f1.scale if f1 is not None else None, ids=self.ids,
-                    vel_out=self.vel, brick=self.brick, rebin=rebin, bin_offsets=self.offsets,
+                    vel_out=self.vel, brick=self.brick, rebin=mode, bin_offsets=self.offsets,
                     ws=self.ws, status=self.status, L=self.field.L, stream=stream)
+        self._counted = mode >= 2 and self.brick is not None
 
 
 class InterpFn(torch.autograd.Function):

@@ -21,6 +21,7 @@ PS_F32, PS_BF16, PS_F16, PS_F64, PS_F32X4, PS_BF16X4, PS_F16X4 = 0, 1, 2, 3, 4, 
 PS_DEV_OK = 0
 PS_DEV_NONFINITE_POS = 1
 PS_DEV_TIMEOUT = 2
+PS_DEV_BAD_BINS = 3
 
 
 class PsGrid(ctypes.Structure):
@@ -65,6 +66,7 @@ SIGNATURES = {
     "ps_rk2_workspace_size": (_SZ, [_GP, _P, _I64]),
     "ps_rk2_step": (_I, [_GP, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _D, _P, _I, _P, _P, _SZ,
                          _P, _P]),
+    "ps_rk2_sort": (_I, [_GP, _P, _I64, _P, _P, _I, _P, _P, _P, _P, _SZ, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -6,6 +6,9 @@
 //          counter returns the particle's rank inside its bin.
 // scan:    exclusive prefix sum of the counters -> bin_offsets (3 phases).
 // scatter: slot = bin_offsets[bin] + rank; writes perm / sorted copies.
+// The count may instead come from the kernel that wrote the positions (it
+// counts each particle's new bin as it stores it, without ranks); bin_run
+// then starts at the scan, and the scatter takes ranks from the counters.
 #include <mutex>
 
 #include "ps_internal.cuh"
@@ -19,14 +22,10 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 __device__ __forceinline__ int bin_of_position(const GridArgs& g, const BrickArgs& b,
                                                double x, double y, double z, bool& ok) {
-  int cx, cy, cz;
-  float t;
-  ok = locate(x, g.inv_h[0], g.n[0], cx, t);
-  ok &= locate(y, g.inv_h[1], g.n[1], cy, t);
-  ok &= locate(z, g.inv_h[2], g.n[2], cz, t);
-  if (!ok) return 0;
-  const int bx = cx / b.B[0], by = cy / b.B[1], bz = cz / b.B[2];
-  return (bz * b.nb[1] + by) * b.nb[0] + bx;
+  const int key = bin_of_coords(b, brick_coord(g, b, x, 0), brick_coord(g, b, y, 1),
+                                brick_coord(g, b, z, 2));
+  ok = key >= 0;
+  return ok ? key : 0;
 }
 
 // Ranks inside runs of equal keys in consecutive lanes: the run's first lane,
@@ -151,8 +150,12 @@ __global__ void scan_tile_offsets(int32_t* tile_sums, int64_t ntiles) {
 }
 
 // Phase 3: scan inside each tile, add the tile offset; out has n+1 entries.
+// clamp >= 0: offsets are clamped to [0, clamp], so that counts that do not
+// add up (see bin_run's `counted`) still give offsets inside the particle
+// arrays.
 __global__ void scan_tiles(const int32_t* __restrict__ in, int64_t n,
-                           const int32_t* __restrict__ tile_off, int32_t* __restrict__ out) {
+                           const int32_t* __restrict__ tile_off, int32_t* __restrict__ out,
+                           int64_t clamp) {
   const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
   // each thread takes kScanItems consecutive elements
   int32_t v[kScanItems];
@@ -169,10 +172,13 @@ __global__ void scan_tiles(const int32_t* __restrict__ in, int64_t n,
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t idx = tile0 + (int64_t)threadIdx.x * kScanItems + i;
-    if (idx < n) out[idx] = run;
+    if (idx < n) out[idx] = clamp < 0 ? run : (int32_t)min(max((int64_t)run, (int64_t)0), clamp);
     run += v[i];
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = tile_off[blockIdx.x] + tot;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const int32_t last = tile_off[blockIdx.x] + tot;
+    out[n] = clamp < 0 ? last : (int32_t)min(max((int64_t)last, (int64_t)0), clamp);
+  }
 }
 
 __global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
@@ -205,6 +211,85 @@ __global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
         pos_sorted[2 * np + slot[u]] = pos[2 * np + p];
       }
       if (ids_sorted) ids_sorted[slot[u]] = ids[p];
+    }
+  }
+}
+
+// Scatter for bins counted by an earlier kernel (bin_run's `counted`), which
+// leaves no ranks: lanes of a warp with the same bin take a run of its slots
+// by one atomicSub on the bin's counter (the counters end at zero).  Each bin
+// and run is checked against the bin's range of slots before the writes; a
+// particle that fails is skipped and reported, as is a total that is not np.
+// Every warp makes the same number of trips (warp-wide intrinsics).
+__global__ void bin_scatter_counted(int64_t np, const double* __restrict__ pos,
+                                    const int32_t* __restrict__ bin_of,
+                                    int32_t* __restrict__ counts,
+                                    const int32_t* __restrict__ offsets,
+                                    int64_t* __restrict__ perm,
+                                    double* __restrict__ pos_sorted,
+                                    const int64_t* __restrict__ ids,
+                                    int64_t* __restrict__ ids_sorted, int64_t nbins,
+                                    int32_t* status) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && offsets[nbins] != np)
+    flag_status(status, PS_DEV_BAD_BINS, offsets[nbins]);
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t base = wid * 32 * kCountUnroll; base < np; base += warps * 32 * kCountUnroll) {
+    int key[kCountUnroll];
+    double x[kCountUnroll], y[kCountUnroll], z[kCountUnroll];
+    int64_t id[kCountUnroll];
+    // bins and payloads of all groups first
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      key[u] = -1 - lane;  // unique per lane when invalid
+      x[u] = y[u] = z[u] = 0.0;
+      id[u] = 0;
+      if (p < np) {
+        const int bn = bin_of[p];
+        if ((uint64_t)(int64_t)bn < (uint64_t)nbins) key[u] = bn;
+        else flag_status(status, PS_DEV_BAD_BINS, p);
+        if (pos_sorted) {
+          x[u] = pos[p];
+          y[u] = pos[np + p];
+          z[u] = pos[2 * np + p];
+        }
+        if (ids_sorted) id[u] = ids[p];
+      }
+    }
+    // one atomic per run of equal bins, all groups' atomics in flight together
+    unsigned peers[kCountUnroll];
+    int old[kCountUnroll];
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      peers[u] = __match_any_sync(FULL, key[u]);
+      old[u] = 0;
+      if (key[u] >= 0 && lane == __ffs(peers[u]) - 1)
+        old[u] = atomicSub(&counts[key[u]], __popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int leader = __ffs(peers[u]) - 1;
+      const int top = __shfl_sync(FULL, old[u], leader);
+      if (key[u] < 0) continue;
+      const int64_t p = base + u * 32 + lane;
+      const int len = __popc(peers[u]);
+      const int r = top - len + __popc(peers[u] & ((1u << lane) - 1u));
+      const int64_t lo = offsets[key[u]], hi = offsets[key[u] + 1];
+      if (top - len < 0 || (int64_t)top > hi - lo) {
+        flag_status(status, PS_DEV_BAD_BINS, p);
+        continue;
+      }
+      const int64_t slot = lo + r;
+      if (perm) perm[slot] = p;
+      if (pos_sorted) {
+        pos_sorted[slot] = x[u];
+        pos_sorted[np + slot] = y[u];
+        pos_sorted[2 * np + slot] = z[u];
+      }
+      if (ids_sorted) ids_sorted[slot] = id[u];
     }
   }
 }
@@ -288,11 +373,13 @@ size_t bin_ws_bytes(const BrickArgs& b, int64_t np, bool need_offsets, bool need
 ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np, const double* pos,
                   int32_t* bin_of, int32_t* bin_offsets, int64_t* perm, double* pos_sorted,
                   const int64_t* ids, int64_t* ids_sorted, int32_t* counts, int32_t* rank,
-                  int32_t* scan_tmp, int32_t* status, cudaStream_t st) {
-  ps_status rc = check_cuda(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (ba.nbins + 1), st),
-                            "bin counts memset");
-  if (rc) return rc;
-  if (np > 0) {
+                  int32_t* scan_tmp, int32_t* status, cudaStream_t st, bool counted) {
+  ps_status rc = PS_OK;
+  if (!counted &&
+      (rc = check_cuda(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (ba.nbins + 1), st),
+                       "bin counts memset")))
+    return rc;
+  if (np > 0 && !counted) {
     bin_count_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(ga, ba, np, pos, bin_of,
                                                                  rank, counts, status);
     if ((rc = check_launch("bin_count"))) return rc;
@@ -303,11 +390,16 @@ ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np, const dou
   scan_tile_offsets<<<1, kScanThreads, 0, st>>>(scan_tmp, ntiles);
   if ((rc = check_launch("scan_tile_offsets"))) return rc;
   scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, ba.nbins, scan_tmp,
-                                                        bin_offsets);
+                                                        bin_offsets, counted ? np : -1);
   if ((rc = check_launch("scan_tiles"))) return rc;
   if (np > 0 && (perm || pos_sorted || ids_sorted)) {
-    bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
-        np, pos, bin_of, rank, bin_offsets, perm, pos_sorted, ids, ids_sorted);
+    if (counted)
+      bin_scatter_counted<<<persistent_blocks(np, 256), 256, 0, st>>>(
+          np, pos, bin_of, counts, bin_offsets, perm, pos_sorted, ids, ids_sorted, ba.nbins,
+          status);
+    else
+      bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
+          np, pos, bin_of, rank, bin_offsets, perm, pos_sorted, ids, ids_sorted);
     if ((rc = check_launch("bin_scatter"))) return rc;
   }
   return PS_OK;
@@ -332,7 +424,7 @@ ps_status bin_run_batch(const BinField* d_tab, int nfields, int64_t total_bins, 
   scan_tile_offsets<<<1, kScanThreads, 0, st>>>(scan_tmp, ntiles);
   if ((rc = check_launch("scan_tile_offsets"))) return rc;
   scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, total_bins, scan_tmp,
-                                                        bin_offsets);
+                                                        bin_offsets, -1);
   if ((rc = check_launch("scan_tiles"))) return rc;
   if (np > 0) {
     bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
@@ -374,7 +466,7 @@ extern "C" ps_status ps_bin_particles(const ps_grid* grid, const int32_t brick[3
   int32_t* rank = c.take<int32_t>(np);
   GridArgs ga = make_grid_args(grid);
   return bin_run(ga, ba, np, pos, bin_of, bin_offsets, perm, pos_sorted, nullptr, nullptr,
-                 counts, rank, scan_tmp, status, as_stream(stream));
+                 counts, rank, scan_tmp, status, as_stream(stream), false);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,5 +540,5 @@ extern "C" ps_status ps_bin_particles_noalloc(const ps_grid* grid, const int32_t
   // bin_run clears the counters before counting, so the contents left by the
   // previous call do not matter
   return bin_run(ga, ba, np, pos, bin_of, bin_offsets, perm, pos_sorted, nullptr, nullptr,
-                 counts, rank, scan_tmp, status, as_stream(stream));
+                 counts, rank, scan_tmp, status, as_stream(stream), false);
 }

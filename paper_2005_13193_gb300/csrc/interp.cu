@@ -480,6 +480,11 @@ struct StagedArgs {
   double dt;
   float dtih[3];  // dt * n/L per axis
   int32_t* status;
+  // counting pass of the next step's bin sort (NULL = off): each particle's
+  // new bin at its slot in pos_out, bin counters (zeroed beforehand)
+  int32_t* next_counts;
+  int32_t* next_bin;
+  int bshift[3];  // log2 of the brick extent, -1 if not a power of two
   CUtensorMap tmap;   // node halo box (valid when tma == 1)
   CUtensorMap tmap2;  // 16-bit nodes: the box of the halo rows' scales
 };
@@ -1122,7 +1127,10 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       if (vi && sub == 0) R.u()[i] = make_float4(u[0], u[1], u[2], __int_as_float(oki ? 1 : 0));
     }
     __syncthreads();
-    // phase C: FP64 position update, one thread per (particle, axis)
+    // phase C: FP64 position update, one thread per (particle, axis); with
+    // next_counts the new brick coordinate along the axis goes to the
+    // gradient records, which the Heun step leaves unused
+    int* nbc = reinterpret_cast<int*>(R.db(0));
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
       if (td[k] >= 0) {
@@ -1130,16 +1138,51 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
         const float4 r = R.u()[i];
         const bool ok = __float_as_int(r.w) != 0;
         const int64_t pp = tp[k];
-        a.pos_out[d * np + pp] = ok ? fma(a.dt * 0.5, (double)(tu1[k] + f4get(r, d)), tx[k])
-                                    : __longlong_as_double(0x7ff8000000000000ll);
+        const double xn = ok ? fma(a.dt * 0.5, (double)(tu1[k] + f4get(r, d)), tx[k])
+                             : __longlong_as_double(0x7ff8000000000000ll);
+        a.pos_out[d * np + pp] = xn;
         if (a.vel) a.vel[d * np + pp] = ok ? tu1[k] : nanf_;
         if (d == 0) {
           if (a.ids_out) a.ids_out[pp] = a.ids_in[pp];
           if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, pp);
         }
+        if (a.next_counts) {
+          // The new cell: the stage-1 cell plus the floor of its fraction plus
+          // the displacement in cells, in FP32.  That floor is the exact one
+          // wherever the sum lies 2^-10 or more from a cell face and
+          // |x n/L| < 2^30: the FP32 and FP64 roundings on both routes stay
+          // below 1e-6 cell.  Elsewhere (and for positions that are not
+          // finite) the FP64 location decides.
+          const float w = tt[k] + 0.5f * a.dtih[d] * (tu1[k] + f4get(r, d));
+          const float fl = floorf(w), fr = w - fl;
+          int c;
+          if (ok && fr >= 0x1p-10f && fr <= 1.f - 0x1p-10f && fabsf(fl) <= 2.f &&
+              fabsf((float)tx[k]) * g.inv_hf[d] < 0x1p30f) {
+            const int nd = g.n[d];
+            c = tcell[k] + (int)fl;  // in [-2, n + 1], n >= 3
+            c = c < 0 ? c + nd : (c >= nd ? c - nd : c);
+          } else {
+            float tn;
+            if (!locate(xn, g.inv_h[d], g.n[d], c, tn)) c = -1;
+          }
+          nbc[d * kRecords + i] =
+              c < 0 ? -1 : (a.bshift[d] >= 0 ? c >> a.bshift[d] : c / a.b.B[d]);
+        }
       }
     }
     __syncthreads();
+    // phase D: the next step's counting, one thread per particle in the last
+    // kRecords / 32 warps, which hold fewer (particle, axis) tasks in phases
+    // A and C than the first ones (nothing below reads these records before
+    // the next round's phase C, several barriers on)
+    if (a.next_counts && warp >= nwarps - kRecords / 32) {
+      const int i = tid - (nwarps * 32 - kRecords);
+      const bool vi = i < m;
+      const int64_t pp = vi ? (a.perm ? a.perm[cb + i] : (int64_t)(cb + i)) : 0;
+      const int key = vi ? bin_of_coords(a.b, nbc[i], nbc[kRecords + i], nbc[2 * kRecords + i])
+                         : 0;
+      count_into_bin(a.next_counts, a.next_bin, a.status, vi, pp, key);
+    }
     }  // MODE == 2
   }
   // a copy still in flight must land before the block's memory is released
@@ -1370,15 +1413,24 @@ __device__ __forceinline__ void brick_warps(const StagedArgs& a, int beg, int en
       float u2[NC];
       gather_group<Tc, NC, false>(halo, hg.PS, hg.SX, inh2, l, c2, t2, g, cf2, sc2, q, kh, kx, kz0,
                                   kz1, u2, dx, dy, dz);
+      const float u1d = sel3(u, ax), u2d = sel3(u2, ax);
+      const double xnew = ok ? fma(a.dt * 0.5, (double)(u1d + u2d), x)
+                             : __longlong_as_double(0x7ff8000000000000ll);
       if (vi && sub < 3) {
-        const float u1d = sel3(u, ax), u2d = sel3(u2, ax);
-        a.pos_out[ax * np + p] = ok ? fma(a.dt * 0.5, (double)(u1d + u2d), x)
-                                    : __longlong_as_double(0x7ff8000000000000ll);
+        a.pos_out[ax * np + p] = xnew;
         if (a.vel) a.vel[ax * np + p] = ok ? u1d : nanf_;
         if (sub == 0) {
           if (a.ids_out) a.ids_out[p] = a.ids_in[p];
           if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
         }
+      }
+      if (a.next_counts) {
+        // the next step's counting: lane sub < 3 of a group holds axis sub
+        const int bc = vi && sub < 3 ? brick_coord(g, a.b, xnew, ax) : 0;
+        const int key = bin_of_coords(a.b, __shfl_sync(FULL, bc, gb),
+                                      __shfl_sync(FULL, bc, gb + 1),
+                                      __shfl_sync(FULL, bc, gb + 2));
+        count_into_bin(a.next_counts, a.next_bin, a.status, vi && sub == 0, p, key);
       }
     }
     if (more) {
@@ -1789,14 +1841,28 @@ __global__ void __launch_bounds__(64) interp_thread(StagedArgs a) {
         gather1<Tc, NC, false>(a, coef, a.scale, halo, P0, c2, t2, r2);
       }
       const double half_dt = a.dt * 0.5;
+      int bc[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        a.pos_out[d * np + p] = ok ? fma(half_dt, (double)(u1[d] + r2.u[d]), x[d])
-                                   : __longlong_as_double(0x7ff8000000000000ll);
+        const double xn = ok ? fma(half_dt, (double)(u1[d] + r2.u[d]), x[d])
+                             : __longlong_as_double(0x7ff8000000000000ll);
+        a.pos_out[d * np + p] = xn;
         if (a.vel) a.vel[d * np + p] = ok ? u1[d] : nanf_;
+        bc[d] = a.next_counts ? brick_coord(g, a.b, xn, d) : 0;
       }
       if (a.ids_out) a.ids_out[p] = a.ids_in[p];
       if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+      if (a.next_counts) {
+        // the next step's counting, one atomic per particle (this loop's
+        // lanes leave it at different trips)
+        int key = bin_of_coords(a.b, bc[0], bc[1], bc[2]);
+        if (key < 0) {
+          flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+          key = 0;
+        }
+        a.next_bin[p] = key;
+        atomicAdd(&a.next_counts[key], 1);
+      }
     }
   }
 }
@@ -2002,7 +2068,11 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   if (rc) return rc;
   a->g = make_grid_args(grid, coef_t);
   a->E = E;
-  for (int d = 0; d < 3; ++d) a->S[d] = a->b.B[d] + 3 + 2 * E;
+  for (int d = 0; d < 3; ++d) {
+    a->S[d] = a->b.B[d] + 3 + 2 * E;
+    const int B = a->b.B[d];
+    a->bshift[d] = (B & (B - 1)) ? -1 : __builtin_ctz((unsigned)B);
+  }
   if (a->S[0] > 32) return fail(PS_ERR_UNSUPPORTED, "brick x extent above 29 cells");
   a->SX = a->S[0];
   a->PS = plane_stride(a->SX, a->S[1]);
@@ -2277,7 +2347,8 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
                             const void* c1, const float* s1, int64_t np,
                             const double* pos_in, double* pos_out, const int32_t* offs,
                             float* vel_out, const int64_t* ids_in, int64_t* ids_out,
-                            double dt, int32_t* status, cudaStream_t st) {
+                            double dt, int32_t* status, int32_t* next_counts,
+                            int32_t* next_bin, cudaStream_t st) {
   if (coef_t == PS_F64)
     return fail(PS_ERR_UNSUPPORTED, "staged RK2 needs F32/BF16/F16 coefficients");
   StagedArgs a{};
@@ -2302,6 +2373,8 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
   a.dtih[1] = d.y;
   a.dtih[2] = d.z;
   a.status = status;
+  a.next_counts = next_counts;
+  a.next_bin = next_bin;
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
     if constexpr (std::is_same<Tc, double>::value) return PS_ERR_UNSUPPORTED;

@@ -94,7 +94,7 @@ ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np,
                   const double* pos, int32_t* bin_of, int32_t* bin_offsets,
                   int64_t* perm, double* pos_sorted, const int64_t* ids,
                   int64_t* ids_sorted, int32_t* counts, int32_t* rank,
-                  int32_t* scan_tmp, int32_t* status, cudaStream_t st);
+                  int32_t* scan_tmp, int32_t* status, cudaStream_t st, bool counted);
 size_t scan_tmp_elems(int64_t nbins);
 
 // Many-field binning (batch.cu): one entry per field.
@@ -181,6 +181,43 @@ __device__ __forceinline__ bool locate(double x, double inv_h, int n, int& cell,
   }
   cell = (int)m;
   return true;
+}
+
+// Brick coordinate along axis d of a position (cell / B), -1 for a position
+// that locate rejects.  The counting pass of the bin sort and the kernels that
+// count for the next step's sort both derive bins from these two functions,
+// so a particle lands in the same bin whichever of them counts it.
+__device__ __forceinline__ int brick_coord(const GridArgs& g, const BrickArgs& b, double x,
+                                           int d) {
+  int c;
+  float t;
+  return locate(x, g.inv_h[d], g.n[d], c, t) ? c / b.B[d] : -1;
+}
+
+// Bin of brick (bx, by, bz), x fastest; -1 if a coordinate is -1.
+__device__ __forceinline__ int bin_of_coords(const BrickArgs& b, int bx, int by, int bz) {
+  return (bx | by | bz) < 0 ? -1 : (bz * b.nb[1] + by) * b.nb[0] + bx;
+}
+
+// Counting step of the bin sort for the particles a warp holds: lane l has
+// particle p (valid) whose bin is key (-1: position rejected; it is counted
+// in bin 0 and reported, as the counting pass does).  The bin goes to
+// bin_of[p]; lanes with equal keys add to the bin's counter with one atomic
+// whose result is not waited for (the scatter takes the ranks later).  All
+// 32 lanes must call.
+__device__ __forceinline__ void count_into_bin(int32_t* counts, int32_t* bin_of,
+                                               int32_t* status, bool valid, int64_t p,
+                                               int key) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  if (valid && key < 0) {
+    flag_status(status, PS_DEV_NONFINITE_POS, p);
+    key = 0;
+  }
+  const int k = valid ? key : -1 - lane;  // unique per lane when invalid
+  const unsigned peers = __match_any_sync(FULL, k);
+  if (valid && lane == __ffs(peers) - 1) atomicAdd(&counts[k], __popc(peers));
+  if (valid) bin_of[p] = k;
 }
 
 // FP64 variant for FP64 coefficients: t = s - floor(s) in FP64.

@@ -92,3 +92,14 @@ def test_bad_arguments_rejected_on_host():
     rc = lib.ps_rk2_step(ctypes.byref(g), _abi.PS_F32, P, None, None, None, 10, P, None, None,
                          float("nan"), None, 0, None, None, 0, None, None)
     assert rc == _abi.PS_ERR_INVALID_ARG
+    # rebin outside 0..3
+    for bad in (-1, 4):
+        rc = lib.ps_rk2_step(ctypes.byref(g), _abi.PS_F32, P, None, None, None, 10, P, None,
+                             None, 1e-3, brick, bad, P, P, 1 << 30, None, None)
+        assert rc == _abi.PS_ERR_INVALID_ARG
+        assert b"rebin" in lib.ps_last_error()
+    # rebin 2 and 3 need the workspace like rebin 1
+    for mode in (1, 2, 3):
+        rc = lib.ps_rk2_step(ctypes.byref(g), _abi.PS_F32, P, None, None, None, 10, P, None,
+                             None, 1e-3, brick, mode, P, None, 0, None, None)
+        assert rc == _abi.PS_ERR_WORKSPACE

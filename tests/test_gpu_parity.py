@@ -618,3 +618,178 @@ def test_lagrangian_accel_matches_oracle(two_fields):
     if two_fields:
         tol += 2 * 1e-5 * 3 * rms / dt
     assert np.abs(a - ref).max() <= tol
+
+
+def _slot_bins(offs):
+    return np.repeat(np.arange(len(offs) - 1), np.diff(offs))
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kind", [torch.float32, ps.F32X4, torch.bfloat16])
+def test_rk2_counted_sort_matches_full_sort(kernel, kind, brick_kernel):
+    # Steps whose sort starts from the counts the previous step's kernel took
+    # while it stored the positions (rebin 2, then 3: the departing particles
+    # found during the update, Sec. 4.3) give every particle the bits of steps
+    # that sort from scratch (rebin 1) and the same bin bounds, which are
+    # those of the oracle's counting sort of each step's starting positions.
+    ps.ps_tune_set("brick_kernel", kernel)
+    n, brick, np_ = (48, 40, 32), (8, 8, 8), 30000
+    field, pos, _ = _case(n, np_, seed=151, spread=1.3)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), kind)
+    dt = 4e-2  # a quarter of a cell per step at unit speed: many particles change brick
+    full = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick, incremental=False)
+    inc = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick)
+    prev_bin = None
+    moved = 0
+    for _ in range(4):
+        start = np.empty_like(pos)
+        start[:, full.ids.cpu().numpy()] = full.pos.cpu().numpy()  # by particle id
+        bin_id, off_ora, _ = oracle.bin_particles(n, brick, start)
+        if prev_bin is not None:
+            moved += int((bin_id != prev_bin).sum())
+        prev_bin = bin_id
+        full.step(dt)
+        inc.step(dt)
+        for tr in (full, inc):
+            np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
+            ids = tr.ids.cpu().numpy()
+            # storage order: the bin order of the starting positions
+            np.testing.assert_array_equal(bin_id[ids], _slot_bins(off_ora))
+        fi, ii = np.argsort(full.ids.cpu().numpy()), np.argsort(inc.ids.cpu().numpy())
+        assert np.array_equal(full.pos.cpu().numpy()[:, fi], inc.pos.cpu().numpy()[:, ii])
+        assert np.array_equal(full.vel.cpu().numpy()[:, fi], inc.vel.cpu().numpy()[:, ii])
+    assert ps.ps_status_read(full.status)[0] == 0
+    assert ps.ps_status_read(inc.status)[0] == 0
+    assert moved > 1000
+
+
+def test_rk2_counted_sort_with_changed_positions():
+    # positions changed between steps leave the counts in the workspace stale:
+    # the sort then follows the old bins, and particles outside their brick's
+    # halo read their stencils from global memory, so results stay exact
+    n = (32, 32, 32)
+    field, pos, cref = _case(n, 8000, seed=171)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=(8, 8, 8))
+    dt = 1e-2
+    tr.step(dt)
+    tr.pos += 0.37  # 1.9 cells: most particles leave their brick
+    ids0 = tr.ids.cpu().numpy()
+    start = tr.pos.cpu().numpy()
+    tr.step(dt)  # rebin 3 with the counts of the unshifted positions
+    new_ref, u1_ref = oracle.rk2_step(cref, start, dt)
+    by_id = np.empty_like(new_ref)
+    by_id[:, ids0] = new_ref
+    rms = np.sqrt((u1_ref ** 2).mean())
+    ids = tr.ids.cpu().numpy()
+    assert np.abs(tr.pos.cpu().numpy() - by_id[:, ids]).max() <= dt * 1e-5 * rms + 1e-13
+    assert ps.ps_status_read(tr.status)[0] == 0
+    # reset_bins: the next step sorts from the positions again
+    tr.reset_bins()
+    start = tr.pos.cpu().numpy()
+    tr.step(dt)
+    _, off_ora, _ = oracle.bin_particles(n, (8, 8, 8), start)
+    np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
+
+
+@pytest.mark.parametrize("fill", [0, 255])
+def test_rk2_counted_sort_rejects_foreign_counts(fill):
+    # rebin 3 on a workspace that holds no counts of these positions: slots
+    # are checked against their bin's range and bin bounds are clamped to the
+    # particle count, so every access stays inside the arrays; the status word
+    # reports PS_DEV_BAD_BINS and the particles keep their positions.  A
+    # rebin 2 step on the same workspace then restores the counts.
+    n, brick, np_ = (32, 32, 32), (8, 8, 8), 5000
+    field, pos, cref = _case(n, np_, seed=181)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    p = torch.from_numpy(pos.copy()).to(DEV)
+    ws = ps.workspace(ps.ps_rk2_workspace_size(n, brick, np_), DEV)
+    ws.fill_(fill)
+    offs = torch.empty(4 ** 3 + 1, dtype=torch.int32, device=DEV)
+    status = torch.zeros(4, dtype=torch.int32, device=DEV)
+    ps.ps_rk2_step(sf.coef, n, p, 1e-2, brick=brick, rebin=3, bin_offsets=offs, ws=ws,
+                   status=status)
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    assert st[0] == ps._abi.PS_DEV_BAD_BINS
+    assert torch.equal(p.cpu(), torch.from_numpy(pos))
+    status.zero_()
+    dt = 1e-2
+    ps.ps_rk2_step(sf.coef, n, p, dt, brick=brick, rebin=2, bin_offsets=offs, ws=ws,
+                   status=status)
+    mid = p.cpu().numpy()
+    ps.ps_rk2_step(sf.coef, n, p, dt, brick=brick, rebin=3, bin_offsets=offs, ws=ws,
+                   status=status)
+    torch.cuda.synchronize()
+    assert status.cpu().numpy()[0] == 0
+    _, off_ora, _ = oracle.bin_particles(n, brick, mid)
+    np.testing.assert_array_equal(offs.cpu().numpy(), off_ora)
+
+
+def test_rk2_sort_then_step_equals_rebinned_step():
+    # ps_rk2_step(rebin 2, then 3) is ps_rk2_sort followed by the rebin 0 step
+    # with the workspace: driven with the caller's own buffers in ping-pong the
+    # two give the same bits, the same bin bounds and the same velocities
+    n, brick, np_ = (40, 32, 24), (8, 8, 8), 12000
+    field, pos, _ = _case(n, np_, seed=191, spread=1.2)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), ps.F32X4)
+    dt = 3e-2
+    tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick)
+    ws = ps.workspace(ps.ps_rk2_workspace_size(n, brick, np_), DEV)
+    offs = torch.empty_like(tr.offsets)
+    status = torch.zeros(4, dtype=torch.int32, device=DEV)
+    bufs = [torch.from_numpy(pos.copy()).to(DEV), torch.empty((3, np_), dtype=torch.float64,
+                                                              device=DEV)]
+    idb = [torch.arange(np_, dtype=torch.int64, device=DEV), torch.empty(np_, dtype=torch.int64,
+                                                                         device=DEV)]
+    vel = torch.empty((3, np_), dtype=torch.float32, device=DEV)
+    for k in range(3):
+        tr.step(dt)
+        ps.ps_rk2_sort(n, brick, bufs[0], bufs[1], offs, ws, ids=idb[0], ids_sorted=idb[1],
+                       counted=k > 0, status=status)
+        ps.ps_rk2_step(sf.coef, n, bufs[1], dt, vel_out=vel, brick=brick, rebin=0,
+                       bin_offsets=offs, ws=ws, status=status)
+        bufs.reverse()
+        idb.reverse()
+        assert torch.equal(offs, tr.offsets)
+        a, b = torch.argsort(tr.ids), torch.argsort(idb[0])
+        assert torch.equal(tr.pos[:, a], bufs[0][:, b])
+        assert torch.equal(tr.vel[:, a], vel[:, b])
+    assert ps.ps_status_read(status)[0] == 0
+    assert ps.ps_status_read(tr.status)[0] == 0
+
+
+@pytest.mark.parametrize("kernel", [0, 2, 3])
+def test_rk2_counted_sort_at_cell_faces(kernel, brick_kernel):
+    # A constant field moves every particle by exactly dt u; targets are put on
+    # cell faces, just either side of them (down to 1e-13 of a cell) and at the
+    # 2^-10 margin of the step kernel's FP32 shortcut, some far from the
+    # origin.  The counts the step takes must be the oracle's counts of the
+    # positions it wrote, face for face.
+    ps.ps_tune_set("brick_kernel", kernel)
+    n, brick = (16, 16, 16), (8, 8, 8)
+    h = TWO_PI / 16
+    u = np.array([0.75, -0.5, 0.3125])
+    field = np.broadcast_to(u[:, None, None, None], (3, 16, 16, 16)).astype(np.float32).copy()
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), ps.F32X4)
+    dt = 0.37 * h
+    eps = [0.0, 1e-13, -1e-13, 1e-9, -1e-9, 1e-6, -1e-6, 2.0 ** -10, -(2.0 ** -10),
+           2.0 ** -10 + 1e-6, 2.0 ** -10 - 1e-6, 0.5]
+    rng = np.random.default_rng(7)
+    tgt = []
+    for e in eps:
+        for far in (0, 1 << 20, -(1 << 31), 3 << 40):
+            face = rng.integers(0, 16, size=3) + far
+            tgt.append((face + e) * h)
+    tgt = np.array(tgt).T  # [3][m]
+    m = tgt.shape[1]
+    pos0 = tgt - dt * u[:, None]
+    p = torch.from_numpy(pos0.copy()).to(DEV)
+    tr = ps.Tracker(sf, p, brick=brick)
+    tr.step(dt)  # rebin 2: counts the written positions
+    after = tr.pos.cpu().numpy()
+    tr.step(dt)  # rebin 3: sorts from those counts
+    _, off_ora, _ = oracle.bin_particles(n, brick, after)
+    np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
+    assert ps.ps_status_read(tr.status)[0] == 0
+    assert m == len(eps) * 4
