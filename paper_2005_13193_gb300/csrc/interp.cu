@@ -835,30 +835,39 @@ __device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
 // round (kRecords), stored field-major so that neither the per-axis writers
 // nor the 8-lane readers conflict on banks:
 //   b[d][i]    float4  b_0..3(t_d) of particle i along axis d
-//   db[d][i]   float4  b'_0..3(t_d)   (gradient mode)
+//   u[i]       float4  (u, v, w, ok) result of the last gather
+//   db[d][i]   float4  b'_0..3(t_d)   (gradient mode only)
 //   loc[d][i]  int     brick-local stencil start along d, -1 = outside halo
 //   cell[d][i] int     global cell along d, -1 = position not finite
-//   u[i]       float4  (u, v, w, ok) result of the last gather
-constexpr int kRecords = 64;   // particles per round
+//   nbc[d][i]  int     brick of the new position along d (Heun step only)
+// 80 particles per round: a brick of the mid density (64 particles on
+// average, Poisson) rarely needs a second, mostly empty round, and the 240
+// (particle, axis) tasks still fit two per thread.
+constexpr int kRecords = 80;   // particles per round
 constexpr int kThreads = 128;  // threads per brick CTA
 
 struct Recs {
-  float4* f;  // b[3], db[3], u: 7 * kRecords float4
-  int* ip;    // lw, cell[3]:     4 * kRecords int
+  float4* f;  // b[3], u, then db[3] in gradient mode
+  int* ip;    // lw, cell[3], then nbc[3] in the Heun step
   __device__ __forceinline__ float4* b(int d) const { return f + d * kRecords; }
-  __device__ __forceinline__ float4* db(int d) const { return f + (3 + d) * kRecords; }
-  __device__ __forceinline__ float4* u() const { return f + 6 * kRecords; }
+  __device__ __forceinline__ float4* u() const { return f + 3 * kRecords; }
+  __device__ __forceinline__ float4* db(int d) const { return f + (4 + d) * kRecords; }
   // byte d of lw[i]: brick-local stencil start along d, -1 outside the halo,
   // -2 position not finite
   __device__ __forceinline__ int* lw() const { return ip; }
   __device__ __forceinline__ int* cell(int d) const { return ip + (1 + d) * kRecords; }
+  __device__ __forceinline__ int* nbc(int d) const { return ip + (4 + d) * kRecords; }
 };
-constexpr size_t kRecBytes = (size_t)kRecords * (7 * sizeof(float4) + 4 * sizeof(int));
+__host__ __device__ constexpr size_t rec_bytes(bool grad) {
+  return (size_t)kRecords * (grad ? 7 * sizeof(float4) + 4 * sizeof(int)
+                                  : 4 * sizeof(float4) + 7 * sizeof(int));
+}
 
+template <bool GRAD>
 __device__ __forceinline__ Recs carve_recs(void* base) {
   Recs r;
   r.f = static_cast<float4*>(base);
-  r.ip = reinterpret_cast<int*>(r.f + 7 * kRecords);
+  r.ip = reinterpret_cast<int*>(r.f + (GRAD ? 7 : 4) * kRecords);
   return r;
 }
 
@@ -1048,8 +1057,8 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
         // copy's rows are SX nodes long, the halo's rows too (dense planes)
         const Tc* nodes = reinterpret_cast<const Tc*>(raw16);
         const float4* scl = reinterpret_cast<const float4*>(
-            raw16 + (node16_scale_offset(hg.Sz, hg.PS, hg.Sy, hg.SX, kRecBytes) -
-                     node16_raw_offset(hg.Sz, hg.PS, kRecBytes)));
+            raw16 + (node16_scale_offset(hg.Sz, hg.PS, hg.Sy, hg.SX, rec_bytes(GRAD)) -
+                     node16_raw_offset(hg.Sz, hg.PS, rec_bytes(GRAD))));
         float4* h = const_cast<float4*>(halo);
         const int npts = hg.Sz * hg.Sy * hg.SX;
         for (int it = threadIdx.x; it < npts; it += blockDim.x) {
@@ -1128,9 +1137,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
     }
     __syncthreads();
     // phase C: FP64 position update, one thread per (particle, axis); with
-    // next_counts the new brick coordinate along the axis goes to the
-    // gradient records, which the Heun step leaves unused
-    int* nbc = reinterpret_cast<int*>(R.db(0));
+    // next_counts the new brick coordinate along the axis goes to nbc
 #pragma unroll
     for (int k = 0; k < TPT; ++k) {
       if (td[k] >= 0) {
@@ -1165,22 +1172,21 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
             float tn;
             if (!locate(xn, g.inv_h[d], g.n[d], c, tn)) c = -1;
           }
-          nbc[d * kRecords + i] =
-              c < 0 ? -1 : (a.bshift[d] >= 0 ? c >> a.bshift[d] : c / a.b.B[d]);
+          R.nbc(d)[i] = c < 0 ? -1 : (a.bshift[d] >= 0 ? c >> a.bshift[d] : c / a.b.B[d]);
         }
       }
     }
     __syncthreads();
     // phase D: the next step's counting, one thread per particle in the last
-    // kRecords / 32 warps, which hold fewer (particle, axis) tasks in phases
-    // A and C than the first ones (nothing below reads these records before
-    // the next round's phase C, several barriers on)
-    if (a.next_counts && warp >= nwarps - kRecords / 32) {
-      const int i = tid - (nwarps * 32 - kRecords);
+    // warps, which hold fewer (particle, axis) tasks in phases A and C than
+    // the first ones (nothing below reads these records before the next
+    // round's phase C, several barriers on)
+    constexpr int kCountWarps = (kRecords + 31) / 32;
+    if (a.next_counts && warp >= nwarps - kCountWarps) {
+      const int i = tid - (nwarps - kCountWarps) * 32;
       const bool vi = i < m;
       const int64_t pp = vi ? (a.perm ? a.perm[cb + i] : (int64_t)(cb + i)) : 0;
-      const int key = vi ? bin_of_coords(a.b, nbc[i], nbc[kRecords + i], nbc[2 * kRecords + i])
-                         : 0;
+      const int key = vi ? bin_of_coords(a.b, R.nbc(0)[i], R.nbc(1)[i], R.nbc(2)[i]) : 0;
       count_into_bin(a.next_counts, a.next_bin, a.status, vi, pp, key);
     }
     }  // MODE == 2
@@ -1489,7 +1495,7 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
   const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
   const Tc* coef = static_cast<const Tc*>(a.coef);
   float4* halo = smem;
-  const Recs R = carve_recs(smem + a.S[2] * a.PS);
+  const Recs R = carve_recs<MODE == 1>(smem + a.S[2] * a.PS);
   if (end - beg < a.min_stage || a.chunked) {
     // an origin far from every cell sends every stencil to global memory
     const int far[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
@@ -1504,8 +1510,9 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
       using G = HaloGeo<12>;
       if constexpr (IsNode16<Tc>::value) {
         unsigned char* base = reinterpret_cast<unsigned char*>(smem);
-        unsigned char* raw = base + node16_raw_offset(G::Sz, G::PS, kRecBytes);
-        unsigned char* sraw = base + node16_scale_offset(G::Sz, G::PS, G::Sy, G::SX, kRecBytes);
+        unsigned char* raw = base + node16_raw_offset(G::Sz, G::PS, rec_bytes(MODE == 1));
+        unsigned char* sraw =
+            base + node16_scale_offset(G::Sz, G::PS, G::Sy, G::SX, rec_bytes(MODE == 1));
         if (threadIdx.x == 0)
           tma_issue_node16(&maps->tmap, &maps->tmap2, raw, sraw, &mbar, P0,
                            (unsigned)(G::Sz * G::Sy * (G::SX * 8 + 16)));
@@ -1574,7 +1581,7 @@ __global__ void __launch_bounds__(kThreads, 6) interp_staged_pipe(const __grid_c
   __shared__ __align__(8) unsigned long long mbar[2];
   if constexpr (IsNode4<Tc>::value && !IsNode16<Tc>::value) {
     float4* H[2] = {smem_p, smem_p + HSP};
-    const Recs R = carve_recs(smem_p + 2 * HSP);
+    const Recs R = carve_recs<MODE == 1>(smem_p + 2 * HSP);
     const int nb = (int)a.b.nbins;
     int bin = next_busy(a, blockIdx.x);
     if (bin >= nb) return;
@@ -2004,9 +2011,9 @@ template <typename Tc, int NC, int MODE>
 __global__ void __launch_bounds__(256, 3) track_bricks(StagedArgs a) {
   extern __shared__ float4 smem[];
   float4* halo = smem;
-  const Recs R = carve_recs(halo + a.S[2] * a.PS);
+  const Recs R = carve_recs<MODE == 1>(halo + a.S[2] * a.PS);
   double* pbuf = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(halo + a.S[2] * a.PS) +
-                                           kRecBytes);
+                                           rec_bytes(MODE == 1));
   unsigned char* raw = reinterpret_cast<unsigned char*>(pbuf + 3 * kRecords);
   int bin = next_busy(a, blockIdx.x);
   const int nb = (int)a.b.nbins;
@@ -2063,7 +2070,7 @@ int plane_stride(int sx, int sy) {
 }
 
 ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[3], int E,
-                      StagedArgs* a, size_t* smem) {
+                      bool grad, StagedArgs* a, size_t* smem) {
   ps_status rc = make_brick_args(grid, brick, &a->b);
   if (rc) return rc;
   a->g = make_grid_args(grid, coef_t);
@@ -2101,10 +2108,10 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   a->tma = 0;
   const bool n16 = coef_t == PS_BF16X4 || coef_t == PS_F16X4;
   a->min_stage = tuning().brick_min_stage;
-  *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + kRecBytes;
+  *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + rec_bytes(grad);
   // room for a tensor copy of 16-bit nodes and their rows' scales
   if (n16 && vec)
-    *smem = node16_scale_offset(a->S[2], a->PS, a->S[1], a->SX, kRecBytes) +
+    *smem = node16_scale_offset(a->S[2], a->PS, a->S[1], a->SX, rec_bytes(grad)) +
             (size_t)a->S[2] * a->S[1] * 16;
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
@@ -2185,7 +2192,7 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
       constexpr int V = 16 / (int)sizeof(Tc);
       const int qx = (a.S[0] + V - 1) / V;
       const size_t raw = (size_t)NC * a.S[1] * a.S[2] * qx * V * sizeof(Tc);
-      const size_t sm = (size_t)a.S[2] * a.PS * sizeof(float4) + kRecBytes +
+      const size_t sm = (size_t)a.S[2] * a.PS * sizeof(float4) + rec_bytes(MODE == 1) +
                         3 * kRecords * sizeof(double) + raw;
       if (sm <= 227 * 1024) {
         auto pk = track_bricks<Tc, NC, MODE>;
@@ -2218,7 +2225,8 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
     if (tuning().brick_kernel == 4 && a.tma && a.E == 0 && a.S[0] == 11 && a.S[1] == 11 &&
         a.S[2] == 11 && a.SX == 12 && a.PS == 132) {
       auto pk = interp_staged_pipe<Tc, NC, MODE>;
-      const size_t sm = (size_t)2 * ((a.S[2] * a.PS + 7) / 8 * 8) * sizeof(float4) + kRecBytes;
+      const size_t sm =
+          (size_t)2 * ((a.S[2] * a.PS + 7) / 8 * 8) * sizeof(float4) + rec_bytes(MODE == 1);
       if (sm > 48 * 1024) {
         ps_status rc = check_cuda(
             cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
@@ -2276,7 +2284,7 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
                           int32_t* status, int chunked, void* out, size_t* smem) {
   if (coef_t == PS_F64) return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
   StagedArgs a{};
-  ps_status rc = fill_staged(grid, coef_t, brick, 0, &a, smem);
+  ps_status rc = fill_staged(grid, coef_t, brick, 0, false, &a, smem);
   if (rc) return rc;
   a.coef = coef;
   a.scale = scale;
@@ -2353,7 +2361,7 @@ ps_status rk2_launch_staged(const ps_grid* grid, const int32_t brick[3], int E,
     return fail(PS_ERR_UNSUPPORTED, "staged RK2 needs F32/BF16/F16 coefficients");
   StagedArgs a{};
   size_t smem;
-  ps_status rc = fill_staged(grid, coef_t, brick, E, &a, &smem);
+  ps_status rc = fill_staged(grid, coef_t, brick, E, false, &a, &smem);
   if (rc) return rc;
   a.coef = c0;
   a.scale = s0;
@@ -2429,7 +2437,7 @@ extern "C" ps_status ps_interp(const ps_grid* grid, int ncomp, ps_dtype coef_t,
   }
   StagedArgs a{};
   size_t smem;
-  if ((rc = fill_staged(grid, coef_t, brick, 0, &a, &smem))) return rc;
+  if ((rc = fill_staged(grid, coef_t, brick, 0, grad != nullptr, &a, &smem))) return rc;
   a.coef = coef;
   a.scale = scale;
   attach_tma(&a, coef_t);
