@@ -139,10 +139,17 @@ __global__ void __launch_bounds__(1024) solve_strided(
   T* dp = dst + d_off + c * d_sc + o * d_so + x + (int64_t)s0 * d_si;
   const T thr = Thr<T>::v;
 
+  // offsets inside a chunk fit in 32 bits (LMAX * stride < 2^31 for n <= 2048)
+  const int si = (int)s_si, di = (int)d_si;
   T v[LMAX];
+  if (len == LMAX) {
 #pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) v[i] = (T)sp[(int64_t)i * s_si];
+    for (int i = 0; i < LMAX; ++i) v[i] = (T)sp[i * si];
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) v[i] = (T)sp[i * si];
+  }
 
   // causal sweep from a zero state; chunk carries by a geometric sum
   const T y = chunk_causal<T, LMAX>(v, len, z);
@@ -179,9 +186,14 @@ __global__ void __launch_bounds__(1024) solve_strided(
   }
   if (j > M) carry = carry / (T(1) - fac);
   chunk_anticausal_fix<T, LMAX>(v, len, carry, z);
+  if (len == LMAX) {
 #pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) dp[(int64_t)i * d_si] = gain * v[i];
+    for (int i = 0; i < LMAX; ++i) dp[i * di] = gain * v[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) dp[i * di] = gain * v[i];
+  }
 }
 
 __device__ __forceinline__ float pow2_at_least(float mx) {
@@ -216,9 +228,14 @@ __device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z
   len = len < 0 ? 0 : (len > L ? L : len);
   T* mine = buf + lane * (L + 1);
   T v[LMAX];
+  if (len == LMAX) {
 #pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) v[i] = mine[i];
+    for (int i = 0; i < LMAX; ++i) v[i] = mine[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) v[i] = mine[i];
+  }
 
   const T y = chunk_causal<T, LMAX>(v, len, z);
   const T a = chunk_zlen<T>(len);
@@ -267,9 +284,14 @@ __device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z
     sc = pow2_at_least(mx);
   }
   const T inv_sc = (T)(1.f / sc);  // exact: sc is a power of two
+  if (len == LMAX) {
 #pragma unroll
-  for (int i = 0; i < LMAX; ++i)
-    if (i < len) mine[i] = gain * v[i] * inv_sc;
+    for (int i = 0; i < LMAX; ++i) mine[i] = gain * v[i] * inv_sc;
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) mine[i] = gain * v[i] * inv_sc;
+  }
   __syncwarp();
   return sc;
 }
@@ -283,13 +305,14 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * (L + 1);
-  const int64_t nrows = (int64_t)ncomp * nz * ny;
-  const int64_t row = (int64_t)blockIdx.x * nwarps + warp;
+  // rows = ncomp * nz * ny <= 3 * 2048^2: 32-bit index arithmetic
+  const int nrows = ncomp * nz * ny;
+  const int row = (int)blockIdx.x * nwarps + warp;
   if (row >= nrows) return;  // whole warp; no block-level barrier below
-  const int yy = (int)(row % ny);
-  const int64_t r2 = row / ny;
-  const int zz = (int)(r2 % nz);
-  const int c = (int)(r2 / nz);
+  const int yy = row % ny;
+  const int r2 = row / ny;
+  const int zz = r2 % nz;
+  const int c = r2 / nz;
 
   const float inv_L = 1.f / (float)L;
   const T* sp = src + sv.off + c * sv.sc + zz * sv.sz + yy * sv.sy;
@@ -360,8 +383,7 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, NodeT
   __shared__ float line_scale[3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 32 * (L + 1);
-  const int64_t row = blockIdx.x;
-  const int yy = (int)(row % ny), zz = (int)(row / ny);
+  const int yy = blockIdx.x, zz = blockIdx.y;  // one (z, y) row per block
   const float inv_L = 1.f / (float)L;
   const T* sp = src + sv.off + warp * sv.sc + zz * sv.sz + yy * sv.sy;
   for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
@@ -437,6 +459,9 @@ ps_status launch_strided(const Tin* src, View sv, int64_t s_so, int64_t s_si, T*
                          View dv, int64_t d_so, int64_t d_si, int nx, int n,
                          int n_other, int ncomp, T z, T gain, cudaStream_t st) {
   StridedCfg cfg = strided_cfg<T>(n);
+  if ((s_si > 0 ? s_si : -s_si) * cfg.lmax >= ((int64_t)1 << 31) ||
+      (d_si > 0 ? d_si : -d_si) * cfg.lmax >= ((int64_t)1 << 31))
+    return fail(PS_ERR_UNSUPPORTED, "line stride too large for one chunk");
   dim3 block(cfg.XW, cfg.M);
   dim3 grid((nx + cfg.XW - 1) / cfg.XW, n_other, ncomp);
   size_t smem = 2 * sizeof(T) * cfg.XW * cfg.M;
@@ -512,8 +537,8 @@ ps_status launch_x_node4_l(const float* src, View sv, NodeT* dst, float* scale4,
         "solve_x_node4 smem attribute");
     if (rc) return rc;
   }
-  const int64_t rows = (int64_t)ny * nz;
-  kern<<<(unsigned)rows, 96, smem, st>>>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain);
+  kern<<<dim3((unsigned)ny, (unsigned)nz), 96, smem, st>>>(src, sv, dst, scale4, rx, nx, ny,
+                                                             nz, L, z, gain);
   return check_launch("solve_x_node4");
 }
 
