@@ -599,11 +599,13 @@ __device__ __forceinline__ bool tma_wait(unsigned long long* mbar, unsigned pari
   const long long t0 = clock64();
   while (true) {
     unsigned done;
+    // the suspend-time hint (ns) lets the thread sleep until the phase
+    // completes instead of polling; each try returns within the hint
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(1000000u)
         : "memory");
     if (done) return true;
     if (clock64() - t0 > (1ll << 31)) return false;
