@@ -557,17 +557,35 @@ __device__ __forceinline__ void tma_issue_halo(const CUtensorMap* map, float4* d
       "r"(smem_u32(mbar))
       : "memory");
 }
-// 16-bit node halos: the raw nodes and the rows' scales land after the
-// records (128-byte aligned), then every thread converts them to the float4
-// halo.  Offsets in bytes from the start of the dynamic shared memory.
-__host__ __device__ __forceinline__ size_t align128(size_t v) { return (v + 127) & ~size_t(127); }
-__host__ __device__ __forceinline__ size_t node16_raw_offset(int Sz, int PS, size_t rec_bytes) {
-  return align128((size_t)Sz * PS * 16 + rec_bytes);
+// 16-bit node halos: the tensor copies put the raw nodes and their rows'
+// scales into the float4 halo's own buffer, near its end (both 128-byte
+// aligned), and the block widens them in place in kNode16Slices slices of
+// nodes: each slice is read into registers, a barrier, then written as
+// float4.  The float4 writes of a slice reach raw bytes of its own or of
+// earlier slices only, and the scales only in the last slice (checked below
+// for the compile-time 8^3 halo).  Offsets in bytes from the halo's start.
+constexpr int kNode16Slices = 4;
+__host__ __device__ constexpr int align_down128(int v) { return v & ~127; }
+__host__ __device__ constexpr int node16_scale_offset(int Sz, int PS, int Sy) {
+  return align_down128(Sz * PS * 16 - Sz * Sy * 16);
 }
-__host__ __device__ __forceinline__ size_t node16_scale_offset(int Sz, int PS, int Sy, int SX,
-                                                               size_t rec_bytes) {
-  return align128(node16_raw_offset(Sz, PS, rec_bytes) + (size_t)Sz * Sy * SX * 8);
+__host__ __device__ constexpr int node16_raw_offset(int Sz, int PS, int Sy, int SX) {
+  return align_down128(node16_scale_offset(Sz, PS, Sy) - Sz * Sy * SX * 8);
 }
+// slice s (s < kNode16Slices - 1) writes float4 nodes below (s + 1) * per;
+// the raw nodes of slice s + 1 start at raw + 8 (s + 1) per
+__host__ __device__ constexpr bool node16_in_place_ok(int Sz, int PS, int Sy, int SX) {
+  const int npts = Sz * Sy * SX, per = (npts + kNode16Slices - 1) / kNode16Slices;
+  bool ok = Sz * PS >= npts && node16_raw_offset(Sz, PS, Sy, SX) >= 0;
+  for (int s = 0; s + 1 < kNode16Slices; ++s) {
+    const int end_write = 16 * (s + 1) * per;
+    ok = ok && end_write <= node16_raw_offset(Sz, PS, Sy, SX) + 8 * (s + 1) * per &&
+         end_write <= node16_scale_offset(Sz, PS, Sy);
+  }
+  return ok;
+}
+static_assert(node16_in_place_ok(11, 132, 11, 12), "16-bit node halo cannot widen in place");
+
 __device__ __forceinline__ void tma_issue_node16(const CUtensorMap* nodes,
                                                  const CUtensorMap* scales, void* raw,
                                                  void* sraw, unsigned long long* mbar,
@@ -1053,21 +1071,40 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       copied = false;
       if (threadIdx.x == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
     }
-    if constexpr (IsNode16<Tc>::value) {
+    // (16-bit node copies come only with the 8^3 halo of 12-node rows)
+    if constexpr (IsNode16<Tc>::value && KS == 12) {
       if (raw16 && cb == beg) {
-        // the copied 16-bit nodes and their rows' scales -> float4 halo; the
-        // copy's rows are SX nodes long, the halo's rows too (dense planes)
+        // the copied 16-bit nodes and their rows' scales -> float4 halo in
+        // the same buffer, slice by slice; the copy's rows are SX nodes long,
+        // the halo's rows too (dense planes)
         const Tc* nodes = reinterpret_cast<const Tc*>(raw16);
         const float4* scl = reinterpret_cast<const float4*>(
-            raw16 + (node16_scale_offset(hg.Sz, hg.PS, hg.Sy, hg.SX, rec_bytes(GRAD)) -
-                     node16_raw_offset(hg.Sz, hg.PS, rec_bytes(GRAD))));
+            raw16 + (node16_scale_offset(hg.Sz, hg.PS, hg.Sy) -
+                     node16_raw_offset(hg.Sz, hg.PS, hg.Sy, hg.SX)));
         float4* h = const_cast<float4*>(halo);
-        const int npts = hg.Sz * hg.Sy * hg.SX;
-        for (int it = threadIdx.x; it < npts; it += blockDim.x) {
-          const Tc n = nodes[it];
-          const float4 sc = scl[it / hg.SX];
-          h[it] = make_float4(node16_value(n.v[0]) * sc.x, node16_value(n.v[1]) * sc.y,
-                              node16_value(n.v[2]) * sc.z, 0.f);
+        constexpr int npts = HaloGeo<KS>::Sz * HaloGeo<KS>::Sy * HaloGeo<KS>::SX;
+        constexpr int per = (npts + kNode16Slices - 1) / kNode16Slices;
+        constexpr int kPer = (per + kThreads - 1) / kThreads;  // nodes per thread per slice
+#pragma unroll 1
+        for (int sl = 0; sl < kNode16Slices; ++sl) {
+          const int lo = sl * per, hi = min(npts, lo + per);
+          float4 v[kPer];
+#pragma unroll
+          for (int k = 0; k < kPer; ++k) {
+            const int it = lo + threadIdx.x + k * kThreads;
+            if (it < hi) {
+              const Tc n = nodes[it];
+              const float4 sc = scl[it / hg.SX];
+              v[k] = make_float4(node16_value(n.v[0]) * sc.x, node16_value(n.v[1]) * sc.y,
+                                 node16_value(n.v[2]) * sc.z, 0.f);
+            }
+          }
+          __syncthreads();
+#pragma unroll
+          for (int k = 0; k < kPer; ++k) {
+            const int it = lo + threadIdx.x + k * kThreads;
+            if (it < hi) h[it] = v[k];
+          }
         }
         __syncthreads();
       }
@@ -1511,10 +1548,9 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
       __shared__ __align__(8) unsigned long long mbar;
       using G = HaloGeo<12>;
       if constexpr (IsNode16<Tc>::value) {
-        unsigned char* base = reinterpret_cast<unsigned char*>(smem);
-        unsigned char* raw = base + node16_raw_offset(G::Sz, G::PS, rec_bytes(MODE == 1));
-        unsigned char* sraw =
-            base + node16_scale_offset(G::Sz, G::PS, G::Sy, G::SX, rec_bytes(MODE == 1));
+        unsigned char* base = reinterpret_cast<unsigned char*>(halo);
+        unsigned char* raw = base + node16_raw_offset(G::Sz, G::PS, G::Sy, G::SX);
+        unsigned char* sraw = base + node16_scale_offset(G::Sz, G::PS, G::Sy);
         if (threadIdx.x == 0)
           tma_issue_node16(&maps->tmap, &maps->tmap2, raw, sraw, &mbar, P0,
                            (unsigned)(G::Sz * G::Sy * (G::SX * 8 + 16)));
@@ -2108,13 +2144,9 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   }
   a->vec = vec ? 1 : 0;
   a->tma = 0;
-  const bool n16 = coef_t == PS_BF16X4 || coef_t == PS_F16X4;
   a->min_stage = tuning().brick_min_stage;
+  // (tensor copies of 16-bit nodes land inside the float4 halo's buffer)
   *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + rec_bytes(grad);
-  // room for a tensor copy of 16-bit nodes and their rows' scales
-  if (n16 && vec)
-    *smem = node16_scale_offset(a->S[2], a->PS, a->S[1], a->SX, rec_bytes(grad)) +
-            (size_t)a->S[2] * a->S[1] * 16;
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
 }
