@@ -1160,6 +1160,9 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
         write_axis<false>(R, i, d, c, t2, ok, sel3(P0, d), d == 0 ? hg.Sx : (d == 1 ? hg.Sy : hg.Sz));
         if (a.coef2 && ok)  // second field: its coefficients are not staged
           reinterpret_cast<signed char*>(R.lw())[4 * i + d] = (signed char)-1;
+        // the predictor's fraction waits in nbc for phase C (the same task
+        // reads it there before it writes the slot)
+        if (a.next_counts) R.nbc(d)[i] = __float_as_int(t2);
       }
     }
     __syncthreads();
@@ -1193,19 +1196,21 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
           if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, pp);
         }
         if (a.next_counts) {
-          // The new cell: the stage-1 cell plus the floor of its fraction plus
-          // the displacement in cells, in FP32.  That floor is the exact one
-          // wherever the sum lies 2^-10 or more from a cell face and
+          // The new cell: the predictor's cell plus the floor of its fraction
+          // plus the corrector's displacement dt (u2 - u1) / 2 in cells, in
+          // FP32 (x^{n+1} = x* + dt (u2 - u1) / 2).  That floor is the exact
+          // one wherever the sum lies 2^-10 or more from a cell face and
           // |x n/L| < 2^30: the FP32 and FP64 roundings on both routes stay
           // below 1e-6 cell.  Elsewhere (and for positions that are not
           // finite) the FP64 location decides.
-          const float w = tt[k] + 0.5f * a.dtih[d] * (tu1[k] + f4get(r, d));
+          const float w = __int_as_float(R.nbc(d)[i]) +
+                          0.5f * a.dtih[d] * (f4get(r, d) - tu1[k]);
           const float fl = floorf(w), fr = w - fl;
           int c;
           if (ok && fr >= 0x1p-10f && fr <= 1.f - 0x1p-10f && fabsf(fl) <= 2.f &&
               fabsf((float)tx[k]) * g.inv_hf[d] < 0x1p30f) {
             const int nd = g.n[d];
-            c = tcell[k] + (int)fl;  // in [-2, n + 1], n >= 3
+            c = R.cell(d)[i] + (int)fl;  // in [-2, n + 1], n >= 3
             c = c < 0 ? c + nd : (c >= nd ? c - nd : c);
           } else {
             float tn;
