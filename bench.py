@@ -77,7 +77,7 @@ def parse():
 # Shared-memory wavefronts (128 B) per particle of the binned Heun step: two
 # 64-point float4 gathers (16) plus the particle records, as counted by ncu
 # (l1tex__data_pipe_lsu_wavefronts_mem_shared_op_{ld,st}) for the node form.
-SMEM_WAVEFRONTS = 24.1
+SMEM_WAVEFRONTS = 24.5
 
 
 def smem_bound_ms(np_: int, sms: int = 152, clock_ghz: float = 2.07) -> float:
