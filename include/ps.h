@@ -352,14 +352,16 @@ ps_status ps_rk2_sort(const ps_grid* grid, const int32_t brick[3], int64_t np,
 /* metadata, that stream and the graph; device scratch comes from ws        */
 /* (ps_batch_workspace_size).  tune_cache: optional text file whose line    */
 /* "brick <bx> <by> <bz>" overrides `brick` (written by the autotuner).     */
-/* Coefficients: PS_F32, PS_BF16 or PS_F16; the batch uses the              */
+/* Coefficients: PS_F32, PS_BF16, PS_F16 or their node forms (PS_F32X4,    */
+/* PS_BF16X4, PS_F16X4, whose halos are tensor copies); the batch uses the  */
 /* one-CTA-per-brick kernel.                                                */
 /* ------------------------------------------------------------------------ */
 typedef struct ps_plan ps_plan;
 typedef struct {
   const void* field; /* [3][nz][ny][nx] F32; read when solve = 1 */
-  void* coef;        /* [3][nz+3][ny+3][rx] of coef_t */
-  float* scale;      /* [3][nz+3][ny+3] for BF16/F16, else NULL */
+  void* coef;        /* [3][nz+3][ny+3][rx] of coef_t (nodes: [nz+3][ny+3][rx][4]) */
+  float* scale;      /* [3][nz+3][ny+3] for BF16/F16 ([nz+3][ny+3][4] for 16-bit */
+                     /* nodes), else NULL */
 } ps_batch_field;
 
 ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int64_t* nps,

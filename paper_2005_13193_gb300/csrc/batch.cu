@@ -101,7 +101,7 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
     return fail(PS_ERR_INVALID_ARG, "need 1..4096 fields with grids and particle counts");
   if (coef_t != PS_F32 && coef_t != PS_BF16 && coef_t != PS_F16 && coef_t != PS_F32X4 &&
       coef_t != PS_BF16X4 && coef_t != PS_F16X4)
-    return fail(PS_ERR_UNSUPPORTED, "batched runs need F32, BF16 or F16 coefficients");
+    return fail(PS_ERR_UNSUPPORTED, "batched runs need F32, BF16 or F16 coefficients (planar or nodes)");
   ps_plan* p = new ps_plan();
   p->nfields = nfields;
   p->coef_t = coef_t;
