@@ -485,8 +485,10 @@ def batch_extras(ps, torch, dev):
 def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg):
     """The same step through the public API from pinned host buffers: every step
     copies the field and the positions in and reads the positions and
-    velocities out.  Inputs are double-buffered on a copy stream, so the next
-    step's upload and this step's readback overlap the compute of this step."""
+    velocities out.  Inputs are double-buffered; uploads and readbacks run on
+    two copy streams (one per direction), and a field buffer is refilled as soon
+    as the solve that read it has finished, so the copies overlap one another
+    and the compute."""
     field_h = field.cpu().pin_memory()
     pos_h = torch.from_numpy(pos_host).pin_memory()
     pos_out_h = torch.empty_like(pos_h).pin_memory()
@@ -501,20 +503,29 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg)
     offsets = torch.empty(nb[0] * nb[1] * nb[2] + 1, dtype=torch.int32, device=dev)
     status = torch.zeros(4, dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream(dev)
-    cs = torch.cuda.Stream(dev)
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
+    up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    ev_field_in, ev_pos_in = [ev(), ev()], [ev(), ev()]
+    ev_field_free, ev_done, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    for b in range(2):  # every buffer starts free
+        ev_field_free[b].record(st)
+        ev_out[b].record(st)
 
     def upload(b):
-        with torch.cuda.stream(cs):
+        with torch.cuda.stream(up):
+            up.wait_event(ev_field_free[b])   # the solve that read this field is done
             field_d[b].copy_(field_h, non_blocking=True)
+            ev_field_in[b].record(up)
+            up.wait_event(ev_out[b])          # this buffer's positions were read back
             pos_d[b].copy_(pos_h, non_blocking=True)
-        ev_in[b].record(cs)
+            ev_pos_in[b].record(up)
 
     def compute(b):
-        st.wait_event(ev_in[b])
-        ids[b].copy_(ids0)
+        st.wait_event(ev_field_in[b])
         ps.ps_spline_coeffs(field_d[b], coef, ws=ws_solve, stream=st)
+        ev_field_free[b].record(st)
+        st.wait_event(ev_pos_in[b])
+        ids[b].copy_(ids0)
         for r in range(RK_STEPS):
             # the first step sorts the uploaded positions; each step's kernel
             # counts the bins of the positions it writes for the next sort
@@ -524,23 +535,28 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg)
         ev_done[b].record(st)
 
     def readback(b):
-        cs.wait_event(ev_done[b])
-        with torch.cuda.stream(cs):
+        with torch.cuda.stream(down):
+            down.wait_event(ev_done[b])
             pos_out_h.copy_(pos_d[b], non_blocking=True)
             vel_h.copy_(vel_d[b], non_blocking=True)
+            ev_out[b].record(down)
 
     def run(steps, t0=None, t1=None):
         if t0 is not None:
-            t0.record(cs)
+            t0.record(st)
+            up.wait_stream(st)
+            down.wait_stream(st)
         upload(0)
         for k in range(steps):
             b = k & 1
-            compute(b)
             if k + 1 < steps:
-                upload(1 - b)   # the other buffer was read back in the previous step
+                upload(1 - b)
+            compute(b)
             readback(b)
         if t1 is not None:
-            t1.record(cs)
+            st.wait_stream(up)
+            st.wait_stream(down)
+            t1.record(st)
 
     run(2)
     torch.cuda.synchronize()
@@ -552,13 +568,29 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg)
     run(steps, a, b)
     torch.cuda.synchronize()
     ms = max_over_ranks(a.elapsed_time(b) / steps, pg, dev)
+    # the host link on its own, one direction at a time, best of three (context
+    # for the number above)
+    def link_gbs(dst, src):
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            dst.copy_(src, non_blocking=True)
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return src.numel() * src.element_size() / (best * 1e-3) / 1e9
+
+    h2d_gbs = link_gbs(field_d[0], field_h)
+    d2h_gbs = link_gbs(pos_out_h, pos_d[0])
     units = 2 * RK_STEPS * NP
     return {"value": whole_job_rate(units, ws_, ms), "unit": UNIT, "ms_per_step": ms,
             "steps": steps,
             "h2d_bytes_per_step": field_h.numel() * 4 + pos_h.numel() * 8,
             "d2h_bytes_per_step": pos_out_h.numel() * 8 + vel_h.numel() * 4,
-            "api": "ps_spline_coeffs + ps_rk2_step(rebin=2, then 3, ids); inputs "
-                   "double-buffered on a copy stream"}
+            "host_link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs},
+            "api": "ps_spline_coeffs + ps_rk2_step(rebin=2, then 3, ids); inputs double-buffered, "
+                   "one copy stream per direction"}
 
 
 # ------------------------------------------------------------- the oracle ----
