@@ -793,3 +793,56 @@ def test_rk2_counted_sort_at_cell_faces(kernel, brick_kernel):
     np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
     assert ps.ps_status_read(tr.status)[0] == 0
     assert m == len(eps) * 4
+
+
+@pytest.mark.parametrize("brick", [(5, 7, 3), (16, 8, 4), (1, 1, 1)])
+def test_rk2_counted_sort_other_bricks(brick):
+    # bricks whose extents are not all powers of two (the new brick is a
+    # division, not a shift) and single-cell bricks: counted sorts match full
+    # sorts bit for bit, and their bounds the oracle's
+    n = (40, 28, 24)
+    field, pos, _ = _case(n, 12000, seed=201, spread=1.2)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), ps.F32X4)
+    dt = 3e-2
+    full = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick, incremental=False)
+    inc = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick)
+    for _ in range(3):
+        start = inc.pos.cpu().numpy()
+        full.step(dt)
+        inc.step(dt)
+        _, off_ora, _ = oracle.bin_particles(n, brick, start)
+        np.testing.assert_array_equal(inc.offsets.cpu().numpy(), off_ora)
+        np.testing.assert_array_equal(full.offsets.cpu().numpy(), off_ora)
+        a, b = torch.argsort(full.ids), torch.argsort(inc.ids)
+        assert torch.equal(full.pos[:, a], inc.pos[:, b])
+    assert ps.ps_status_read(inc.status)[0] == 0
+
+
+def test_rk2_counted_sort_degenerate_sets():
+    # no particles at all, and every particle in one cell (one bin holds them
+    # all, every other bin is empty)
+    n, brick = (16, 16, 16), (8, 8, 8)
+    field, _, cref = _case(n, 10, seed=211)
+    sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
+    ws = ps.workspace(ps.ps_rk2_workspace_size(n, brick, 0), DEV)
+    offs = torch.empty(2 ** 3 + 1, dtype=torch.int32, device=DEV)
+    empty = torch.empty((3, 0), dtype=torch.float64, device=DEV)
+    for mode in (2, 3):
+        ps.ps_rk2_step(sf.coef, n, empty, 1e-3, brick=brick, rebin=mode, bin_offsets=offs, ws=ws)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(offs).item() == 0
+    ps.ps_rk2_sort(n, brick, empty, torch.empty_like(empty), offs, ws, counted=True)
+    torch.cuda.synchronize()
+    h = TWO_PI / 16
+    pos = np.full((3, 3000), 2.5 * h) + np.linspace(0, 0.4 * h, 3000)[None, :]
+    tr = ps.Tracker(sf, torch.from_numpy(pos.copy()).to(DEV), brick=brick)
+    ref = pos.copy()
+    for _ in range(3):
+        tr.step(1e-3)
+        ref, _ = oracle.rk2_step(cref, ref, 1e-3)
+    ids = tr.ids.cpu().numpy()
+    assert np.abs(tr.pos.cpu().numpy() - ref[:, ids]).max() <= 3 * 1e-3 * 1e-5 * 4 + 1e-13
+    _, off_ora, _ = oracle.bin_particles(n, brick, tr.pos.cpu().numpy())
+    tr.step(1e-3)
+    np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
+    assert ps.ps_status_read(tr.status)[0] == 0

@@ -31,3 +31,32 @@ def test_spectral_field_planes_recipe():
     # amplitude per shell falls off (k^-5/3 shell energy): compare shells 2 and 6
     e = lambda s: (np.abs(F[:, (np.sqrt(k2) >= s - 0.5) & (np.sqrt(k2) < s + 0.5)]) ** 2).sum()
     assert e(2) > e(6)
+
+
+def test_tracker_rebin_modes(monkeypatch):
+    # Tracker picks ps_rk2_step's rebin mode on the host: sort from the
+    # positions and count (2) on the first step, then sort from the counts its
+    # previous step took (3); a step with given bins (0), reset_bins() or
+    # incremental=False go back to sorting from the positions
+    import types
+
+    import paper_2005_13193_gb300 as ps
+    seen = []
+    monkeypatch.setattr(ps, "ps_rk2_step", lambda *a, **k: seen.append(k["rebin"]))
+    monkeypatch.setattr(ps, "workspace", lambda nbytes, device="cpu": torch.empty(0))
+    field = types.SimpleNamespace(n=(16, 16, 16), L=(2 * np.pi,) * 3, coef=None, scale=None)
+    pos = torch.zeros((3, 100), dtype=torch.float64)
+    tr = ps.Tracker(field, pos, brick=(8, 8, 8), keep_velocity=False)
+    for _ in range(3):
+        tr.step(1e-3)
+    tr.step(1e-3, rebin=False)
+    tr.step(1e-3)
+    tr.reset_bins()
+    tr.step(1e-3)
+    tr.step(1e-3)
+    assert seen == [2, 3, 3, 0, 2, 2, 3]
+    seen.clear()
+    full = ps.Tracker(field, pos, brick=(8, 8, 8), keep_velocity=False, incremental=False)
+    full.step(1e-3)
+    full.step(1e-3)
+    assert seen == [1, 1]
