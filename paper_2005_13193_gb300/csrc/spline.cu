@@ -209,6 +209,12 @@ __device__ __forceinline__ float pow2_at_least(float mx) {
 __device__ __forceinline__ int skew(int e, float inv_L) {
   return e + (int)(((float)e + 0.5f) * inv_L);
 }
+// The same index when every lane's chunk is full (L == LMAX, known at
+// compile time): e + e / L, a shift for the power-of-two chunk lengths.
+template <int LMAX>
+__device__ __forceinline__ int skew_l(int e, int L, float inv_L) {
+  return L == LMAX ? e + e / LMAX : skew(e, inv_L);
+}
 
 // x pass: one warp per x-line.  The line is staged in shared memory with a
 // skew (element e at e + e/L) so that lane l reads its chunk [l L, l L + L)
@@ -316,13 +322,13 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
 
   const float inv_L = 1.f / (float)L;
   const T* sp = src + sv.off + c * sv.sc + zz * sv.sz + yy * sv.sy;
-  for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
+  for (int e = lane; e < nx; e += 32) buf[skew_l<LMAX>(e, L, inv_L)] = sp[e];
   __syncwarp();
   const float sc = line_solve<T, LMAX, QUANT>(buf, nx, L, lane, z, gain);
 
   if (!padded) {
     Tout* orow = dst + dv.off + c * dv.sc + zz * dv.sz + yy * dv.sy;
-    for (int e = lane; e < nx; e += 32) orow[e] = (Tout)buf[skew(e, inv_L)];
+    for (int e = lane; e < nx; e += 32) orow[e] = (Tout)buf[skew_l<LMAX>(e, L, inv_L)];
     return;
   }
   int pys[2], pzs[2];
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(256) solve_x(const T* src, View sv, Tout* dst,
       Tout* orow = dst + dv.off + c * dv.sc + Pz * dv.sz + Py * dv.sy;
       // the row pitch dv.sy >= nx + 3; the tail of the row is zeroed
       for (int P = lane; P < dv.sy; P += 32) {
-        const int e = skew(padded_to_node(P, nx), inv_L);
+        const int e = skew_l<LMAX>(padded_to_node(P, nx), L, inv_L);
         const T val = P < nx + 3 ? buf[e] : T(0);
         if constexpr (sizeof(T) == 8)
           orow[P] = cvt_out_d<Tout>((double)val);
@@ -386,7 +392,7 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, NodeT
   const int yy = blockIdx.x, zz = blockIdx.y;  // one (z, y) row per block
   const float inv_L = 1.f / (float)L;
   const T* sp = src + sv.off + warp * sv.sc + zz * sv.sz + yy * sv.sy;
-  for (int e = lane; e < nx; e += 32) buf[skew(e, inv_L)] = sp[e];
+  for (int e = lane; e < nx; e += 32) buf[skew_l<LMAX>(e, L, inv_L)] = sp[e];
   __syncwarp();
   const float sc = line_solve<T, LMAX, Q>(buf, nx, L, lane, z, gain);
   if (lane == 0) line_scale[warp] = sc;
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, NodeT
       for (int P = threadIdx.x; P < rx; P += blockDim.x) {
         float a = 0.f, b = 0.f, c = 0.f;
         if (P < nx + 3) {
-          const int e = skew(padded_to_node(P, nx), inv_L);
+          const int e = skew_l<LMAX>(padded_to_node(P, nx), L, inv_L);
           a = (float)b0[e];
           b = (float)b1[e];
           c = (float)b2[e];
