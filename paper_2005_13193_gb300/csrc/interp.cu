@@ -485,6 +485,9 @@ struct StagedArgs {
   int32_t* next_counts;
   int32_t* next_bin;
   int bshift[3];  // log2 of the brick extent, -1 if not a power of two
+  // high word of the double 2^30 L/n per axis: |x| has a smaller high word
+  // (sign cleared) only if |x n/L| < 2^30, read without an FP64 operation
+  int xguard_hi[3];
   CUtensorMap tmap;   // node halo box (valid when tma == 1)
   CUtensorMap tmap2;  // 16-bit nodes: the box of the halo rows' scales
 };
@@ -1208,7 +1211,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
           const float fl = floorf(w), fr = w - fl;
           int c;
           if (ok && fr >= 0x1p-10f && fr <= 1.f - 0x1p-10f && fabsf(fl) <= 2.f &&
-              fabsf((float)tx[k]) * g.inv_hf[d] < 0x1p30f) {
+              (__double2hiint(tx[k]) & 0x7fffffff) < a.xguard_hi[d]) {
             const int nd = g.n[d];
             c = R.cell(d)[i] + (int)fl;  // in [-2, n + 1], n >= 3
             c = c < 0 ? c + nd : (c >= nd ? c - nd : c);
@@ -2122,6 +2125,10 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
     a->S[d] = a->b.B[d] + 3 + 2 * E;
     const int B = a->b.B[d];
     a->bshift[d] = (B & (B - 1)) ? -1 : __builtin_ctz((unsigned)B);
+    const double xg = 1073741824.0 / a->g.inv_h[d];  // 2^30 cells
+    int64_t bits;
+    memcpy(&bits, &xg, sizeof(bits));
+    a->xguard_hi[d] = (int)(bits >> 32);
   }
   if (a->S[0] > 32) return fail(PS_ERR_UNSUPPORTED, "brick x extent above 29 cells");
   a->SX = a->S[0];
