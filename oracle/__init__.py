@@ -71,6 +71,7 @@ def _load():
             lib.ora_basis.argtypes = [d, P, P]
             lib.ora_basis.restype = None
             lib.ora_locate.argtypes = [d, d, i32, P, P]
+            lib.ora_spline_coeffs_truncated.argtypes = [P, i32, i32, P, P]
             lib.ora_green.argtypes = [i64, i64, P]
             lib.ora_green.restype = None
             lib.ora_set_num_threads.argtypes = [i32]
@@ -125,6 +126,18 @@ def spline_coeffs(field, n=None) -> np.ndarray:
     n_arr = np.array([nx, ny, nz], dtype=np.int32)
     coef = np.empty((ncomp, nz + 3, ny + 3, nx + 3), dtype=np.float64)
     _check(_load().ora_spline_coeffs(_p(n_arr), ncomp, _p(field), _p(coef)))
+    return coef
+
+
+def spline_coeffs_truncated(field, K) -> np.ndarray:
+    """Sec. 2.2 Operation 1 through the periodic inverse's entries G_N(d), cut to
+    |d| <= K (2K + 1 <= N): field [ncomp][nz][ny][nx] -> padded coefficients."""
+    field = _f64(field)
+    assert field.ndim == 4
+    ncomp, nz, ny, nx = field.shape
+    n_arr = np.array([nx, ny, nz], dtype=np.int32)
+    coef = np.empty((ncomp, nz + 3, ny + 3, nx + 3), dtype=np.float64)
+    _check(_load().ora_spline_coeffs_truncated(_p(n_arr), ncomp, int(K), _p(field), _p(coef)))
     return coef
 
 

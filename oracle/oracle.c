@@ -593,6 +593,66 @@ static double green(int64_t d, int64_t n) {
 
 void ora_green(int64_t n, int64_t d, double* out) { *out = green(d, n); }
 
+/* ------------------------------------------------------------------------ */
+/* Truncated-inverse coefficients: the periodic solve of Sec. 2.2 written as */
+/* the convolution with the inverse's entries G_N (above), kept for |d| <= K */
+/* only:  c_j = sum_{d=-K..K} G_N(d) g_{(j+d) mod N}  along x, then y, then  */
+/* z, then the same N+3 padding as ora_spline_coeffs.  With 2K + 1 = N (N    */
+/* odd) every residue appears once and the result is the exact solve's.     */
+/* Requires 1 <= K and 2K + 1 <= N on every axis.                           */
+/* ------------------------------------------------------------------------ */
+static void fir_axis(const int64_t n[3], int axis, int K, const double* in, double* out) {
+  const int64_t N = n[axis];
+  const int64_t stride = axis == 0 ? 1 : (axis == 1 ? n[0] : n[0] * n[1]);
+  const int64_t vol = n[0] * n[1] * n[2];
+  double* g = (double*)malloc(sizeof(double) * (size_t)(2 * K + 1));
+  for (int d = -K; d <= K; ++d) g[d + K] = green(d, N);
+#pragma omp parallel for schedule(static)
+  for (int64_t idx = 0; idx < vol; ++idx) {
+    const int64_t j = (idx / stride) % N;
+    const int64_t base = idx - j * stride;
+    double acc = 0.0;
+    for (int d = -K; d <= K; ++d) {
+      int64_t m = (j + d) % N;
+      if (m < 0) m += N;
+      acc += g[d + K] * in[base + m * stride];
+    }
+    out[idx] = acc;
+  }
+  free(g);
+}
+
+int ora_spline_coeffs_truncated(const int32_t n[3], int ncomp, int K, const double* field,
+                                double* coef) {
+  if (ncomp < 1 || K < 1) return ORA_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 3 || 2 * K + 1 > n[d]) return ORA_ERR_ARG;
+  const int64_t nn[3] = {n[0], n[1], n[2]};
+  const int64_t nx = n[0], ny = n[1], nz = n[2];
+  const int64_t mx = nx + 3, my = ny + 3, mz = nz + 3;
+  const int64_t vol = nx * ny * nz;
+  double* a = (double*)malloc(sizeof(double) * (size_t)vol);
+  double* b = (double*)malloc(sizeof(double) * (size_t)vol);
+  if (!a || !b) { free(a); free(b); return ORA_ERR_NOMEM; }
+  for (int c = 0; c < ncomp; ++c) {
+    fir_axis(nn, 0, K, field + (int64_t)c * vol, a);
+    fir_axis(nn, 1, K, a, b);
+    fir_axis(nn, 2, K, b, a);
+    double* out = coef + (int64_t)c * mx * my * mz;
+#pragma omp parallel for schedule(static)
+    for (int64_t Pz = 0; Pz < mz; ++Pz)
+      for (int64_t Py = 0; Py < my; ++Py)
+        for (int64_t Px = 0; Px < mx; ++Px) {
+          int64_t z = pad_source(Pz, nz), y = pad_source(Py, ny),
+                  x = pad_source(Px, nx);
+          out[(Pz * my + Py) * mx + Px] = a[(z * ny + y) * nx + x];
+        }
+  }
+  free(a);
+  free(b);
+  return ORA_OK;
+}
+
 int ora_interp_windowed(const int32_t n[3], const double L[3],
                         const float* field, int64_t np, const double* pos,
                         double* vel) {

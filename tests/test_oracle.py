@@ -480,3 +480,44 @@ def test_lagrangian_accel_closed_forms():
         errs.append(max(np.abs(acc[0] - ex).max(), np.abs(acc[1:]).max()))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 6 < r1 < 11 and 6.5 < r2 < 10, errs
+
+
+def test_truncated_inverse_full_circulant_is_the_solve():
+    # with 2K + 1 = N on every axis the cut convolution keeps every entry of
+    # the periodic inverse: it must equal the Thomas + Sherman-Morrison solve
+    rng = np.random.default_rng(41)
+    f = rng.standard_normal((2, 9, 9, 9))
+    np.testing.assert_allclose(oracle.spline_coeffs_truncated(f, 4), oracle.spline_coeffs(f),
+                               rtol=0, atol=1e-13)
+    f = rng.standard_normal((1, 7, 7, 7))
+    np.testing.assert_allclose(oracle.spline_coeffs_truncated(f, 3), oracle.spline_coeffs(f),
+                               rtol=0, atol=1e-13)
+
+
+def test_truncated_inverse_error_bound_and_rate():
+    # the entries beyond |d| = K sum to at most 2 sqrt3 |r|^(K+1) / (1 - |r|)
+    # per axis; through three axes with sum |G| = 3 each the error is below
+    # 27 times that of max|g|, and it shrinks by r^2 per two more taps
+    rng = np.random.default_rng(42)
+    f = rng.standard_normal((1, 48, 40, 36))
+    exact = oracle.spline_coeffs(f)
+    r = abs(math.sqrt(3.0) - 2.0)
+    errs = []
+    for K in (4, 6, 8, 10, 12, 15):
+        e = np.abs(oracle.spline_coeffs_truncated(f, K) - exact).max()
+        tail = 2 * math.sqrt(3.0) * r ** (K + 1) / (1 - r)
+        assert e <= 27 * tail * np.abs(f).max(), (K, e)
+        errs.append(e)
+    for a, b in zip(errs[:4], errs[1:5]):
+        assert 0.03 < b / a < 0.15, errs  # r^2 = 0.072
+
+
+def test_truncated_inverse_constant_field_closed_form():
+    # a constant maps to the constant times the cube of the kept entries' sum,
+    # a geometric series: sqrt3 (1 + 2 r (1 - r^K) / (1 - r)) (N large, r^N ~ 0)
+    r = math.sqrt(3.0) - 2.0
+    c = np.full((1, 64, 64, 64), 1.7)
+    for K in (1, 3, 7, 15):
+        S = math.sqrt(3.0) * (1 + 2 * r * (1 - r ** K) / (1 - r))
+        np.testing.assert_allclose(oracle.spline_coeffs_truncated(c, K), 1.7 * S ** 3,
+                                   rtol=0, atol=1e-13)
