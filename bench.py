@@ -311,6 +311,7 @@ def run_ours(args):
         result["interp_sorted_vs_unsorted"] = interp_extras(ps, torch, dev, coef, bufs[0], n3)
         result["coef_forms"] = precision_forms(ps, torch, dev, field, coef, bufs[0], n3)
         result["batched_48_fields"] = batch_extras(ps, torch, dev)
+        result["solve_forms"] = solve_forms(ps, torch, dev, field)
     if not args.no_e2e:
         result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_,
                                     pg)
@@ -437,6 +438,25 @@ def precision_forms(ps, torch, dev, field, coef_nodes, pos_now, n3):
         del c, s, wsq
     if ps.ps_status_read(status)[0] != 0:
         raise RuntimeError("device status set in the coefficient-form runs")
+    return out
+
+
+def solve_forms(ps, torch, dev, field):
+    """The same 512^3 three-component solve, planar FP32 output: the exact
+    chunked recursions (ps_spline_coeffs) against the convolution with the
+    periodic inverse cut to |d| <= 15 (ps_spline_coeffs_truncated)."""
+    n3 = (N, N, N)
+    exact = torch.empty(ps.coef_shape(n3, 3, torch.float32), dtype=torch.float32, device=dev)
+    trunc = torch.empty_like(exact)
+    ws_e = ps.workspace(ps.ps_spline_coeffs_workspace_size(n3, 3, torch.float32), dev)
+    ws_t = ps.workspace(ps.ps_spline_truncated_workspace_size(n3, 3), dev)
+    t_exact = _event_ms(torch, lambda: ps.ps_spline_coeffs(field, exact, ws=ws_e), 5)
+    t_trunc = _event_ms(torch, lambda: ps.ps_spline_coeffs_truncated(field, trunc, K=15,
+                                                                     ws=ws_t), 5)
+    diff = (trunc - exact).abs().max().item() / exact.abs().max().item()
+    out = {"exact_ms": t_exact, "truncated_k15_ms": t_trunc,
+           "max_diff_rel_max_coef": diff}
+    del exact, trunc, ws_e, ws_t
     return out
 
 

@@ -158,6 +158,26 @@ ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype field_t,
                            void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Operation 1 through the inverse (Sec. 2.2's periodic system, solved as a */
+/* convolution): the inverse of the 1/6, 4/6, 1/6 circulant of N nodes has  */
+/* entries G_N(d) = sqrt(3) (r^|d| + r^(N-|d|)) / (1 - r^N), r = sqrt(3)-2; */
+/* keeping |d| <= K gives, along x, y and z,                                */
+/*   c_j = sum_{d=-K..K} G_N(d) g_{(j+d) mod N},                            */
+/* off the exact solve by less than 27 * 2 sqrt(3) |r|^(K+1) / (1 - |r|)    */
+/* of max|g| (K = 15: 1e-7 relative, below FP32 rounding).  Every output    */
+/* depends only on its 2K+1 neighbours per axis.                            */
+/*   field: [ncomp][nz][ny][nx] F32, ncomp 1..3;  1 <= K <= 15, 2K+1 <= n.  */
+/*   coef: the padded PS_F32 layout of ps_spline_coeffs ([ncomp][nz+3]     */
+/*         [ny+3][rx], rx = ps_coef_row_pitch(nx, PS_F32)), 16-byte aligned.*/
+/*   ws: ps_spline_truncated_workspace_size bytes, 256-byte aligned.        */
+/* ------------------------------------------------------------------------ */
+size_t ps_spline_truncated_workspace_size(const ps_grid* grid, int ncomp);
+ps_status ps_spline_coeffs_truncated(const ps_grid* grid, int ncomp,
+                                     const float* field, int K, float* coef,
+                                     void* ws, size_t ws_bytes, void* stream);
+
+
+/* ------------------------------------------------------------------------ */
 /* Bin sort (Sec. 3: each particle is handled where the coefficients of its */
 /* stencil live).  Cell a_d = floor(x_d * n_d/L_d) mod n_d (FP64, one       */
 /* rounded multiply), brick b_d = a_d / brick[d], nb_d = ceil(n_d/brick[d]),*/

@@ -245,6 +245,30 @@ def ps_bin_particles(n, brick, pos: torch.Tensor, bin_of: torch.Tensor, bin_offs
                                    _ptr(ws), ws_bytes, _ptr(status), _stream(stream)))
 
 
+def ps_spline_truncated_workspace_size(n, ncomp: int, L=DEFAULT_L) -> int:
+    g = make_grid(n, L)
+    return int(_lib().ps_spline_truncated_workspace_size(ctypes.byref(g), ncomp))
+
+
+def ps_spline_coeffs_truncated(field: torch.Tensor, coef: torch.Tensor, K: int = 15,
+                               ws: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
+    """Operation 1 (Sec. 2.2) through the periodic inverse cut to |d| <= K: field
+    [ncomp][nz][ny][nx] F32 -> padded F32 coefficients (the layout of PS_F32)."""
+    n = grid_of_field(field)
+    ncomp = field.shape[0]
+    _dev(field, "field", torch.float32)
+    _dev(coef, "coef", torch.float32)
+    if tuple(coef.shape) != coef_shape(n, ncomp, torch.float32):
+        raise ValueError(f"coef shape {tuple(coef.shape)} != {coef_shape(n, ncomp, torch.float32)}")
+    if ws is None:
+        ws = workspace(ps_spline_truncated_workspace_size(n, ncomp, L), field.device)
+    _dev(ws, "ws")
+    g = make_grid(n, L)
+    _check(_lib().ps_spline_coeffs_truncated(ctypes.byref(g), ncomp, _ptr(field), int(K),
+                                             _ptr(coef), _ptr(ws), ws.numel() * ws.element_size(),
+                                             _stream(stream)))
+
+
 def ps_interp(coef: torch.Tensor, n, pos: torch.Tensor, vel: torch.Tensor,
               scale: Optional[torch.Tensor] = None, perm: Optional[torch.Tensor] = None,
               bin_offsets: Optional[torch.Tensor] = None, brick=None,

@@ -50,6 +50,8 @@ SIGNATURES = {
     "ps_status_read": (_I, [_P, _P, _P]),
     "ps_spline_coeffs_workspace_size": (_SZ, [_GP, _I, _I]),
     "ps_spline_coeffs": (_I, [_GP, _I, _I, _P, _I, _P, _P, _P, _SZ, _P]),
+    "ps_spline_truncated_workspace_size": (_SZ, [_GP, _I]),
+    "ps_spline_coeffs_truncated": (_I, [_GP, _I, _P, _I, _P, _P, _SZ, _P]),
     "ps_bin_workspace_size": (_SZ, [_GP, _P, _I64]),
     "ps_bin_particles": (_I, [_GP, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P, _P]),
     "ps_bin_particles_noalloc": (_I, [_GP, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),

@@ -846,3 +846,51 @@ def test_rk2_counted_sort_degenerate_sets():
     tr.step(1e-3)
     np.testing.assert_array_equal(tr.offsets.cpu().numpy(), off_ora)
     assert ps.ps_status_read(tr.status)[0] == 0
+
+
+def _trunc_bar(K, field):
+    # three passes, each a sum of 2K + 1 FP32 products of values bounded by
+    # 9 max|field| (sum |G| = 3 per axis already filtered)
+    return 3 * (2 * K + 1) * 2.0 ** -24 * 9 * np.abs(field).max()
+
+
+@pytest.mark.parametrize("n,K", [((32, 32, 32), 15), ((37, 33, 40), 12), ((12, 10, 9), 4),
+                                 ((9, 9, 9), 4), ((64, 48, 40), 8), ((300, 31, 33), 15)])
+def test_truncated_solve_matches_oracle(n, K):
+    # the convolution with the periodic inverse's entries cut at |d| <= K,
+    # against the oracle's FP64 convolution; the row padding stays zero
+    field = synth.random_field(n, ncomp=3, seed=221).astype(np.float32)
+    ref = oracle.spline_coeffs_truncated(field.astype(np.float64), K)
+    f = torch.from_numpy(field).to(DEV)
+    coef = torch.full(ps.coef_shape(n, 3, torch.float32), 7.0, dtype=torch.float32, device=DEV)
+    ps.ps_spline_coeffs_truncated(f, coef, K=K)
+    got = coef.cpu().numpy()
+    assert np.abs(got[..., :n[0] + 3] - ref).max() <= _trunc_bar(K, field)
+    assert not np.any(got[..., n[0] + 3:])
+
+
+def test_truncated_solve_against_exact_solve():
+    # with K = 15 the neglected entries are below FP32 rounding: the result
+    # meets the exact solve (GPU and oracle) within the two rounding bars
+    n = (64, 48, 40)
+    field = synth.random_field(n, ncomp=3, seed=231).astype(np.float32)
+    exact = oracle.spline_coeffs(field.astype(np.float64))
+    f = torch.from_numpy(field).to(DEV)
+    coef = torch.empty(ps.coef_shape(n, 3, torch.float32), dtype=torch.float32, device=DEV)
+    ps.ps_spline_coeffs_truncated(f, coef, K=15)
+    r = abs(math.sqrt(3.0) - 2.0)
+    tail = 27 * 2 * math.sqrt(3.0) * r ** 16 / (1 - r) * np.abs(field).max()
+    got = coef.cpu().numpy()[..., :n[0] + 3]
+    assert np.abs(got - exact).max() <= _trunc_bar(15, field) + tail
+    sf = ps.SplineField.from_field(f, torch.float32)
+    gpu_exact = sf.padded().cpu().numpy()
+    assert np.abs(got - gpu_exact).max() <= _trunc_bar(15, field) + tail + coef_tol(field)
+
+
+def test_truncated_solve_rejects_bad_K():
+    f = torch.zeros((3, 16, 16, 16), dtype=torch.float32, device=DEV)
+    coef = torch.empty(ps.coef_shape((16, 16, 16), 3, torch.float32), dtype=torch.float32,
+                       device=DEV)
+    for K in (0, 8, 16):  # 2K+1 = 17 > 16 for K = 8
+        with pytest.raises(ps.PSError):
+            ps.ps_spline_coeffs_truncated(f, coef, K=K)
