@@ -10,8 +10,9 @@
 // K = 15 the neglected entries sum to 3.4e-9 per axis, below FP32 rounding.
 //
 // Passes: z, then y (one thread per x column and run of kRun outputs along
-// the axis, lanes along x), then x, which also writes the N+3 padded layout
-// of ps_spline_coeffs(PS_F32) from a node row staged in shared memory.
+// the axis, lanes along x), then x (one warp per row), which also writes the
+// N+3 padded layout of ps_spline_coeffs(PS_F32) from a node row staged in
+// shared memory.
 #include <cmath>
 
 #include "ps_internal.cuh"
@@ -70,21 +71,26 @@ __device__ __forceinline__ int pad_node(int P, int n) {
   return m;
 }
 
-// x pass and padding: one block per padded row (Py, Pz, component).  The node
-// row is staged in shared memory at index e + e / 8, so that the threads'
-// windows (kRunX apart) fall on distinct banks; each thread writes kRunX
-// consecutive padded values (zeros beyond nx + 3) as two 16-byte stores.
-__global__ void __launch_bounds__(256) fir_x_pad(const float* __restrict__ src,
-                                                 float* __restrict__ dst, int nx, int ny, int nz,
-                                                 int64_t rx, Taps t) {
-  extern __shared__ float row[];
-  const int Py = blockIdx.x, Pz = blockIdx.y, c = blockIdx.z;
+// x pass and padding: one warp per padded row (Py, Pz, component), kRowsX
+// rows per block.  The warp stages its node row in its own slice of shared
+// memory at index e + e / 8, so that the lanes' windows (kRunX apart) fall on
+// distinct banks; each lane then writes runs of kRunX consecutive padded
+// values (zeros beyond nx + 3) as two 16-byte stores, 32 runs per trip.
+constexpr int kRowsX = 4;
+__global__ void __launch_bounds__(32 * kRowsX) fir_x_pad(const float* __restrict__ src,
+                                                         float* __restrict__ dst, int nx,
+                                                         int ny, int nz, int64_t rx, Taps t) {
+  extern __shared__ float rows[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int Py = blockIdx.x * kRowsX + warp, Pz = blockIdx.y, c = blockIdx.z;
+  if (Py >= ny + 3) return;  // whole warp; no block-level barrier below
+  float* row = rows + warp * (nx + nx / 8 + 1);
   const int y = pad_node(Py, ny), z = pad_node(Pz, nz);
   const float* sp = src + (((int64_t)c * nz + z) * ny + y) * nx;
-  for (int e = threadIdx.x; e < nx; e += blockDim.x) row[e + (e >> 3)] = sp[e];
-  __syncthreads();
+  for (int e = lane; e < nx; e += 32) row[e + (e >> 3)] = sp[e];
+  __syncwarp();
   float* orow = dst + (((int64_t)c * (nz + 3) + Pz) * (ny + 3) + Py) * rx;
-  for (int P0 = threadIdx.x * kRunX; P0 < rx; P0 += blockDim.x * kRunX) {
+  for (int P0 = lane * kRunX; P0 < rx; P0 += 32 * kRunX) {
     // node of padded index P is P - 1 (mod nx): the window starts at node
     // P0 - 1 - kKMax
     int m = (P0 - 1 - kKMax) % nx;
@@ -166,8 +172,9 @@ extern "C" ps_status ps_spline_coeffs_truncated(const ps_grid* grid, int ncomp,
                 st>>>(a, b, nx, ny, (int64_t)nx, 1, (int64_t)nx * ny, 0, make_taps(ny, K));
   if ((rc = check_launch("fir_strided y"))) return rc;
   const int64_t rx = coef_pitch(nx, PS_F32);
-  const size_t smem = (size_t)(nx + nx / 8 + 1) * sizeof(float);
-  fir_x_pad<<<dim3((unsigned)(ny + 3), (unsigned)(nz + 3), (unsigned)ncomp), 256, smem, st>>>(
-      b, coef, nx, ny, nz, rx, make_taps(nx, K));
+  const size_t smem = (size_t)kRowsX * (nx + nx / 8 + 1) * sizeof(float);
+  fir_x_pad<<<dim3((unsigned)((ny + 3 + kRowsX - 1) / kRowsX), (unsigned)(nz + 3),
+                   (unsigned)ncomp),
+              32 * kRowsX, smem, st>>>(b, coef, nx, ny, nz, rx, make_taps(nx, K));
   return check_launch("fir_x_pad");
 }
