@@ -22,10 +22,13 @@
  *   never frees them and, on these calls, allocates no device memory: scratch
  *   comes from the caller through (ws, ws_bytes), sized by the matching
  *   *_workspace_size() query.  ws must be 256-byte aligned.
- * - Device-side anomalies (a non-finite or out-of-range position) never trap:
- *   they are recorded in an optional caller-owned device word
- *   `int32_t status[4]` = {code, first index low 32 bits, high 32 bits,
- *   count} and the affected outputs are NaN.  Read it with ps_status_read().
+ * - Device-side anomalies never trap: they are recorded in an optional
+ *   caller-owned device word `int32_t status[4]` = {code, first index low 32
+ *   bits, high 32 bits, count}.  A non-finite or out-of-range position gives
+ *   NaN outputs for that particle (PS_DEV_NONFINITE_POS); a brick whose halo
+ *   copy does not complete within the bounded wait (about a second) has its
+ *   particles gather from global memory instead, so its outputs stay correct
+ *   (PS_DEV_TIMEOUT).  Read it with ps_status_read().
  *
  * Layouts (x is the fastest index everywhere)
  * -------------------------------------------
@@ -113,21 +116,27 @@ const char* ps_version(void);
  * the storage layout, not of the method (the paper stores N+3 per line). */
 int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
 
-/* Launch-shape knobs (not part of the method): "brick_kernel" 0 = one CTA per
- * brick, 8 lanes per particle, phases separated by block barriers (default),
- * 1 = persistent CTAs that prefetch the next brick's halo while processing the
- * current one, 2 = one CTA per brick, one thread per particle, 3 = one CTA per
- * brick, every warp walking its own particles with no barrier after the
- * staging, 4 = persistent CTAs with two node-halo buffers, the next brick's
- * tensor copy in flight (node coefficients only; otherwise 0 runs);
- * "brick_ctas_per_sm" in [1, 8] (default 3,
- * persistent form only); "brick_min_stage" in [0, 2^20] (default 8): in the
- * one-CTA-per-brick kernel, bricks holding fewer particles skip the halo
- * staging and gather their stencils from global memory; "node_tma" 0 or 1
- * (default 1): halos of node coefficients by tensor copy; "solve_xw" 0, 8, 16
- * or 32 (0 = default 16): x extent of a block of the strided spline passes.
+/* Launch-shape knobs (not part of the method):
+ *  "brick_kernel" (for the brick-staged calls, bins given): -1 = automatic
+ *     (default; 5 for the gradient tensor and for 16-bit coefficients, 0
+ *     otherwise), 0 = one CTA per brick, 8 lanes per particle, phases
+ *     separated by block barriers, 2 = one CTA per brick, one thread per
+ *     particle, 5 = one CTA per brick, four lanes per particle, each holding
+ *     one z-row of the stencil in registers (the Heun predictor reuses it
+ *     when it stays in its cell); 16-bit node halos stay 16-bit in shared
+ *     memory.  Forms a case does not support fall back to 0.
+ *  "brick_min_stage" in [0, 2^20] (default 8): bricks holding fewer particles
+ *     skip the halo staging and gather their stencils from global memory.
+ *  "node_tma" 0 or 1 (default 1): halos of node coefficients by tensor copy.
+ *  "solve_xw" 0, 8, 16 or 32 (0 = default 16): x extent of a block of the
+ *     strided spline passes.
+ *  "wait_probe" in [0, 2^30] (default 0), a test knob: > 0 makes every
+ *     staged brick wait, after its halo copy has landed, on a barrier that
+ *     nothing completes, for that many clocks; the wait gives up, the status
+ *     word reports PS_DEV_TIMEOUT and the brick's particles read their
+ *     stencils from global memory (results unchanged).
  * Process-wide; set them before capturing work in a graph.  ps_tune_get
- * returns -1 for an unknown key. */
+ * returns -1 for an unknown key (and for "brick_kernel" = automatic). */
 ps_status ps_tune_set(const char* key, int64_t value);
 int64_t ps_tune_get(const char* key);
 

@@ -27,7 +27,7 @@ from . import BatchPlan, PSError, SplineField, Tracker, ps_tune_get, ps_tune_set
 # within 32 nodes
 CANDIDATES = ((8, 8, 8), (8, 8, 4), (8, 4, 4), (4, 4, 4), (8, 8, 16), (16, 8, 8),
               (16, 8, 4), (16, 16, 8))
-KERNELS = (0, 1, 2)
+KERNELS = (0, 2, 5)
 
 
 def _time_ms(fn, warmup: int, reps: int, stream=None) -> float:

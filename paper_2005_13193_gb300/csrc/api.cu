@@ -112,7 +112,8 @@ extern "C" const char* ps_last_error(void) { return g_err; }
 extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
   if (!key) return fail(PS_ERR_INVALID_ARG, "key is NULL");
   if (!strcmp(key, "brick_kernel")) {
-    if (value < 0 || value > 4) return fail(PS_ERR_INVALID_ARG, "brick_kernel is 0 to 4");
+    if (value != -1 && value != 0 && value != 2 && value != 5)
+      return fail(PS_ERR_INVALID_ARG, "brick_kernel is -1 (auto), 0, 2 or 5");
     tuning().brick_kernel = (int)value;
     return PS_OK;
   }
@@ -132,9 +133,9 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
     tuning().node_tma = (int)value;
     return PS_OK;
   }
-  if (!strcmp(key, "brick_ctas_per_sm")) {
-    if (value < 1 || value > 8) return fail(PS_ERR_INVALID_ARG, "brick_ctas_per_sm in [1, 8]");
-    tuning().brick_ctas_per_sm = (int)value;
+  if (!strcmp(key, "wait_probe")) {
+    if (value < 0 || value > (1 << 30)) return fail(PS_ERR_INVALID_ARG, "wait_probe in [0, 2^30]");
+    tuning().wait_probe = (int)value;
     return PS_OK;
   }
   return fail(PS_ERR_INVALID_ARG, "unknown tuning key '%s'", key);
@@ -143,10 +144,10 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
 extern "C" int64_t ps_tune_get(const char* key) {
   if (!key) return -1;
   if (!strcmp(key, "brick_kernel")) return tuning().brick_kernel;
-  if (!strcmp(key, "brick_ctas_per_sm")) return tuning().brick_ctas_per_sm;
   if (!strcmp(key, "brick_min_stage")) return tuning().brick_min_stage;
   if (!strcmp(key, "node_tma")) return tuning().node_tma;
   if (!strcmp(key, "solve_xw")) return tuning().solve_xw;
+  if (!strcmp(key, "wait_probe")) return tuning().wait_probe;
   return -1;
 }
 

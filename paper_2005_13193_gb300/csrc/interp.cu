@@ -27,51 +27,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "ps_internal.cuh"
+#include "staged.cuh"
 
 namespace ps {
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename T>
-__device__ __forceinline__ T pick4(const T b[4], int q) {
-  return q == 0 ? b[0] : (q == 1 ? b[1] : (q == 2 ? b[2] : b[3]));
-}
-template <typename T>
-__device__ __forceinline__ T sel3(const T v[3], int i) {
-  return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
-}
-
-template <int G, typename T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-  for (int d = 1; d < G; d <<= 1) v += __shfl_xor_sync(FULL, v, d);
-  return v;
-}
-
-template <typename Tc>
-__device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
-                                                              const float* scale,
-                                                              const GridArgs& g, int c,
-                                                              int Pz, int Py, int Px) {
-  if constexpr (IsNode16<Tc>::value) {
-    // component c of a 16-bit node, times its line's scale
-    const int64_t row = (int64_t)Pz * g.m[1] + Py;
-    return node16_value(coef[row * g.rx + Px].v[c]) * __ldg(scale + row * 4 + c);
-  } else if constexpr (IsNode4<Tc>::value) {
-    // component c of node (Pz, Py, Px); the node's other components share
-    // the 16-byte segment
-    const int64_t node = ((int64_t)Pz * g.m[1] + Py) * g.rx + Px;
-    return __ldg(reinterpret_cast<const float*>(coef + node) + c);
-  } else {
-    const int64_t m1 = g.m[1], m2 = g.m[2];
-    const int64_t row = ((int64_t)c * m2 + Pz) * m1 + Py;
-    typename AccOf<Tc>::type v = CoefLoad<Tc>::ld(coef + row * g.rx + Px);
-    if (IsQuant<Tc>::value) v *= __ldg(scale + row);
-    return v;
-  }
-}
 
 // The first three lanes of each group of G lanes locate one axis each; the
 // cell indices and fractions are broadcast to the whole group.  xd returns
@@ -451,409 +410,6 @@ __global__ void __launch_bounds__(256) rk2_direct(GridArgs g, const Tc* __restri
   }
 }
 
-// ------------------------------------------------------------- staged ----
-
-struct StagedArgs {
-  GridArgs g;
-  BrickArgs b;
-  int E;        // extra halo cells on each side
-  int S[3];     // staged extent per axis: B + 3 + 2E
-  int SX;       // row stride in float4 units (= S[0])
-  int PS;       // plane stride in float4 units: >= SX*S[1], = 4 (mod 8)
-  int vec;      // 1: halo rows are whole 16-byte vectors inside the array
-  int min_stage;  // bricks with fewer particles gather from global memory
-  int tma;        // 1: the node halo is one tensor copy described by tmap
-  int chunked;    // 1: bins are runs of particles (sparse field): no halo
-  const void* coef;
-  const float* scale;
-  const void* coef2;  // second-stage field of an RK2 step; NULL = same as coef
-  const float* scale2;
-  int64_t np;
-  const double* pos_in;
-  double* pos_out;
-  const int64_t* perm;
-  const int32_t* offs;
-  float* vel;
-  float* grad;
-  const int64_t* ids_in;
-  int64_t* ids_out;
-  double dt;
-  float dtih[3];  // dt * n/L per axis
-  int32_t* status;
-  // counting pass of the next step's bin sort (NULL = off): each particle's
-  // new bin at its slot in pos_out, bin counters (zeroed beforehand)
-  int32_t* next_counts;
-  int32_t* next_bin;
-  int bshift[3];  // log2 of the brick extent, -1 if not a power of two
-  // high word of the double 2^30 L/n per axis: |x| has a smaller high word
-  // (sign cleared) only if |x n/L| < 2^30, read without an FP64 operation
-  int xguard_hi[3];
-  CUtensorMap tmap;   // node halo box (valid when tma == 1)
-  CUtensorMap tmap2;  // 16-bit nodes: the box of the halo rows' scales
-};
-
-// Halo geometry (extents, row and plane strides in float4 units).  KS > 0
-// fixes at compile time the cubic halo of KS points per axis of the 8^3
-// brick (KS = 11, plane stride 124 = 4 mod 8), so that every index in the
-// staging and the gathers folds into immediates; KS = 0 reads the launch
-// arguments.
-template <int KS> struct HaloGeo {
-  int Sx, Sy, Sz, SX, PS;
-  __device__ __forceinline__ explicit HaloGeo(const StagedArgs& a)
-      : Sx(a.S[0]), Sy(a.S[1]), Sz(a.S[2]), SX(a.SX), PS(a.PS) {}
-};
-template <> struct HaloGeo<11> {
-  static constexpr int Sx = 11, Sy = 11, Sz = 11, SX = 11, PS = 124;
-  __device__ __forceinline__ explicit HaloGeo(const StagedArgs&) {}
-};
-// The same halo with 12-point rows: the layout of a tensor copy of a node
-// halo, whose plane of 12 x 11 points is 132 = 4 (mod 8) float4 long.
-template <> struct HaloGeo<12> {
-  static constexpr int Sx = 11, Sy = 11, Sz = 11, SX = 12, PS = 132;
-  __device__ __forceinline__ explicit HaloGeo(const StagedArgs&) {}
-};
-__device__ __forceinline__ bool is_cube11(const StagedArgs& a) {
-  return a.S[0] == 11 && a.S[1] == 11 && a.S[2] == 11 && a.SX == 11 && a.PS == 124;
-}
-__device__ __forceinline__ bool is_cube11_rows12(const StagedArgs& a) {
-  return a.S[0] == 11 && a.S[1] == 11 && a.S[2] == 11 && a.SX == 12 && a.PS == 132;
-}
-
-// ------------------------------------------------- tensor-copy staging ----
-// One thread arms an mbarrier with the byte count of the box and issues the
-// tensor copy of the brick's node halo; the copy completes the barrier's
-// phase, after which every thread that waited on it sees the data.
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void tma_init_barrier(unsigned long long* mbar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Arms the barrier's current phase with the box's byte count and issues the
-// copy (the barrier was initialised before).
-__device__ __forceinline__ void tma_copy_halo(const CUtensorMap* map, float4* dst,
-                                              unsigned long long* mbar, const int P0[3],
-                                              unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(0), "r"(P0[0]), "r"(P0[1]), "r"(P0[2]),
-      "r"(smem_u32(mbar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_issue_halo(const CUtensorMap* map, float4* dst,
-                                               unsigned long long* mbar, const int P0[3],
-                                               unsigned bytes) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(0), "r"(P0[0]), "r"(P0[1]), "r"(P0[2]),
-      "r"(smem_u32(mbar))
-      : "memory");
-}
-// 16-bit node halos: the tensor copies put the raw nodes and their rows'
-// scales into the float4 halo's own buffer, near its end (both 128-byte
-// aligned), and the block widens them in place in kNode16Slices slices of
-// nodes: each slice is read into registers, a barrier, then written as
-// float4.  The float4 writes of a slice reach raw bytes of its own or of
-// earlier slices only, and the scales only in the last slice (checked below
-// for the compile-time 8^3 halo).  Offsets in bytes from the halo's start.
-constexpr int kNode16Slices = 4;
-__host__ __device__ constexpr int align_down128(int v) { return v & ~127; }
-__host__ __device__ constexpr int node16_scale_offset(int Sz, int PS, int Sy) {
-  return align_down128(Sz * PS * 16 - Sz * Sy * 16);
-}
-__host__ __device__ constexpr int node16_raw_offset(int Sz, int PS, int Sy, int SX) {
-  return align_down128(node16_scale_offset(Sz, PS, Sy) - Sz * Sy * SX * 8);
-}
-// slice s (s < kNode16Slices - 1) writes float4 nodes below (s + 1) * per;
-// the raw nodes of slice s + 1 start at raw + 8 (s + 1) per
-__host__ __device__ constexpr bool node16_in_place_ok(int Sz, int PS, int Sy, int SX) {
-  const int npts = Sz * Sy * SX, per = (npts + kNode16Slices - 1) / kNode16Slices;
-  bool ok = Sz * PS >= npts && node16_raw_offset(Sz, PS, Sy, SX) >= 0;
-  for (int s = 0; s + 1 < kNode16Slices; ++s) {
-    const int end_write = 16 * (s + 1) * per;
-    ok = ok && end_write <= node16_raw_offset(Sz, PS, Sy, SX) + 8 * (s + 1) * per &&
-         end_write <= node16_scale_offset(Sz, PS, Sy);
-  }
-  return ok;
-}
-static_assert(node16_in_place_ok(11, 132, 11, 12), "16-bit node halo cannot widen in place");
-
-__device__ __forceinline__ void tma_issue_node16(const CUtensorMap* nodes,
-                                                 const CUtensorMap* scales, void* raw,
-                                                 void* sraw, unsigned long long* mbar,
-                                                 const int P0[3], unsigned bytes) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
-               "r"(bytes)
-               : "memory");
-  // node pairs are the 16-byte inner unit: x coordinate P0[0] / 2
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(raw)),
-      "l"(reinterpret_cast<unsigned long long>(nodes)), "r"(0), "r"(P0[0] >> 1), "r"(P0[1]),
-      "r"(P0[2]), "r"(smem_u32(mbar))
-      : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(sraw)),
-      "l"(reinterpret_cast<unsigned long long>(scales)), "r"(0), "r"(P0[1]), "r"(P0[2]),
-      "r"(smem_u32(mbar))
-      : "memory");
-}
-
-// Waits for the barrier's phase of the given parity, giving up after about
-// 2^31 clocks (about a second); returns whether the phase completed.
-__device__ __forceinline__ bool tma_wait(unsigned long long* mbar, unsigned parity = 0) {
-  const unsigned a = smem_u32(mbar);
-  const long long t0 = clock64();
-  while (true) {
-    unsigned done;
-    // the suspend-time hint (ns) lets the thread sleep until the phase
-    // completes instead of polling; each try returns within the hint
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(a), "r"(parity), "r"(1000000u)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
-  }
-}
-
-// Padded index (any integer) -> interior padded index of the same node.
-__device__ __forceinline__ int wrap_row(int P, int n) {
-  while (P < 1) P += n;
-  while (P > n) P -= n;
-  return P;
-}
-
-// Copy the brick halo (S[0] x S[1] x S[2] padded points) into shared memory
-// as float4 (u, v, w, 0) per point.  16 (or 32) lanes walk x within a row,
-// the block covers 16 (or 8) rows at a time; each thread loads four rows
-// before storing them so that the loads overlap.
-template <typename Tc, int NC>
-__device__ __forceinline__ void stage_halo(const StagedArgs& a, const Tc* __restrict__ coef,
-                                           const int P0[3], float4* halo, bool sync = true) {
-  const GridArgs& g = a.g;
-  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
-  const bool narrow = Sx <= 16;
-  const int tx = narrow ? (threadIdx.x & 15) : (threadIdx.x & 31);
-  const int ty = narrow ? (threadIdx.x >> 4) : (threadIdx.x >> 5);
-  const int RS = narrow ? (int)(blockDim.x >> 4) : (int)(blockDim.x >> 5);  // rows per step
-  const bool xact = tx < Sx;
-  const int Px = wrap_row(P0[0] + tx, g.n[0]);
-  const int64_t m0 = g.rx, m1 = g.m[1], m2 = g.m[2];
-  const int64_t cs = m0 * m1 * m2;
-  const int nrows = Sy * Sz;
-  int ly = ty % Sy, lz = ty / Sy;
-  for (int r = ty; r < nrows; r += 4 * RS) {
-    float v[4][NC];
-    int dst[4];
-    bool act[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      act[u] = xact && (r + u * RS) < nrows;
-      const int Py = wrap_row(P0[1] + ly, g.n[1]);
-      const int Pz = wrap_row(P0[2] + lz, g.n[2]);
-      const int64_t row = (int64_t)Pz * m1 + Py;
-      dst[u] = lz * a.PS + ly * a.SX + tx;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        float x = 0.f;
-        if (act[u]) {
-          if constexpr (IsNode16<Tc>::value) {
-            x = node16_value(coef[row * m0 + Px].v[c]) * __ldg(a.scale + row * 4 + c);
-          } else if constexpr (IsNode4<Tc>::value) {
-            x = __ldg(reinterpret_cast<const float*>(coef + row * m0 + Px) + c);
-          } else {
-            x = (float)CoefLoad<Tc>::ld(coef + c * cs + row * m0 + Px);
-            if (IsQuant<Tc>::value) x *= __ldg(a.scale + c * m2 * m1 + row);
-          }
-        }
-        v[u][c] = x;
-      }
-      ly += RS;
-      while (ly >= Sy) {
-        ly -= Sy;
-        ++lz;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (act[u])
-        halo[dst[u]] = make_float4(v[u][0], NC > 1 ? v[u][NC > 1 ? 1 : 0] : 0.f,
-                                   NC > 2 ? v[u][NC > 2 ? 2 : 0] : 0.f, 0.f);
-  }
-  if (sync) __syncthreads();
-}
-
-// Vector staging.  With E = 0 and bricks that tile the grid, the halo of
-// brick b spans padded indices [b B, b B + B + 2] on every axis, inside the
-// padded array; when B is a multiple of the vector width V (16 bytes) every
-// halo row starts on a 16-byte boundary (the row pitch is a multiple of 16
-// bytes), so each row is read with ceil(S_x / V) 16-byte loads per component
-// and transposed in registers into the float4-per-point layout.
-template <typename Tc> struct Vec16;
-template <> struct Vec16<float> {
-  static constexpr int V = 4;
-  static __device__ __forceinline__ void load(const float* p, float s, float out[4]) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    out[0] = v.x * s; out[1] = v.y * s; out[2] = v.z * s; out[3] = v.w * s;
-  }
-};
-template <typename H> struct Vec16Half {
-  static constexpr int V = 8;
-  static __device__ __forceinline__ void load(const H* p, float s, float out[8]) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-    const unsigned w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const unsigned short lo = (unsigned short)(w[i] & 0xffffu), hi = (unsigned short)(w[i] >> 16);
-      out[2 * i] = CoefLoadBits<H>::f(lo) * s;
-      out[2 * i + 1] = CoefLoadBits<H>::f(hi) * s;
-    }
-  }
-};
-template <> struct Vec16<__nv_bfloat16> : Vec16Half<__nv_bfloat16> {};
-template <> struct Vec16<__half> : Vec16Half<__half> {};
-
-template <typename Tc, int NC, int KS>
-__device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
-                                                      const Tc* __restrict__ coef,
-                                                      const int P0[3], float4* halo, bool sync);
-
-// Node coefficients: one 16-byte load and store per halo point, consecutive
-// threads along the rows.
-template <typename Tc, int KS>
-__device__ __forceinline__ void stage_nodes(const StagedArgs& a, const Tc* __restrict__ coef,
-                                            const int P0[3], float4* halo) {
-  const HaloGeo<KS> hg(a);
-  const int64_t rx = a.g.rx, m1 = a.g.m[1];
-  const Tc* b0 = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
-  const int nrow = hg.Sy * hg.Sz, npts = nrow * hg.Sx;
-  for (int it = threadIdx.x; it < npts; it += blockDim.x) {
-    const int r = it / hg.Sx, x = it - r * hg.Sx;
-    const int lz = r / hg.Sy, ly = r - lz * hg.Sy;
-    const int64_t roff = (int64_t)lz * m1 + ly;
-    if constexpr (IsNode16<Tc>::value) {
-      const Tc n = b0[roff * rx + x];
-      const float4 sc = __ldg(reinterpret_cast<const float4*>(a.scale) +
-                              ((int64_t)P0[2] * m1 + P0[1]) + roff);
-      halo[lz * hg.PS + ly * hg.SX + x] =
-          make_float4(node16_value(n.v[0]) * sc.x, node16_value(n.v[1]) * sc.y,
-                      node16_value(n.v[2]) * sc.z, 0.f);
-    } else {
-      halo[lz * hg.PS + ly * hg.SX + x] = __ldg(b0 + roff * rx + x);
-    }
-  }
-}
-
-template <typename Tc, int NC, int KS = 0>
-__device__ __forceinline__ void stage_halo_vec(const StagedArgs& a, const Tc* __restrict__ coef,
-                                               const int P0[3], float4* halo, bool sync = true) {
-  if constexpr (IsNode4<Tc>::value) {
-    stage_nodes<Tc, KS>(a, coef, P0, halo);
-    if (sync) __syncthreads();
-  } else {
-    stage_halo_vec_planar<Tc, NC, KS>(a, coef, P0, halo, sync);
-  }
-}
-
-template <typename Tc, int NC, int KS>
-__device__ __forceinline__ void stage_halo_vec_planar(const StagedArgs& a,
-                                                      const Tc* __restrict__ coef,
-                                                      const int P0[3], float4* halo, bool sync) {
-  constexpr int V = Vec16<Tc>::V;
-  constexpr int U = 8 / V;               // rows in flight per thread
-  const GridArgs& g = a.g;
-  const HaloGeo<KS> hg(a);
-  const int Sx = hg.Sx, Sy = hg.Sy, Sz = hg.Sz;
-  const int qx = (Sx + V - 1) / V;       // vectors per halo row (<= 4)
-  const int qd = threadIdx.x & 3, rs = threadIdx.x >> 2;
-  const int RS = blockDim.x >> 2;        // rows per block step
-  const int64_t rx = g.rx, m1 = g.m[1], m2 = g.m[2];
-  const int64_t cs = rx * m1 * m2;
-  const int nrows = Sy * Sz;
-  if (V == 4 && qx == 3 && (Sx & 1)) {
-    // Items in groups of 24 = 8 rows x 3 vectors, ordered so that the eight
-    // lanes of each 128-bit store phase write (rows r..r+3, vectors 0-1) or
-    // (rows r..r+7, vector 2): with an odd row stride these hit eight distinct
-    // 16-byte bank groups.
-    const Tc* b0 = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
-    const int nitems = (nrows + 7) / 8 * 24;
-    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-      const int grp = it / 24, l = it - grp * 24;
-      const int rr = l < 16 ? (l >> 1) : l - 16;
-      const int q = l < 16 ? (l & 1) : 2;
-      const int r = grp * 8 + rr;
-      if (r >= nrows) continue;
-      const int lz = r / Sy, ly = r - lz * Sy;
-      const int64_t roff = ((int64_t)lz * m1 + ly) * rx + q * 4;
-      float v[NC][4];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        float sc = 1.f;
-        if (IsQuant<Tc>::value)
-          sc = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
-        Vec16<Tc>::load(b0 + c * cs + roff, sc, v[c]);
-      }
-      const int h0 = lz * hg.PS + ly * hg.SX + q * 4;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (q * 4 + i < Sx)
-          halo[h0 + i] = make_float4(v[0][i], NC > 1 ? v[NC > 1 ? 1 : 0][i] : 0.f,
-                                     NC > 2 ? v[NC > 2 ? 2 : 0][i] : 0.f, 0.f);
-    }
-    if (sync) __syncthreads();
-    return;
-  }
-  const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0] + qd * V;
-  for (int r0 = rs; r0 < nrows; r0 += U * RS) {
-    float v[U][NC][V];
-    int h0[U];
-    bool act[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = r0 + u * RS;
-      act[u] = qd < qx && r < nrows;
-      const int lz = r / Sy, ly = r - lz * Sy;
-      h0[u] = lz * hg.PS + ly * hg.SX + qd * V;
-      const int64_t roff = ((int64_t)lz * m1 + ly) * rx;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        if (act[u]) {
-          float s = 1.f;
-          if (IsQuant<Tc>::value)
-            s = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
-          Vec16<Tc>::load(base + c * cs + roff, s, v[u][c]);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (act[u])
-#pragma unroll
-        for (int i = 0; i < V; ++i)
-          if (qd * V + i < Sx)
-            halo[h0[u] + i] = make_float4(v[u][0][i], NC > 1 ? v[u][NC > 1 ? 1 : 0][i] : 0.f,
-                                          NC > 2 ? v[u][NC > 2 ? 2 : 0][i] : 0.f, 0.f);
-  }
-  if (sync) __syncthreads();
-}
-
 // Particle records in shared memory, one entry per particle of the current
 // round (kRecords), stored field-major so that neither the per-axis writers
 // nor the 8-lane readers conflict on banks:
@@ -930,14 +486,14 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
                                         const Tc* __restrict__ coef,
                                         const float* __restrict__ scale, int q, int kh,
                                         float out[NC], float dx[NC], float dy[NC],
-                                        float dz[NC]) {
+                                        float dz[NC], bool staged_ok = true) {
   const float bxq = reinterpret_cast<const float*>(R.b(0))[4 * i + q];
   const float4 by = R.b(1)[i];
   const float2 bzp = reinterpret_cast<const float2*>(R.b(2))[2 * i + kh];
   const float bz[2] = {bzp.x, bzp.y};
   const int w = R.lw()[i];
   const bool ok = (__vcmpeq4(w, 0xfefefefe) & 0x00ffffff) == 0;
-  const bool inh = (w & 0x00808080) == 0;
+  const bool inh = staged_ok && (w & 0x00808080) == 0;
   float4 dby = make_float4(0.f, 0.f, 0.f, 0.f);
   float dbz[2] = {0.f, 0.f};
   if (GRAD) {
@@ -1005,10 +561,6 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
   return ok;
 }
 
-template <typename Tc, int NC>
-__device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsigned char* raw,
-                                            double* pbuf);
-
 // Particles [beg, end) of one brick whose halo is in shared memory, in rounds
 // of kRecords:
 //   A  one thread per (particle, axis): locate (exact FP64 index arithmetic),
@@ -1017,17 +569,14 @@ __device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsign
 //   A' (Heun) one thread per (particle, axis): predictor cell in FP32;
 //   B' second gather (u2);
 //   C  one thread per (particle, axis): FP64 position update and stores.
-// pbuf: optional shared copy of the first round's positions ([3][kRecords]).
-// raw_next: if set, the copies of brick next_bin are issued as soon as phase
-// A has consumed pbuf.
 template <typename Tc, int NC, int MODE, int KS = 0>
 __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int end,
                                               const int P0[3], const float4* halo,
-                                              const Recs& R, double* pbuf,
-                                              unsigned char* raw_next, int next_bin,
+                                              const Recs& R,
                                               unsigned long long* mbar = nullptr,
                                               const unsigned char* raw16 = nullptr,
-                                              unsigned parity = 0) {
+                                              unsigned parity = 0,
+                                              unsigned long long* probe = nullptr) {
   constexpr bool GRAD = MODE == 1;
   bool copied = true;  // the halo's tensor copy completed (or there is none)
   const GridArgs& g = a.g;
@@ -1059,20 +608,22 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       if (td[k] >= 0) {
         const int i = ti[k], d = td[k];
         tp[k] = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
-        tx[k] = (pbuf && cb == beg) ? pbuf[d * kRecords + i] : a.pos_in[d * np + tp[k]];
+        tx[k] = a.pos_in[d * np + tp[k]];
         const bool ok = locate(tx[k], g.inv_h[d], g.n[d], tcell[k], tt[k]);
         write_axis<GRAD>(R, i, d, tcell[k], tt[k], ok, sel3(P0, d),
                          d == 0 ? hg.Sx : (d == 1 ? hg.Sy : hg.Sz));
       }
     }
     __syncthreads();
-    if constexpr (!IsNode4<Tc>::value)
-      if (raw_next && cb == beg) issue_brick<Tc, NC>(a, next_bin, raw_next, pbuf);
     // the barrier above also ordered the mbarrier's initialisation before
-    // these waits; a copy that never completes is reported, not waited for
-    if (mbar && cb == beg && !tma_wait(mbar, parity)) {
-      copied = false;
-      if (threadIdx.x == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
+    // these waits; a copy that does not complete in time is reported and the
+    // brick's particles read global memory (one decision for the whole
+    // block: the 16-bit widening below is shared)
+    if (mbar && cb == beg) {
+      bool done = tma_wait(mbar, parity);
+      if (done && probe) done = tma_wait(probe, 0, a.wait_probe);
+      copied = __syncthreads_and(done);
+      if (!copied && threadIdx.x == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
     }
     // (16-bit node copies come only with the 8^3 halo of 12-node rows)
     if constexpr (IsNode16<Tc>::value && KS == 12) {
@@ -1119,7 +670,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
       const bool oki = gather8<Tc, NC, GRAD>(halo, hg.PS, hg.SX, R, vi ? i : b4, g, coef, a.scale,
-                                             q, kh, u, dx, dy, dz);
+                                             q, kh, u, dx, dy, dz, copied);
       if (!vi) continue;
       if constexpr (MODE <= 1) {
         const int64_t pi = a.perm ? a.perm[cb + i] : (int64_t)(cb + i);
@@ -1177,7 +728,7 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const bool vi = i < m;
       float u[NC], dx[NC], dy[NC], dz[NC];
       const bool oki = gather8<Tc, NC, false>(halo, hg.PS, hg.SX, R, vi ? i : b4, g, cf2, sc2, q,
-                                              kh, u, dx, dy, dz);
+                                              kh, u, dx, dy, dz, copied);
       if (vi && sub == 0) R.u()[i] = make_float4(u[0], u[1], u[2], __int_as_float(oki ? 1 : 0));
     }
     __syncthreads();
@@ -1242,291 +793,6 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
   if (!copied) tma_wait(mbar, parity);
 }
 
-// ------------------------------------------------ warp-autonomous form ----
-// After the brick's halo is staged, every warp walks its own particles, four
-// at a time (8 lanes each), with no further block-level barrier: lanes 0-2 of
-// a group locate the particle along x, y, z (exact FP64 index arithmetic) and
-// broadcast (cell, t) to the group by shuffles; every lane then evaluates
-// only the basis values its share of the stencil needs, gathers, and the
-// group's butterfly leaves the sum in all 8 lanes, so the Heun predictor is
-// located redundantly by each lane in FP32 and the second gather follows at
-// once; lanes 0-2 write the FP64 update of their axis.
-
-// Lane-constant selector of one B-spline basis function b_i (Sec. 2.2,
-// Operation 2), evaluated in cancellation-free forms: b_0 = s^3/6,
-// b_1 = (3t^3 - 6t^2 + 4)/6, b_2(t) = b_1(1 - t), b_3 = t^3/6 (s = 1 - t).
-struct BasisPick {
-  bool flip, outer;
-};
-__device__ __forceinline__ BasisPick basis_pick(int i) {
-  return BasisPick{i == 0 || i == 2, i == 0 || i == 3};
-}
-__device__ __forceinline__ float basis_one(BasisPick k, float t) {
-  const float u = k.flip ? 1.f - t : t;
-  const float u2 = u * u;
-  return (k.outer ? u2 * u : fmaf(u2, fmaf(3.f, u, -6.f), 4.f)) * (1.f / 6.f);
-}
-__device__ __forceinline__ float dbasis_one(BasisPick k, float t) {
-  const float u = k.flip ? 1.f - t : t;
-  const float v = (k.outer ? u * u : u * fmaf(3.f, u, -4.f)) * 0.5f;
-  return k.flip ? -v : v;
-}
-
-// Stencil of one particle by its group of 8 lanes: lane (q, kh) covers
-// column a_x + q and z rows kh, kh + 2.  `inh`: the stencil lies in the
-// staged halo (local start l*); otherwise the rows are read from global
-// memory.  All lanes of the group return the sums.
-template <typename Tc, int NC, bool GRAD>
-__device__ __forceinline__ void gather_group(const float4* __restrict__ halo, int PS, int SX,
-                                             bool inh, const int l[3], const int cell[3],
-                                             const float t[3], const GridArgs& g,
-                                             const Tc* __restrict__ coef,
-                                             const float* __restrict__ scale, int q, int kh,
-                                             BasisPick kx, BasisPick kz0, BasisPick kz1,
-                                             float out[NC], float dx[NC], float dy[NC],
-                                             float dz[NC]) {
-  const float bxq = basis_one(kx, t[0]);
-  float by[4];
-  bspline<float>(t[1], by);
-  const float bz[2] = {basis_one(kz0, t[2]), basis_one(kz1, t[2])};
-  float dbxq = 0.f, dby[4] = {0.f, 0.f, 0.f, 0.f}, dbz[2] = {0.f, 0.f};
-  if (GRAD) {
-    dbxq = dbasis_one(kx, t[0]);
-    dbspline<float>(t[1], dby);
-    dbz[0] = dbasis_one(kz0, t[2]);
-    dbz[1] = dbasis_one(kz1, t[2]);
-  }
-  float acc[NC], accy[NC], accz[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = accy[c] = accz[c] = 0.f;
-  if (inh) {
-    const float4* hp = halo + (l[2] + kh) * PS + l[1] * SX + l[0] + q;
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 v = hp[2 * kk * PS + j * SX];
-        const float vv[3] = {v.x, v.y, v.z};
-        const float w = by[j] * bz[kk];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
-        if (GRAD) {
-          const float wy = dby[j] * bz[kk], wz = by[j] * dbz[kk];
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            accy[c] = fmaf(wy, vv[c], accy[c]);
-            accz[c] = fmaf(wz, vv[c], accz[c]);
-          }
-        }
-      }
-    }
-  } else {
-    const int ax = max(cell[0], 0), ay = max(cell[1], 0), az = max(cell[2], 0);
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float w = by[j] * bz[kk];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const float v = load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j, ax + q);
-          acc[c] = fmaf(w, v, acc[c]);
-          if (GRAD) {
-            accy[c] = fmaf(dby[j] * bz[kk], v, accy[c]);
-            accz[c] = fmaf(by[j] * dbz[kk], v, accz[c]);
-          }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
-  if (GRAD) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      dx[c] = group_sum<8>(dbxq * acc[c]) * g.inv_hf[0];
-      dy[c] = group_sum<8>(bxq * accy[c]) * g.inv_hf[1];
-      dz[c] = group_sum<8>(bxq * accz[c]) * g.inv_hf[2];
-    }
-  }
-}
-
-// Stencil start relative to the halo origin, and whether it lies inside.
-template <int KS>
-__device__ __forceinline__ bool in_halo(const HaloGeo<KS>& hg, const int P0[3],
-                                        const int cell[3], int l[3]) {
-  const int S[3] = {hg.Sx, hg.Sy, hg.Sz};
-  bool in = true;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    l[d] = cell[d] - P0[d];
-    in = in && (unsigned)l[d] <= (unsigned)(S[d] - 4);
-  }
-  return in;
-}
-
-// Particles [beg, end) of one brick.  `staged`: the halo stores were issued
-// by this block and are published by the barrier below (taken by every
-// thread); otherwise all stencils come from global memory.
-template <typename Tc, int NC, int MODE, int KS>
-__device__ __forceinline__ void brick_warps(const StagedArgs& a, int beg, int end,
-                                            const int P0[3], const float4* halo, bool staged) {
-  constexpr bool GRAD = MODE == 1;
-  const HaloGeo<KS> hg(a);
-  static_assert(MODE != 2 || NC == 3, "the Heun step advances three components");
-  const GridArgs& g = a.g;
-  const Tc* coef = static_cast<const Tc*>(a.coef);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int q = lane & 3, kh = (lane >> 2) & 1, sub = lane & 7, gb = lane & ~7;
-  const BasisPick kx = basis_pick(q), kz0 = basis_pick(kh), kz1 = basis_pick(kh + 2);
-  const int64_t np = a.np;
-  const int m = end - beg;
-  const float nanf_ = __int_as_float(0x7fc00000);
-  const int ax = sub < 3 ? sub : 0;  // the axis this lane locates
-
-  // stage-1 location of this warp's first particles, before the barrier that
-  // publishes the staged halo; later iterations load the next particles'
-  // positions before working on the current ones
-  const int step = nwarps * 4;
-  int b4 = warp * 4;
-  double x = 0.0, xn = 0.0;
-  int64_t p = 0, pn = 0;
-  int cl = 0;
-  float tl = 0.f;
-  auto load_mine = [&](int base, int64_t& pp, double& xx) {
-    const int i = base + (lane >> 3);
-    const int ii = i < m ? i : base;
-    pp = a.perm ? a.perm[beg + ii] : (int64_t)(beg + ii);
-    if (sub < 3) xx = a.pos_in[ax * np + pp];
-  };
-  auto locate_mine = [&]() {
-    cl = 0;
-    tl = 0.f;
-    if (sub < 3 && !locate(x, g.inv_h[ax], g.n[ax], cl, tl)) cl = -1;
-  };
-  if (b4 < m) {
-    load_mine(b4, p, x);
-    locate_mine();
-  }
-  if (staged) __syncthreads();
-  for (; b4 < m; b4 += step) {
-    const bool more = b4 + step < m;
-    if (more) load_mine(b4 + step, pn, xn);
-    const bool vi = b4 + (lane >> 3) < m;
-    int cell[3];
-    float t[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      cell[d] = __shfl_sync(FULL, cl, gb + d);
-      t[d] = __shfl_sync(FULL, tl, gb + d);
-    }
-    const bool ok = (cell[0] | cell[1] | cell[2]) >= 0;
-    int l[3];
-    const bool inh = staged && ok && in_halo(hg, P0, cell, l);
-    float u[NC], dx[NC], dy[NC], dz[NC];
-    gather_group<Tc, NC, GRAD>(halo, hg.PS, hg.SX, inh, l, cell, t, g, coef, a.scale, q, kh, kx,
-                               kz0, kz1, u, dx, dy, dz);
-    if constexpr (MODE <= 1) {
-      if (vi) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-          if (sub == c) a.vel[(int64_t)c * np + p] = ok ? u[c] : nanf_;
-        if (GRAD && a.grad) {
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            if (sub == 3) a.grad[((int64_t)c * 3 + 0) * np + p] = ok ? dx[c] : nanf_;
-            if (sub == 4) a.grad[((int64_t)c * 3 + 1) * np + p] = ok ? dy[c] : nanf_;
-            if (sub == 5) a.grad[((int64_t)c * 3 + 2) * np + p] = ok ? dz[c] : nanf_;
-          }
-        }
-        if (sub == 7 && !ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
-      }
-    } else {
-      // Heun predictor x* = x + dt u1, located in FP32 relative to the
-      // stage-1 cell by every lane of the group
-      int c2[3];
-      float t2[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float tt = t[d] + (ok ? u[d] * a.dtih[d] : 0.f);
-        float fl = floorf(tt);
-        if (!(fabsf(fl) < 1.0e9f)) fl = 0.f;
-        t2[d] = fminf(fmaxf(tt - fl, 0.f), 1.f);
-        int c = cell[d] + (int)fl;
-        if (c < 0 || c >= g.n[d]) {
-          c %= g.n[d];
-          if (c < 0) c += g.n[d];
-        }
-        c2[d] = ok ? c : -1;
-      }
-      // a second field's coefficients are not staged
-      const bool inh2 = staged && ok && !a.coef2 && in_halo(hg, P0, c2, l);
-      const Tc* cf2 = a.coef2 ? static_cast<const Tc*>(a.coef2) : coef;
-      const float* sc2 = a.coef2 ? a.scale2 : a.scale;
-      float u2[NC];
-      gather_group<Tc, NC, false>(halo, hg.PS, hg.SX, inh2, l, c2, t2, g, cf2, sc2, q, kh, kx, kz0,
-                                  kz1, u2, dx, dy, dz);
-      const float u1d = sel3(u, ax), u2d = sel3(u2, ax);
-      const double xnew = ok ? fma(a.dt * 0.5, (double)(u1d + u2d), x)
-                             : __longlong_as_double(0x7ff8000000000000ll);
-      if (vi && sub < 3) {
-        a.pos_out[ax * np + p] = xnew;
-        if (a.vel) a.vel[ax * np + p] = ok ? u1d : nanf_;
-        if (sub == 0) {
-          if (a.ids_out) a.ids_out[p] = a.ids_in[p];
-          if (!ok) flag_status(a.status, PS_DEV_NONFINITE_POS, p);
-        }
-      }
-      if (a.next_counts) {
-        // the next step's counting: lane sub < 3 of a group holds axis sub
-        const int bc = vi && sub < 3 ? brick_coord(g, a.b, xnew, ax) : 0;
-        const int key = bin_of_coords(a.b, __shfl_sync(FULL, bc, gb),
-                                      __shfl_sync(FULL, bc, gb + 1),
-                                      __shfl_sync(FULL, bc, gb + 2));
-        count_into_bin(a.next_counts, a.next_bin, a.status, vi && sub == 0, p, key);
-      }
-    }
-    if (more) {
-      p = pn;
-      x = xn;
-      locate_mine();
-    }
-  }
-}
-
-// One brick: stage its halo (unless it holds fewer than min_stage
-// particles), then process its particles warp by warp.
-template <typename Tc, int NC, int MODE, int KS>
-__device__ __forceinline__ void brick_body_g(const StagedArgs& a, int bin, float4* smem) {
-  const int beg = a.offs[bin], end = a.offs[bin + 1];
-  if (beg >= end) return;
-  const int nbx = a.b.nb[0], nby = a.b.nb[1];
-  const int bzi = bin / (nbx * nby);
-  const int rem = bin - bzi * nbx * nby;
-  const int byi = rem / nbx, bxi = rem - byi * nbx;
-  const int P0[3] = {bxi * a.b.B[0] - a.E, byi * a.b.B[1] - a.E, bzi * a.b.B[2] - a.E};
-  const Tc* coef = static_cast<const Tc*>(a.coef);
-  float4* halo = smem;
-  // a few particles: staging the whole halo would move more bytes than
-  // their stencils
-  const bool staged = end - beg >= a.min_stage;
-  if (staged) {
-    if (a.vec)
-      stage_halo_vec<Tc, NC, KS>(a, coef, P0, halo, false);
-    else
-      stage_halo<Tc, NC>(a, coef, P0, halo, false);
-  }
-  brick_warps<Tc, NC, MODE, KS>(a, beg, end, P0, halo, staged);
-}
-
-template <typename Tc, int NC, int MODE>
-__device__ __forceinline__ void brick_body(const StagedArgs& a, int bin, float4* smem) {
-  if (is_cube11(a))
-    brick_body_g<Tc, NC, MODE, 11>(a, bin, smem);
-  else
-    brick_body_g<Tc, NC, MODE, 0>(a, bin, smem);
-}
-
 // Phased form of one brick: stage the halo (unless the brick holds fewer than
 // min_stage particles, whose stencils are then read from global memory), then
 // the location / gather / update phases of process_brick.
@@ -1546,15 +812,18 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
   if (end - beg < a.min_stage || a.chunked) {
     // an origin far from every cell sends every stencil to global memory
     const int far[3] = {-(1 << 29), -(1 << 29), -(1 << 29)};
-    process_brick<Tc, NC, MODE>(a, beg, end, far, halo, R, nullptr, nullptr, 0);
+    process_brick<Tc, NC, MODE>(a, beg, end, far, halo, R);
     return;
   }
   if constexpr (TMA && IsNode4<Tc>::value) {
     // `maps` (with the tensor maps) is the kernel argument block or lies in
     // global memory; the destinations must be 128-byte aligned
     if (a.tma && maps && is_cube11_rows12(a) && (smem_u32(halo) & 127) == 0) {
-      __shared__ __align__(8) unsigned long long mbar;
+      __shared__ __align__(8) unsigned long long mbar, probe_bar;
       using G = HaloGeo<12>;
+      // test knob: a barrier that nothing completes, waited on after the copy
+      unsigned long long* probe = a.wait_probe > 0 ? &probe_bar : nullptr;
+      if (probe && threadIdx.x == 0) tma_init_barrier(probe);
       if constexpr (IsNode16<Tc>::value) {
         unsigned char* base = reinterpret_cast<unsigned char*>(halo);
         unsigned char* raw = base + node16_raw_offset(G::Sz, G::PS, G::Sy, G::SX);
@@ -1562,13 +831,14 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
         if (threadIdx.x == 0)
           tma_issue_node16(&maps->tmap, &maps->tmap2, raw, sraw, &mbar, P0,
                            (unsigned)(G::Sz * G::Sy * (G::SX * 8 + 16)));
-        process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar,
-                                        raw);
+        process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, &mbar,
+                                        raw, 0, probe);
       } else {
         if (threadIdx.x == 0)
           tma_issue_halo(&maps->tmap, halo, &mbar, P0,
                          (unsigned)(sizeof(float4) * G::PS * G::Sz));
-        process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0, &mbar);
+        process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, &mbar,
+                                        nullptr, 0, probe);
       }
       return;
     }
@@ -1577,19 +847,19 @@ __device__ __forceinline__ void brick_phased(const StagedArgs& a, int bin, float
   // the barrier that follows it also publishes the staged halo
   if (a.vec && is_cube11(a)) {
     stage_halo_vec<Tc, NC, 11>(a, coef, P0, halo, false);
-    process_brick<Tc, NC, MODE, 11>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
+    process_brick<Tc, NC, MODE, 11>(a, beg, end, P0, halo, R);
     return;
   }
   if (a.vec && is_cube11_rows12(a)) {
     stage_halo_vec<Tc, NC, 12>(a, coef, P0, halo, false);
-    process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
+    process_brick<Tc, NC, MODE, 12>(a, beg, end, P0, halo, R);
     return;
   }
   if (a.vec)
     stage_halo_vec<Tc, NC>(a, coef, P0, halo, false);
   else
     stage_halo<Tc, NC>(a, coef, P0, halo, false);
-  process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, nullptr, nullptr, 0);
+  process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R);
 }
 
 // MODE 0: vel; 1: vel + grad; 2: fused Heun step.  One CTA per brick.  The
@@ -1600,76 +870,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == 2 ? 6 : 7)
     interp_staged(const __grid_constant__ StagedArgs a) {
   extern __shared__ __align__(128) float4 smem_a128[];
   brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128, &a);
-}
-
-// The warp-autonomous form ("brick_kernel" 3): no particle records, no block
-// barrier after the staging.
-template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(kThreads, sizeof(Tc) == 2 ? 6 : 7) interp_staged_warp(StagedArgs a) {
-  extern __shared__ float4 smem[];
-  brick_body<Tc, NC, MODE>(a, blockIdx.x, smem);
-}
-
-__device__ __forceinline__ int next_busy(const StagedArgs& a, int bin);
-__device__ __forceinline__ void brick_origin(const StagedArgs& a, int bin, int P0[3]);
-
-// Persistent pipelined form for node coefficients ("brick_kernel" 4): each
-// block walks bricks blockIdx.x, + gridDim.x, ...; while it processes one,
-// the tensor copy of its next non-empty brick's halo fills the other of two
-// halo buffers, each with its own mbarrier whose phase parity alternates.
-template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(kThreads, 6) interp_staged_pipe(const __grid_constant__ StagedArgs a) {
-  using G = HaloGeo<12>;
-  constexpr int HS = G::Sz * G::PS;        // float4 per halo
-  constexpr int HSP = (HS + 7) / 8 * 8;    // buffers 128-byte aligned
-  constexpr unsigned kBytes = (unsigned)(sizeof(float4) * HS);
-  extern __shared__ __align__(128) float4 smem_p[];
-  __shared__ __align__(8) unsigned long long mbar[2];
-  if constexpr (IsNode4<Tc>::value && !IsNode16<Tc>::value) {
-    float4* H[2] = {smem_p, smem_p + HSP};
-    const Recs R = carve_recs<MODE == 1>(smem_p + 2 * HSP);
-    const int nb = (int)a.b.nbins;
-    int bin = next_busy(a, blockIdx.x);
-    if (bin >= nb) return;
-    if (smem_u32(smem_p) & 127) {
-      // a tensor copy needs 128-byte aligned destinations: plain loads instead
-      for (; bin < nb; bin = next_busy(a, bin + gridDim.x)) {
-        int P0[3];
-        brick_origin(a, bin, P0);
-        stage_halo_vec<Tc, NC, 12>(a, static_cast<const Tc*>(a.coef), P0, H[0], false);
-        process_brick<Tc, NC, MODE, 12>(a, a.offs[bin], a.offs[bin + 1], P0, H[0], R, nullptr,
-                                        nullptr, 0);
-      }
-      return;
-    }
-    if (threadIdx.x == 0) {
-      tma_init_barrier(&mbar[0]);
-      tma_init_barrier(&mbar[1]);
-      int P0[3];
-      brick_origin(a, bin, P0);
-      tma_copy_halo(&a.tmap, H[0], &mbar[0], P0, kBytes);
-    }
-    __syncthreads();  // the barriers' initialisation before any wait
-    unsigned parity[2] = {0u, 0u};
-    int c = 0;
-    while (bin < nb) {
-      const int next = next_busy(a, bin + gridDim.x);
-      // the other buffer's last reader was the previous brick, which ended with
-      // a block barrier
-      if (threadIdx.x == 0 && next < nb) {
-        int Pn[3];
-        brick_origin(a, next, Pn);
-        tma_copy_halo(&a.tmap, H[c ^ 1], &mbar[c ^ 1], Pn, kBytes);
-      }
-      int P0[3];
-      brick_origin(a, bin, P0);
-      process_brick<Tc, NC, MODE, 12>(a, a.offs[bin], a.offs[bin + 1], P0, H[c], R, nullptr,
-                                      nullptr, 0, &mbar[c], nullptr, parity[c]);
-      parity[c] ^= 1u;
-      c ^= 1;
-      bin = next;
-    }
-  }
 }
 
 // Many fields in one launch: block b handles global brick b; the field is the
@@ -1920,166 +1120,6 @@ __global__ void __launch_bounds__(64) interp_thread(StagedArgs a) {
   }
 }
 
-// ------------------------------------------------------ persistent form ----
-// Each CTA walks bricks b = blockIdx.x, blockIdx.x + gridDim.x, ...  While it
-// processes the particles of one brick, the halo rows of its next non-empty
-// brick (16-byte cp.async copies into a raw buffer) and that brick's first
-// kRecords positions are already in flight; at the top of the next iteration
-// the raw rows are transposed into the float4-per-point halo.  Needs the
-// vector staging conditions (a.vec).
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void brick_origin(const StagedArgs& a, int bin, int P0[3]) {
-  const int nbx = a.b.nb[0], nby = a.b.nb[1];
-  const int bzi = bin / (nbx * nby);
-  const int rem = bin - bzi * nbx * nby;
-  const int byi = rem / nbx, bxi = rem - byi * nbx;
-  P0[0] = bxi * a.b.B[0];
-  P0[1] = byi * a.b.B[1];
-  P0[2] = bzi * a.b.B[2];
-}
-
-// Next brick (in this CTA's sequence) holding particles, or nbins.
-__device__ __forceinline__ int next_busy(const StagedArgs& a, int bin) {
-  const int nb = (int)a.b.nbins;
-  while (bin < nb && a.offs[bin] >= a.offs[bin + 1]) bin += gridDim.x;
-  return bin < nb ? bin : nb;
-}
-
-// Raw row buffer: [NC][rows][qx * V] elements of Tc, rows 16-byte aligned.
-template <typename Tc, int NC>
-__device__ __forceinline__ void issue_brick(const StagedArgs& a, int bin, unsigned char* raw,
-                                            double* pbuf) {
-  constexpr int V = Vec16<Tc>::V;
-  const GridArgs& g = a.g;
-  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
-  const int qx = (Sx + V - 1) / V;
-  const int nrows = Sy * Sz;
-  int P0[3];
-  brick_origin(a, bin, P0);
-  const int64_t rx = g.rx, m1 = g.m[1], m2 = g.m[2];
-  const int64_t cs = rx * m1 * m2;
-  const Tc* coef = static_cast<const Tc*>(a.coef);
-  const Tc* base = coef + ((int64_t)P0[2] * m1 + P0[1]) * rx + P0[0];
-  Tc* rawt = reinterpret_cast<Tc*>(raw);
-  // thread -> (vector q of a row, row slot); rows advance by blockDim/4
-  const int q = threadIdx.x & 3, RS = blockDim.x >> 2;
-  if (q < qx) {
-    int ly = (threadIdx.x >> 2) % Sy, lz = (threadIdx.x >> 2) / Sy;
-    const int dly = RS % Sy, dlz = RS / Sy;
-    for (int r = threadIdx.x >> 2; r < nrows; r += RS) {
-      const Tc* src = base + ((int64_t)lz * m1 + ly) * rx + q * V;
-      Tc* dst = rawt + (int64_t)r * (qx * V) + q * V;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) cp_async16(dst + (int64_t)c * nrows * qx * V, src + c * cs);
-      ly += dly;
-      lz += dlz;
-      if (ly >= Sy) {
-        ly -= Sy;
-        ++lz;
-      }
-    }
-  }
-  const int beg = a.offs[bin], end = a.offs[bin + 1];
-  const int m = min(kRecords, end - beg);
-  if (!a.perm && threadIdx.x < m)
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      cp_async8(pbuf + d * kRecords + threadIdx.x, a.pos_in + d * a.np + beg + threadIdx.x);
-  cp_async_commit();
-}
-
-// Raw rows -> float4 (u, v, w, 0) per halo point (with the x-line scale of
-// quantised coefficients).
-template <typename Tc, int NC>
-__device__ __forceinline__ void transpose_brick(const StagedArgs& a, const int P0[3],
-                                                const unsigned char* raw, float4* halo) {
-  constexpr int V = Vec16<Tc>::V;
-  const GridArgs& g = a.g;
-  const int Sx = a.S[0], Sy = a.S[1], Sz = a.S[2];
-  const int qx = (Sx + V - 1) / V;
-  const int nrows = Sy * Sz;
-  const Tc* rawt = reinterpret_cast<const Tc*>(raw);
-  const int64_t m1 = g.m[1], m2 = g.m[2];
-  const int q = threadIdx.x & 3, RS = blockDim.x >> 2;
-  if (q >= qx) return;
-  int ly = (threadIdx.x >> 2) % Sy, lz = (threadIdx.x >> 2) / Sy;
-  const int dly = RS % Sy, dlz = RS / Sy;
-  for (int r = threadIdx.x >> 2; r < nrows; r += RS, ly += dly, lz += dlz) {
-    if (ly >= Sy) {
-      ly -= Sy;
-      ++lz;
-    }
-    float v[NC][V];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float s = 1.f;
-      if (IsQuant<Tc>::value)
-        s = __ldg(a.scale + ((int64_t)c * m2 + P0[2] + lz) * m1 + P0[1] + ly);
-      const Tc* src = rawt + (int64_t)(c * nrows + r) * (qx * V) + q * V;
-      if constexpr (std::is_same<Tc, float>::value) {
-        const float4 w = *reinterpret_cast<const float4*>(src);
-        v[c][0] = w.x; v[c][1] = w.y; v[c][2] = w.z; v[c][3] = w.w;
-      } else {
-        const uint4 w = *reinterpret_cast<const uint4*>(src);
-        const unsigned ww[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          v[c][2 * i] = CoefLoadBits<Tc>::f((unsigned short)(ww[i] & 0xffffu)) * s;
-          v[c][2 * i + 1] = CoefLoadBits<Tc>::f((unsigned short)(ww[i] >> 16)) * s;
-        }
-      }
-    }
-    const int h0 = lz * a.PS + ly * a.SX + q * V;
-#pragma unroll
-    for (int i = 0; i < V; ++i)
-      if (q * V + i < Sx)
-        halo[h0 + i] = make_float4(v[0][i], NC > 1 ? v[NC > 1 ? 1 : 0][i] : 0.f,
-                                   NC > 2 ? v[NC > 2 ? 2 : 0][i] : 0.f, 0.f);
-  }
-}
-
-template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(256, 3) track_bricks(StagedArgs a) {
-  extern __shared__ float4 smem[];
-  float4* halo = smem;
-  const Recs R = carve_recs<MODE == 1>(halo + a.S[2] * a.PS);
-  double* pbuf = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(halo + a.S[2] * a.PS) +
-                                           rec_bytes(MODE == 1));
-  unsigned char* raw = reinterpret_cast<unsigned char*>(pbuf + 3 * kRecords);
-  int bin = next_busy(a, blockIdx.x);
-  const int nb = (int)a.b.nbins;
-  if (bin >= nb) return;
-  issue_brick<Tc, NC>(a, bin, raw, pbuf);
-  while (bin < nb) {
-    cp_async_wait_all();
-    __syncthreads();
-    int P0[3];
-    brick_origin(a, bin, P0);
-    transpose_brick<Tc, NC>(a, P0, raw, halo);
-    __syncthreads();
-    const int beg = a.offs[bin], end = a.offs[bin + 1];
-    const int nxt = next_busy(a, bin + gridDim.x);
-    process_brick<Tc, NC, MODE>(a, beg, end, P0, halo, R, a.perm ? nullptr : pbuf,
-                                nxt < nb ? raw : nullptr, nxt);
-    bin = nxt;
-  }
-}
-
 // ------------------------------------------------------------------ host ----
 
 template <typename F>
@@ -2157,11 +1197,14 @@ ps_status fill_staged(const ps_grid* grid, ps_dtype coef_t, const int32_t brick[
   a->vec = vec ? 1 : 0;
   a->tma = 0;
   a->min_stage = tuning().brick_min_stage;
+  a->wait_probe = tuning().wait_probe;
   // (tensor copies of 16-bit nodes land inside the float4 halo's buffer)
   *smem = (size_t)a->S[2] * a->PS * sizeof(float4) + rec_bytes(grad);
   if (*smem > 227 * 1024) return fail(PS_ERR_UNSUPPORTED, "brick halo exceeds shared memory");
   return PS_OK;
 }
+
+}  // namespace
 
 // Tensor map of the node halo box (4 floats x SX nodes x S[1] rows x S[2]
 // planes) over the PS_F32X4 array; the driver's encoder is looked up once.
@@ -2217,6 +1260,8 @@ bool encode_node_halo_map(StagedArgs* a, ps_dtype coef_t) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+namespace {
+
 // Use a tensor copy for the halo when the coefficients are nodes, the halo
 // rows fit the copy layout and the array is 16-byte aligned.
 void attach_tma(StagedArgs* a, ps_dtype coef_t) {
@@ -2231,31 +1276,30 @@ void attach_tma(StagedArgs* a, ps_dtype coef_t) {
   a->tma = encode_node_halo_map(a, coef_t) ? 1 : 0;
 }
 
+template <typename Tc> struct DtypeOf { static constexpr int v = -1; };
+template <> struct DtypeOf<float> { static constexpr int v = PS_F32; };
+template <> struct DtypeOf<float4> { static constexpr int v = PS_F32X4; };
+template <> struct DtypeOf<__nv_bfloat16> { static constexpr int v = PS_BF16; };
+template <> struct DtypeOf<__half> { static constexpr int v = PS_F16; };
+template <> struct DtypeOf<bf16x4> { static constexpr int v = PS_BF16X4; };
+template <> struct DtypeOf<f16x4> { static constexpr int v = PS_F16X4; };
+
 template <typename Tc, int NC, int MODE>
 ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
-  if constexpr (sizeof(Tc) == 4 || sizeof(Tc) == 2) {
-    if (a.vec && tuning().brick_kernel == 1) {
-      constexpr int V = 16 / (int)sizeof(Tc);
-      const int qx = (a.S[0] + V - 1) / V;
-      const size_t raw = (size_t)NC * a.S[1] * a.S[2] * qx * V * sizeof(Tc);
-      const size_t sm = (size_t)a.S[2] * a.PS * sizeof(float4) + rec_bytes(MODE == 1) +
-                        3 * kRecords * sizeof(double) + raw;
-      if (sm <= 227 * 1024) {
-        auto pk = track_bricks<Tc, NC, MODE>;
-        if (sm > 48 * 1024) {
-          ps_status rc = check_cuda(
-              cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-              "persistent smem attribute");
-          if (rc) return rc;
-        }
-        const int64_t grid = std::min<int64_t>(a.b.nbins,
-                                               (int64_t)sm_count() * tuning().brick_ctas_per_sm);
-        pk<<<(unsigned)grid, kThreads, sm, st>>>(a);
-        return check_launch("track_bricks");
-      }
+  // brick_kernel -1 (default): the measured-faster form per case, the quad
+  // kernel for the gradient tensor and for 16-bit coefficients (planar ones
+  // too, so that both storages of the same values give the same bits), the
+  // phased kernel otherwise
+  int k = tuning().brick_kernel;
+  if (k < 0) k = (MODE == 1 || IsQuant<Tc>::value) ? 5 : 0;
+  if constexpr (NC == 3 && DtypeOf<Tc>::v >= 0) {
+    if (k == 5) {
+      bool done = false;
+      ps_status rc = launch_quad(a, (ps_dtype)DtypeOf<Tc>::v, MODE, st, &done);
+      if (rc || done) return rc;
     }
   }
-  if (tuning().brick_kernel == 2) {
+  if (k == 2) {
     auto tk = interp_thread<Tc, NC, MODE>;
     const size_t hs = (size_t)a.S[2] * a.PS * sizeof(float4);
     if (hs > 48 * 1024) {
@@ -2266,35 +1310,6 @@ ps_status launch_staged(const StagedArgs& a, size_t smem, cudaStream_t st) {
     }
     tk<<<(unsigned)a.b.nbins, 64, hs, st>>>(a);
     return check_launch("interp_thread");
-  }
-  if constexpr (IsNode4<Tc>::value && !IsNode16<Tc>::value) {
-    if (tuning().brick_kernel == 4 && a.tma && a.E == 0 && a.S[0] == 11 && a.S[1] == 11 &&
-        a.S[2] == 11 && a.SX == 12 && a.PS == 132) {
-      auto pk = interp_staged_pipe<Tc, NC, MODE>;
-      const size_t sm =
-          (size_t)2 * ((a.S[2] * a.PS + 7) / 8 * 8) * sizeof(float4) + rec_bytes(MODE == 1);
-      if (sm > 48 * 1024) {
-        ps_status rc = check_cuda(
-            cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-            "pipelined smem attribute");
-        if (rc) return rc;
-      }
-      const int64_t grid = std::min<int64_t>(a.b.nbins, (int64_t)sm_count() * 4);
-      pk<<<(unsigned)grid, kThreads, sm, st>>>(a);
-      return check_launch("interp_staged_pipe");
-    }
-  }
-  if (tuning().brick_kernel == 3) {
-    auto wk = interp_staged_warp<Tc, NC, MODE>;
-    const size_t hs = (size_t)a.S[2] * a.PS * sizeof(float4);
-    if (hs > 48 * 1024) {
-      ps_status rc = check_cuda(
-          cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs),
-          "warp-form smem attribute");
-      if (rc) return rc;
-    }
-    wk<<<(unsigned)a.b.nbins, kThreads, hs, st>>>(a);
-    return check_launch("interp_staged_warp");
   }
   auto kern = interp_staged<Tc, NC, MODE>;
   if (smem > 48 * 1024) {

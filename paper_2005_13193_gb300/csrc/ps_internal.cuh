@@ -71,11 +71,11 @@ ps_status make_brick_args(const ps_grid* g, const int32_t brick[3], BrickArgs* o
 
 // Launch-shape choices an autotuner may change (ps_tune_set).
 struct Tuning {
-  int brick_kernel = 0;       // 0: one CTA per brick; 1: persistent, pipelined
-  int brick_ctas_per_sm = 3;  // resident CTAs per SM of the persistent form
+  int brick_kernel = -1;      // -1 auto, 0 phased, 2 thread per particle, 5 quad
   int brick_min_stage = 8;    // per-brick kernel: fewer particles skip the halo
   int node_tma = 1;           // PS_F32X4 halos by tensor copy
   int solve_xw = 0;           // x extent of a strided-pass block (0: default)
+  int wait_probe = 0;         // test knob: clocks of a wait that cannot complete
 };
 Tuning& tuning();
 int sm_count();
