@@ -288,6 +288,11 @@ def run_ours(args):
                    "coef_storage": "f32x4 nodes (u, v, w, 0)",
                    "positions": "f64", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{ws_} (independent problems)"},
+        # the unit is one interpolation; a Heun step interpolates each particle
+        # twice, so particle steps per second are half the value
+        "rates": {"interpolations_per_s": value, "particle_rk2_steps_per_s": value / 2,
+                  "unit_note": "value counts interpolations of (u, v, w); each Heun RK2 "
+                               "step interpolates every particle twice"},
         "gpu_launches": LAUNCHES_PER_STEP * K,
         "clocks": clk,
         "roofline": {"bound": "hbm", "kernel": DOMINANT, "achieved": achieved, "peak": peak,
@@ -314,6 +319,7 @@ def run_ours(args):
         result["coef_forms"] = precision_forms(ps, torch, dev, field, coef, bufs[0], n3)
         result["batched_48_fields"] = batch_extras(ps, torch, dev)
         result["solve_forms"] = solve_forms(ps, torch, dev, field)
+        result["precision_1536"] = precision_extras(ps, torch, dev)
     if not args.no_e2e:
         result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_,
                                     pg)
@@ -459,6 +465,84 @@ def solve_forms(ps, torch, dev, field):
     out = {"exact_ms": t_exact, "truncated_k15_ms": t_trunc,
            "max_diff_rel_max_coef": diff}
     del exact, trunc, ws_e, ws_t
+    return out
+
+
+PREC_N = 1536
+PREC_NP = 300_000_000
+# single-interpolation floors at the measured HBM peak (positions 24 B in,
+# velocities 12 B out per particle, the coefficients once at 12 B (FP32) or
+# 6 B (16-bit) per node); the prec rows of the roofline table
+PREC_FLOOR = {"f32x4": 3.7e10, "bf16x4": 6.2e10, "f16x4": 6.2e10}
+
+
+def precision_extras(ps, torch, dev):
+    """The 1536^3 workload: FP32 field (k^-5/3, 1 <= |k| <= 512), 300,000,000
+    uniform particles; per coefficient storage (FP32, BF16 and FP16 nodes):
+    the solve, one binned interpolation of every particle and one binned Heun
+    step, device-timed with CUDA events.  Skipped below 200 GB of free
+    device memory."""
+    from paper_2005_13193_gb300 import synth
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 200e9:
+        return {"skipped": f"needs 200 GB of free device memory, {free / 1e9:.0f} GB free"}
+    n3 = (PREC_N,) * 3
+    peak, _ = measured_peaks()
+    field = synth.spectral_field_planes(PREC_N, 512, seed=1002, device=dev)
+    pos = torch.from_numpy(synth.uniform_particles(PREC_NP, seed=2002)).to(dev)
+    bins, pos_b = ps.bin_particles(n3, BRICK, pos, want_sorted=True, want_perm=False)
+    offs = bins.offsets
+    del bins, pos
+    vel = torch.empty((3, PREC_NP), dtype=torch.float32, device=dev)
+    work = torch.empty_like(pos_b)
+    status = torch.zeros(4, dtype=torch.int32, device=dev)
+    out = {"grid": PREC_N, "particles": PREC_NP, "brick": list(BRICK)}
+    for name, dt_, cb in (("f32x4", ps.F32X4, 12), ("bf16x4", ps.BF16X4, 6),
+                          ("f16x4", ps.F16X4, 6)):
+        c = torch.empty(ps.coef_shape(n3, 3, dt_), dtype=ps._storage_dtype(dt_), device=dev)
+        shp = ps.scale_shape(n3, 3, dt_)
+        sc = torch.empty(shp, dtype=torch.float32, device=dev) if shp is not None else None
+        wsq = ps.workspace(ps.ps_spline_coeffs_workspace_size(n3, 3, dt_), dev)
+        t_solve = _event_ms(torch, lambda: ps.ps_spline_coeffs(field, c, scale=sc, ws=wsq), 3,
+                            warmup=1)
+        del wsq
+        t_int = _event_ms(torch, lambda: ps.ps_interp(c, n3, pos_b, vel, scale=sc,
+                                                      bin_offsets=offs, brick=BRICK,
+                                                      status=status), 3, warmup=1)
+        evs = []
+
+        def rk():
+            work.copy_(pos_b)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ps.ps_rk2_step(c, n3, work, DT, scale_n=sc, vel_out=vel, brick=BRICK, rebin=False,
+                           bin_offsets=offs, status=status)
+            b.record()
+            evs.append((a, b))
+        rk()
+        evs.clear()
+        for _ in range(3):
+            rk()
+        torch.cuda.synchronize()
+        t_rk = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        coef_alg = cb * (PREC_N + 3) ** 3  # cb: bytes of the three components of a node
+        solve_min = 3 * 4 * PREC_N ** 3 + coef_alg
+        interp_alg = PREC_NP * 36 + coef_alg
+        rk_alg = PREC_NP * 60 + coef_alg
+        out[name] = {
+            "solve_ms": t_solve, "solve_gbs_min_bytes": solve_min / (t_solve * 1e-3) / 1e9,
+            "solve_frac_of_peak": solve_min / (t_solve * 1e-3) / 1e9 / peak,
+            "interp_ms": t_int, "interp_particles_per_s": PREC_NP / (t_int * 1e-3),
+            "interp_frac_of_peak": interp_alg / (t_int * 1e-3) / 1e9 / peak,
+            "interp_vs_floor": PREC_NP / (t_int * 1e-3) / PREC_FLOOR[name],
+            "rk2_kernel_ms": t_rk, "rk2_interpolations_per_s": 2 * PREC_NP / (t_rk * 1e-3),
+            "rk2_frac_of_peak": rk_alg / (t_rk * 1e-3) / 1e9 / peak,
+            "coef_bytes": c.numel() * c.element_size()}
+        del c, sc
+        torch.cuda.empty_cache()
+    out["status"] = [int(v) for v in ps.ps_status_read(status)]
+    del field, pos_b, offs, vel, work
+    torch.cuda.empty_cache()
     return out
 
 
@@ -617,12 +701,15 @@ def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg)
 
 # ------------------------------------------------------------- the oracle ----
 
-CPU_SAMPLE = 65536
+CPU_SAMPLE = 65536      # particles of the all-core sample
+CPU_SAMPLE_1T = 8192    # particles of the single-thread sample
+SOLVE_1T_N = 256        # grid of the single-thread solve
 
 
 def oracle_step(oracle, field64, pos_sample):
-    """One bounded sample of the workload on the host: the full 512^3 solve and
-    10 RK2 steps of a particle subsample.  Returns (t_solve, t_rk2)."""
+    """One bounded sample of the workload on the host: the full 512^3 FP64
+    solve, then 10 RK2 steps of a particle subsample on those coefficients.
+    Returns (t_solve, t_rk2) in seconds, both measured."""
     t = time.perf_counter()
     coef = oracle.spline_coeffs(field64)
     t_solve = time.perf_counter() - t
@@ -634,27 +721,75 @@ def oracle_step(oracle, field64, pos_sample):
     return t_solve, t_rk
 
 
-def extrapolated_rate(t_solve, t_rk):
-    t_full = t_solve + t_rk * (NP / CPU_SAMPLE)
+def full_step_rate(t_solve, t_rk, n_sample):
+    """Interpolations per second of the full step (solve + 10 RK2 steps of NP
+    particles) from its measured parts: the solve timed in full, the particle
+    steps timed on n_sample particles and scaled by NP / n_sample (each
+    particle's work does not depend on how many there are)."""
+    t_full = t_solve + t_rk * (NP / n_sample)
     return 2 * RK_STEPS * NP / t_full
 
 
+def _timed(fn):
+    t = time.perf_counter()
+    out = fn()
+    return out, time.perf_counter() - t
+
+
+def _rk2_sample(oracle, coef, pos_host, n_sample):
+    p = pos_host[:, :n_sample].copy()
+    t = time.perf_counter()
+    for _ in range(RK_STEPS):
+        p, _ = oracle.rk2_step(coef, p, DT)
+    return time.perf_counter() - t
+
+
 def cpu_baseline(field_np, pos_host):
+    """The oracle timed on the host: all cores and one thread, the solve
+    (GB/s of algorithmic bytes: FP64 field in, FP64 padded coefficients out)
+    and the RK2 particle steps (interpolations/s) measured separately; value
+    = the full step's rate built from the all-core parts."""
     import numpy as np
+    import torch
 
     import oracle
+    from paper_2005_13193_gb300 import synth
     cores = os.cpu_count() or 1
-    oracle.set_num_threads(cores)
     field64 = field_np.astype(np.float64)
-    t_solve, t_rk = oracle_step(oracle, field64, pos_host[:, :CPU_SAMPLE])
-    return {"value": extrapolated_rate(t_solve, t_rk), "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"full 512^3 FP64 solve ({t_solve:.1f} s) + 10 RK2 steps of "
-                      f"{CPU_SAMPLE} particles ({t_rk:.2f} s), particle part scaled to "
-                      f"{NP} particles"}
+    sbytes = lambda n: 3 * 8 * (n ** 3 + (n + 3) ** 3)  # noqa: E731
+    oracle.set_num_threads(cores)
+    coef, t_solve = _timed(lambda: oracle.spline_coeffs(field64))
+    t_rk = _rk2_sample(oracle, coef, pos_host, CPU_SAMPLE)
+    allc = {"threads": oracle.num_threads(), "solve_grid": N, "solve_s": t_solve,
+            "solve_gbs": sbytes(N) / t_solve / 1e9, "rk2_sample_particles": CPU_SAMPLE,
+            "rk2_sample_s": t_rk, "interp_per_s": 2 * RK_STEPS * CPU_SAMPLE / t_rk}
+    # one thread: the solve of a 256^3 field of the same recipe (the 512^3 one
+    # would take most of a minute), the particle steps on the 512^3 coefficients
+    f1 = synth.spectral_field(SOLVE_1T_N, SOLVE_1T_N // 3, seed=FIELD_SEED, device="cpu",
+                              dtype=torch.float64).numpy()
+    oracle.set_num_threads(1)
+    _, t1_solve = _timed(lambda: oracle.spline_coeffs(f1))
+    t1_rk = _rk2_sample(oracle, coef, pos_host, CPU_SAMPLE_1T)
+    one = {"threads": oracle.num_threads(), "solve_grid": SOLVE_1T_N, "solve_s": t1_solve,
+           "solve_gbs": sbytes(SOLVE_1T_N) / t1_solve / 1e9,
+           "rk2_sample_particles": CPU_SAMPLE_1T, "rk2_sample_s": t1_rk,
+           "interp_per_s": 2 * RK_STEPS * CPU_SAMPLE_1T / t1_rk}
+    oracle.set_num_threads(cores)
+    return {"value": full_step_rate(t_solve, t_rk, CPU_SAMPLE), "unit": UNIT,
+            "cores": allc["threads"], "kind": "oracle", "extrapolated": True,
+            "sample": (f"all cores: full 512^3 FP64 solve ({t_solve:.2f} s) + 10 RK2 steps of "
+                       f"{CPU_SAMPLE} particles ({t_rk:.2f} s), both measured; value = the full "
+                       f"step's rate with the particle part scaled to {NP} particles"),
+            "full_step_s_extrapolated": t_solve + t_rk * NP / CPU_SAMPLE,
+            "all_cores": allc, "single_thread": one}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores.  Each step is one
+    measured bounded sample (the full 512^3 solve + 10 RK2 steps of
+    CPU_SAMPLE particles); ms_per_step is that sample's measured time, value
+    the full step's rate built from its measured parts (extrapolated: the
+    particle steps scaled to NP)."""
     import numpy as np
     import torch
 
@@ -673,27 +808,36 @@ def run_reference(args):
     oracle.set_num_threads(cores)
     for _ in range(args.warmup):
         oracle_step(oracle, field64, pos)
-    rates, solves, rks = [], [], []
+    solves, rks, walls = [], [], []
     t0 = time.perf_counter()
     for _ in range(args.steps):
+        t = time.perf_counter()
         ts, tr = oracle_step(oracle, field64, pos)
+        walls.append(time.perf_counter() - t)
         solves.append(ts)
         rks.append(tr)
-        rates.append(extrapolated_rate(ts, tr))
     wall = time.perf_counter() - t0
-    ms = 1e3 * (statistics.mean(solves) + statistics.mean(rks) * NP / CPU_SAMPLE)
-    value = 2 * RK_STEPS * NP / (ms * 1e-3)
-    sample = (f"full 512^3 FP64 solve + 10 RK2 steps of {CPU_SAMPLE} particles per step, "
-              f"particle part scaled to {NP}")
+    t_solve, t_rk = statistics.mean(solves), statistics.mean(rks)
+    value = full_step_rate(t_solve, t_rk, CPU_SAMPLE)
+    sample_ms = 1e3 * statistics.mean(walls)
+    sample = (f"full 512^3 FP64 solve ({t_solve:.2f} s) + 10 RK2 steps of {CPU_SAMPLE} "
+              f"particles ({t_rk:.3f} s) per step, both measured; value = the full step's "
+              f"rate with the particle part scaled to {NP} particles")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sample_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded spectral field, uniform particles)",
         "config": {"workload": WORKLOAD, "grid": N, "particles": NP, "rk2_steps": RK_STEPS,
                    "dt": DT, "brick": list(BRICK)},
+        "extrapolated": True,
+        "measured": {"solve_s": t_solve, "rk2_sample_s": t_rk, "sample_particles": CPU_SAMPLE,
+                     "sample_step_ms": sample_ms,
+                     "sample_interp_per_s": 2 * RK_STEPS * CPU_SAMPLE / t_rk,
+                     "solve_gbs": 3 * 8 * (N ** 3 + (N + 3) ** 3) / t_solve / 1e9,
+                     "full_step_s_extrapolated": t_solve + t_rk * NP / CPU_SAMPLE},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample, "extrapolated": True},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }))

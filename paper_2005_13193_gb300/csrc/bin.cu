@@ -339,14 +339,10 @@ __global__ void bin_count_batch_kernel(const BinField* __restrict__ tab, int nfi
   }
 }
 
+// Grid of a grid-stride kernel: enough blocks for the work, at most a full
+// occupancy of the current device (its own SM count, read per call).
 int persistent_blocks(int64_t work, int threads) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 132;
-  }
+  const int sms = sm_count();
   int64_t need = (work + threads - 1) / threads;
   int64_t cap = (int64_t)sms * (2048 / threads);
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);

@@ -357,13 +357,19 @@ def test_rk2_time_dependent_field_uses_both():
 
 # -------------------------------------------------------------- windowed ----
 
-def test_windowed_matches_full_oracle():
-    n = 64
-    field = synth.random_field(n, ncomp=3, seed=61).astype(np.float32)
-    pos = synth.uniform_particles(40, seed=62)
+@pytest.mark.parametrize("n", [64, 128])
+def test_windowed_matches_full_oracle(n):
+    # the windowed evaluation (the periodic inverse cut to |d| <= 24 per axis,
+    # a 52^3 window per particle) against the full solve, at two grid sizes,
+    # with particles on and next to the periodic boundary besides random ones
+    field = synth.random_field(n, ncomp=3, seed=61 + n).astype(np.float32)
+    edge = np.array([[0.0, 2 * np.pi - 1e-12, np.pi, 1e-12],
+                     [2 * np.pi - 1e-9, 0.0, 1e-9, np.pi],
+                     [np.pi, 1e-12, 2 * np.pi - 1e-12, 0.0]])
+    pos = np.concatenate([synth.uniform_particles(40, seed=62 + n), edge], axis=1)
     full = oracle.interp(oracle.spline_coeffs(field.astype(np.float64)), pos)
     win = oracle.interp_windowed(field, pos)
-    np.testing.assert_allclose(win, full, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(win, full, rtol=0, atol=1e-12 * np.abs(full).max())
 
 
 def test_nonfinite_position_is_reported():
