@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--extras", default="interp,forms,batch,solve,prec",
+                    help="comma list of the extra measurements to run (rank 0): interp, "
+                         "forms, batch, solve, prec")
     # smaller cases of the same workload (profiling captures); defaults = mid
     ap.add_argument("--grid", type=int, default=None)
     ap.add_argument("--particles", type=int, default=None)
@@ -315,11 +318,17 @@ def run_ours(args):
     }
 
     if not args.no_extras and rank == 0:
-        result["interp_sorted_vs_unsorted"] = interp_extras(ps, torch, dev, coef, bufs[0], n3)
-        result["coef_forms"] = precision_forms(ps, torch, dev, field, coef, bufs[0], n3)
-        result["batched_48_fields"] = batch_extras(ps, torch, dev)
-        result["solve_forms"] = solve_forms(ps, torch, dev, field)
-        result["precision_1536"] = precision_extras(ps, torch, dev)
+        want = set(args.extras.split(","))
+        if "interp" in want:
+            result["interp_sorted_vs_unsorted"] = interp_extras(ps, torch, dev, coef, bufs[0], n3)
+        if "forms" in want:
+            result["coef_forms"] = precision_forms(ps, torch, dev, field, coef, bufs[0], n3)
+        if "batch" in want:
+            result["batched_48_fields"] = batch_extras(ps, torch, dev)
+        if "solve" in want:
+            result["solve_forms"] = solve_forms(ps, torch, dev, field)
+        if "prec" in want:
+            result["precision_1536"] = precision_extras(ps, torch, dev)
     if not args.no_e2e:
         result["e2e"] = e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_,
                                     pg)
