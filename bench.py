@@ -368,7 +368,14 @@ def interp_extras(ps, torch, dev, coef, pos_sorted_by_bin, n3):
             # du/dt + (u . grad) u with a second field: 2 + 9 sums per particle
             ("sorted_accel_direct", lambda: ps.ps_lagrangian_accel(coef, n3, pos_sorted, acc,
                                                                    coef_np1=coef,
-                                                                   dt_field=1.0))):
+                                                                   dt_field=1.0)),
+            # the same two from each brick's staged halo (the second field's
+            # stencils from global memory)
+            ("sorted_staged_hessian", lambda: ps.ps_interp_hessian(
+                coef, n3, pos_sorted, hess, bin_offsets=bins2.offsets, brick=BRICK)),
+            ("sorted_staged_accel", lambda: ps.ps_lagrangian_accel(
+                coef, n3, pos_sorted, acc, coef_np1=coef, dt_field=1.0,
+                bin_offsets=bins2.offsets, brick=BRICK))):
         for _ in range(3):
             fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -277,14 +277,18 @@ ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype coef_t,
 /* Second derivatives of the interpolant (the cubic spline is twice         */
 /* continuously differentiable, Sec. 2.2): the 64-term sum of Eq. (spline)  */
 /* with d2b/dt2 = (1-t, 3t-2, 1-3t, t) along one axis (or db/dt along two), */
-/* times n_a n_b / (L_a L_b).  Direct gathers, any particle order.          */
+/* times n_a n_b / (L_a L_b).                                               */
+/*   perm, bin_offsets, brick: as for ps_interp.  bin_offsets == NULL:      */
+/*   direct gathers, any particle order; given (three components, not      */
+/*   F64): each brick's stencils from its halo staged in shared memory.     */
 /*   hess: [ncomp][6][np] F32 in the order xx, yy, zz, xy, xz, yz.          */
 /*   Non-finite positions give NaN and set the status word.                 */
 /* ------------------------------------------------------------------------ */
 ps_status ps_interp_hessian(const ps_grid* grid, int ncomp, ps_dtype coef_t,
                             const void* coef, const float* scale, int64_t np,
-                            const double* pos, float* hess, int32_t* status,
-                            void* stream);
+                            const double* pos, const int64_t* perm,
+                            const int32_t* bin_offsets, const int32_t brick[3],
+                            float* hess, int32_t* status, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Lagrangian acceleration of fluid particles (Sec. 2.1: they move with the */
@@ -292,14 +296,18 @@ ps_status ps_interp_hessian(const ps_grid* grid, int ncomp, ps_dtype coef_t,
 /* convective term from the field at t (coef_n), du/dt as                   */
 /* (u(coef_np1) - u(coef_n)) / dt_field when coef_np1 is given, else 0.     */
 /*   acc: [3][np] F32; vel (optional): [3][np] F32, u from coef_n.          */
-/*   dt_field > 0 when coef_np1 is given.  Direct gathers.                  */
+/*   dt_field > 0 when coef_np1 is given.  perm, bin_offsets, brick: as for */
+/*   ps_interp (bin_offsets == NULL: direct gathers, any order; given: the  */
+/*   stencils of coef_n from each brick's staged halo, those of coef_np1    */
+/*   from global memory).                                                   */
 /* ------------------------------------------------------------------------ */
 ps_status ps_lagrangian_accel(const ps_grid* grid, ps_dtype coef_t,
                               const void* coef_n, const float* scale_n,
                               const void* coef_np1, const float* scale_np1,
                               double dt_field, int64_t np, const double* pos,
-                              float* acc, float* vel, int32_t* status,
-                              void* stream);
+                              const int64_t* perm, const int32_t* bin_offsets,
+                              const int32_t brick[3], float* acc, float* vel,
+                              int32_t* status, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* One second-order Runge-Kutta step (Sec. 2.1; Sec. 4.3), Heun's form:     */

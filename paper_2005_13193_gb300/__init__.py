@@ -314,9 +314,12 @@ def ps_interp_backward(coef: torch.Tensor, n, pos: torch.Tensor, g_vel: torch.Te
 
 
 def ps_interp_hessian(coef: torch.Tensor, n, pos: torch.Tensor, hess: torch.Tensor,
-                      scale: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
-                      L=DEFAULT_L, stream=None):
-    """Second derivatives of Eq. (spline): hess [ncomp][6][np] (xx, yy, zz, xy, xz, yz)."""
+                      scale: Optional[torch.Tensor] = None, perm: Optional[torch.Tensor] = None,
+                      bin_offsets: Optional[torch.Tensor] = None, brick=None,
+                      status: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
+    """Second derivatives of Eq. (spline): hess [ncomp][6][np] (xx, yy, zz, xy, xz, yz).
+    With bin_offsets (and brick, perm as for ps_interp) the stencils come from each
+    brick's staged halo."""
     _check_coef_shape(coef, n)
     ncomp = _ncomp_of(coef)
     np_ = pos.shape[1]
@@ -324,10 +327,13 @@ def ps_interp_hessian(coef: torch.Tensor, n, pos: torch.Tensor, hess: torch.Tens
     _dev(pos, "pos", torch.float64)
     _dev(hess, "hess", torch.float32, ncomp * 6 * np_)
     _dev(scale, "scale", torch.float32)
+    _dev(perm, "perm", torch.int64, np_)
+    _dev(bin_offsets, "bin_offsets", torch.int32)
     _dev(status, "status", torch.int32, 4)
     g = make_grid(n, L)
     _check(_lib().ps_interp_hessian(ctypes.byref(g), ncomp, _coef_type(coef), _ptr(coef),
-                                    _ptr(scale), np_, _ptr(pos), _ptr(hess), _ptr(status),
+                                    _ptr(scale), np_, _ptr(pos), _ptr(perm), _ptr(bin_offsets),
+                                    _brick_arr(brick), _ptr(hess), _ptr(status),
                                     _stream(stream)))
 
 
@@ -335,9 +341,12 @@ def ps_lagrangian_accel(coef_n: torch.Tensor, n, pos: torch.Tensor, acc: torch.T
                         coef_np1: Optional[torch.Tensor] = None, dt_field: float = 1.0,
                         scale_n: Optional[torch.Tensor] = None,
                         scale_np1: Optional[torch.Tensor] = None,
-                        vel: Optional[torch.Tensor] = None, status: Optional[torch.Tensor] = None,
-                        L=DEFAULT_L, stream=None):
-    """a = du/dt + (u . grad) u at pos [3][np] -> acc [3][np] (du/dt from two fields)."""
+                        vel: Optional[torch.Tensor] = None, perm: Optional[torch.Tensor] = None,
+                        bin_offsets: Optional[torch.Tensor] = None, brick=None,
+                        status: Optional[torch.Tensor] = None, L=DEFAULT_L, stream=None):
+    """a = du/dt + (u . grad) u at pos [3][np] -> acc [3][np] (du/dt from two fields).
+    With bin_offsets (and brick, perm as for ps_interp) the stencils of coef_n come from
+    each brick's staged halo."""
     _check_coef_shape(coef_n, n)
     np_ = pos.shape[1]
     _dev(coef_n, "coef_n")
@@ -347,12 +356,15 @@ def ps_lagrangian_accel(coef_n: torch.Tensor, n, pos: torch.Tensor, acc: torch.T
     _dev(pos, "pos", torch.float64)
     _dev(acc, "acc", torch.float32, 3 * np_)
     _dev(vel, "vel", torch.float32, 3 * np_)
+    _dev(perm, "perm", torch.int64, np_)
+    _dev(bin_offsets, "bin_offsets", torch.int32)
     _dev(status, "status", torch.int32, 4)
     g = make_grid(n, L)
     _check(_lib().ps_lagrangian_accel(ctypes.byref(g), _coef_type(coef_n), _ptr(coef_n),
                                       _ptr(scale_n), _ptr(coef_np1), _ptr(scale_np1),
-                                      float(dt_field), np_, _ptr(pos), _ptr(acc), _ptr(vel),
-                                      _ptr(status), _stream(stream)))
+                                      float(dt_field), np_, _ptr(pos), _ptr(perm),
+                                      _ptr(bin_offsets), _brick_arr(brick), _ptr(acc),
+                                      _ptr(vel), _ptr(status), _stream(stream)))
 
 
 def ps_rk2_workspace_size(n, brick, np_: int, L=DEFAULT_L) -> int:
@@ -463,23 +475,31 @@ class SplineField:
         return out
 
     def hessian(self, pos: torch.Tensor, status: Optional[torch.Tensor] = None,
-                stream=None) -> torch.Tensor:
-        """Second derivatives at pos: [ncomp][6][np] (xx, yy, zz, xy, xz, yz)."""
+                bins: Optional["Bins"] = None, stream=None) -> torch.Tensor:
+        """Second derivatives at pos: [ncomp][6][np] (xx, yy, zz, xy, xz, yz); with
+        `bins` of these positions, from each brick's staged halo."""
         h = torch.empty((self.ncomp, 6, pos.shape[1]), dtype=torch.float32, device=pos.device)
-        ps_interp_hessian(self.coef, self.n, pos, h, scale=self.scale, status=status, L=self.L,
-                          stream=stream)
+        ps_interp_hessian(self.coef, self.n, pos, h, scale=self.scale,
+                          perm=bins.perm if bins is not None else None,
+                          bin_offsets=bins.offsets if bins is not None else None,
+                          brick=bins.brick if bins is not None else None, status=status,
+                          L=self.L, stream=stream)
         return h
 
     def acceleration(self, pos: torch.Tensor, later: Optional["SplineField"] = None,
                      dt_field: float = 1.0, status: Optional[torch.Tensor] = None,
-                     stream=None) -> torch.Tensor:
+                     bins: Optional["Bins"] = None, stream=None) -> torch.Tensor:
         """Lagrangian acceleration du/dt + (u . grad) u at pos ([3][np]); du/dt from
-        `later` (the field dt_field later) when given."""
+        `later` (the field dt_field later) when given; with `bins` of these positions,
+        from each brick's staged halo."""
         a = torch.empty((3, pos.shape[1]), dtype=torch.float32, device=pos.device)
         ps_lagrangian_accel(self.coef, self.n, pos, a,
                             coef_np1=later.coef if later is not None else None,
                             dt_field=dt_field, scale_n=self.scale,
                             scale_np1=later.scale if later is not None else None,
+                            perm=bins.perm if bins is not None else None,
+                            bin_offsets=bins.offsets if bins is not None else None,
+                            brick=bins.brick if bins is not None else None,
                             status=status, L=self.L, stream=stream)
         return a
 

@@ -57,8 +57,9 @@ SIGNATURES = {
     "ps_bin_particles_noalloc": (_I, [_GP, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "ps_interp": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "ps_interp_backward": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P, _P]),
-    "ps_interp_hessian": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P]),
-    "ps_lagrangian_accel": (_I, [_GP, _I, _P, _P, _P, _P, _D, _I64, _P, _P, _P, _P, _P]),
+    "ps_interp_hessian": (_I, [_GP, _I, _I, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
+    "ps_lagrangian_accel": (_I, [_GP, _I, _P, _P, _P, _P, _D, _I64, _P, _P, _P, _P, _P, _P,
+                                _P, _P]),
     "ps_batch_plan": (_I, [_I, _GP, _P, _I, _P, ctypes.c_char_p, _P]),
     "ps_batch_workspace_size": (_SZ, [_P]),
     "ps_batch_num_particles": (_I64, [_P]),

@@ -1570,10 +1570,41 @@ extern "C" ps_status ps_interp_backward(const ps_grid* grid, int ncomp, ps_dtype
   return PS_OK;
 }
 
+// Brick-staged form of the second derivatives (mode 3) or the Lagrangian
+// acceleration (mode 4) by the quad kernel; *done false where it does not
+// apply (the caller then gathers directly).
+static ps_status staged_extra(const ps_grid* grid, ps_dtype coef_t, const void* coef,
+                              const float* scale, const void* coef2, const float* scale2,
+                              double inv_dt, int64_t np, const double* pos,
+                              const int64_t* perm, const int32_t* bin_offsets,
+                              const int32_t brick[3], float* out, float* vel, int32_t* status,
+                              int mode, cudaStream_t st, bool* done) {
+  *done = false;
+  StagedArgs a{};
+  size_t smem;
+  ps_status rc = fill_staged(grid, coef_t, brick, 0, false, &a, &smem);
+  if (rc) return rc;
+  a.coef = coef;
+  a.scale = scale;
+  a.coef2 = coef2;
+  a.scale2 = scale2;
+  attach_tma(&a, coef_t);
+  a.np = np;
+  a.pos_in = pos;
+  a.perm = perm;
+  a.offs = bin_offsets;
+  a.grad = out;
+  a.vel = vel;
+  a.dt = inv_dt;
+  a.status = status;
+  return launch_quad(a, coef_t, mode, st, done);
+}
+
 extern "C" ps_status ps_interp_hessian(const ps_grid* grid, int ncomp, ps_dtype coef_t,
                                        const void* coef, const float* scale, int64_t np,
-                                       const double* pos, float* hess, int32_t* status,
-                                       void* stream) {
+                                       const double* pos, const int64_t* perm,
+                                       const int32_t* bin_offsets, const int32_t brick[3],
+                                       float* hess, int32_t* status, void* stream) {
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if (ncomp != 1 && ncomp != 3) return fail(PS_ERR_INVALID_ARG, "ncomp must be 1 or 3");
@@ -1583,7 +1614,15 @@ extern "C" ps_status ps_interp_hessian(const ps_grid* grid, int ncomp, ps_dtype 
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np == 0) return PS_OK;
   if (!pos || !hess) return fail(PS_ERR_INVALID_ARG, "pos and hess are required");
+  if (perm && !bin_offsets) return fail(PS_ERR_INVALID_ARG, "perm needs bin_offsets");
+  if (bin_offsets && !brick) return fail(PS_ERR_INVALID_ARG, "bin_offsets needs brick");
   cudaStream_t st = as_stream(stream);
+  if (bin_offsets && ncomp == 3 && coef_t != PS_F64) {
+    bool done = false;
+    rc = staged_extra(grid, coef_t, coef, scale, nullptr, nullptr, 0.0, np, pos, perm,
+                      bin_offsets, brick, hess, nullptr, status, 3, st, &done);
+    if (rc || done) return rc;
+  }
   GridArgs g = make_grid_args(grid, coef_t);
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
@@ -1602,8 +1641,9 @@ extern "C" ps_status ps_lagrangian_accel(const ps_grid* grid, ps_dtype coef_t,
                                          const void* coef_n, const float* scale_n,
                                          const void* coef_np1, const float* scale_np1,
                                          double dt_field, int64_t np, const double* pos,
-                                         float* acc, float* vel, int32_t* status,
-                                         void* stream) {
+                                         const int64_t* perm, const int32_t* bin_offsets,
+                                         const int32_t brick[3], float* acc, float* vel,
+                                         int32_t* status, void* stream) {
   ps_status rc = validate_grid(grid);
   if (rc) return rc;
   if ((rc = check_coef(coef_t, coef_n, scale_n))) return rc;
@@ -1613,9 +1653,17 @@ extern "C" ps_status ps_lagrangian_accel(const ps_grid* grid, ps_dtype coef_t,
   if (np < 0) return fail(PS_ERR_INVALID_ARG, "np < 0");
   if (np == 0) return PS_OK;
   if (!pos || !acc) return fail(PS_ERR_INVALID_ARG, "pos and acc are required");
+  if (perm && !bin_offsets) return fail(PS_ERR_INVALID_ARG, "perm needs bin_offsets");
+  if (bin_offsets && !brick) return fail(PS_ERR_INVALID_ARG, "bin_offsets needs brick");
   cudaStream_t st = as_stream(stream);
-  GridArgs g = make_grid_args(grid, coef_t);
   const double inv_dt = coef_np1 ? 1.0 / dt_field : 0.0;
+  if (bin_offsets && coef_t != PS_F64) {
+    bool done = false;
+    rc = staged_extra(grid, coef_t, coef_n, scale_n, coef_np1, scale_np1, inv_dt, np, pos, perm,
+                      bin_offsets, brick, acc, vel, status, 4, st, &done);
+    if (rc || done) return rc;
+  }
+  GridArgs g = make_grid_args(grid, coef_t);
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
     lagrangian_accel_direct<Tc><<<quad_blocks(np), 256, 0, st>>>(

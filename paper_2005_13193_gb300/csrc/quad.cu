@@ -166,6 +166,74 @@ __device__ __forceinline__ void qdbasis(float t, float d[4]) {
   d[3] = __fmul_rn(tt, 0.5f);
 }
 
+// d2 b / dt2 of the same basis (piecewise linear: the spline is twice
+// continuously differentiable, Sec. 2.2).
+__device__ __forceinline__ void qddbasis(float t, float d[4]) {
+  d[0] = __fsub_rn(1.f, t);
+  d[1] = __fmaf_rn(3.f, t, -2.f);
+  d[2] = __fmaf_rn(-3.f, t, 1.f);
+  d[3] = t;
+}
+
+// The six second derivatives (in cells^-2) of the three components at
+// (t_x, t_y, t_z): out[e][c], e = xx, yy, zz, xy, xz, yz; every lane of the
+// quad returns them (the same bits).
+__device__ __forceinline__ void quad_sum_hess(const float v[16][3], const float t[3], int k,
+                                              float out[6][3]) {
+  float bx[4], by[4], dbx[4], dby[4], ddbx[4], ddby[4], z4[4];
+  qbasis(t[0], bx);
+  qbasis(t[1], by);
+  qdbasis(t[0], dbx);
+  qdbasis(t[1], dby);
+  qddbasis(t[0], ddbx);
+  qddbasis(t[1], ddby);
+  qbasis(t[2], z4);
+  const float bz = pick4(z4, k);
+  qdbasis(t[2], z4);
+  const float dbz = pick4(z4, k);
+  qddbasis(t[2], z4);
+  const float ddbz = pick4(z4, k);
+  // y sums of the x sums: A = by s0, Bx = by s1, By = dby s0, Cxx = by s2,
+  // Cyy = ddby s0, Cxy = dby s1 (s0, s1, s2: x sums with b, b', b'')
+  float A[3] = {0.f, 0.f, 0.f}, Bx[3] = {0.f, 0.f, 0.f}, By[3] = {0.f, 0.f, 0.f};
+  float Cxx[3] = {0.f, 0.f, 0.f}, Cyy[3] = {0.f, 0.f, 0.f}, Cxy[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float s0 = __fmul_rn(bx[0], v[4 * j][c]), s1 = __fmul_rn(dbx[0], v[4 * j][c]),
+            s2 = __fmul_rn(ddbx[0], v[4 * j][c]);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) {
+        s0 = __fmaf_rn(bx[i], v[4 * j + i][c], s0);
+        s1 = __fmaf_rn(dbx[i], v[4 * j + i][c], s1);
+        s2 = __fmaf_rn(ddbx[i], v[4 * j + i][c], s2);
+      }
+      A[c] = __fmaf_rn(by[j], s0, A[c]);
+      Bx[c] = __fmaf_rn(by[j], s1, Bx[c]);
+      By[c] = __fmaf_rn(dby[j], s0, By[c]);
+      Cxx[c] = __fmaf_rn(by[j], s2, Cxx[c]);
+      Cyy[c] = __fmaf_rn(ddby[j], s0, Cyy[c]);
+      Cxy[c] = __fmaf_rn(dby[j], s1, Cxy[c]);
+    }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    out[0][c] = __fmul_rn(bz, Cxx[c]);
+    out[1][c] = __fmul_rn(bz, Cyy[c]);
+    out[2][c] = __fmul_rn(ddbz, A[c]);
+    out[3][c] = __fmul_rn(bz, Cxy[c]);
+    out[4][c] = __fmul_rn(dbz, Bx[c]);
+    out[5][c] = __fmul_rn(dbz, By[c]);
+  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      out[e][c] = __fadd_rn(out[e][c], __shfl_xor_sync(FULL, out[e][c], 1));
+      out[e][c] = __fadd_rn(out[e][c], __shfl_xor_sync(FULL, out[e][c], 2));
+    }
+}
+
 // Sum of the quad's stencil with the basis at (t_x, t_y, t_z): every lane
 // returns the three components, with the same bits in all four lanes (the
 // products and the butterfly's sums are rounded explicitly).  GRAD also
@@ -285,10 +353,12 @@ __device__ __forceinline__ void quad_locate(const StagedArgs& a, const QGeo<CT>&
 // Phase B for chunk ch (eight particles) of a round, by one warp: quad
 // (lane >> 2) takes position 8 ch + (lane >> 2) of the interleaved lists.
 // MODE 0: velocities; 1: velocities and the gradient tensor; 2: fused Heun
-// step.  `stays` counts (per warp) the particles whose next bin is st.bin.
+// step; 3: second derivatives; 4: Lagrangian acceleration.  `stays` counts
+// (per warp) the particles whose next bin is st.bin.
 template <typename Tc, int MODE, int CT>
 __device__ __forceinline__ void quad_chunk(const StagedArgs& a, const QGeo<CT>& geo,
-                                           const QStage& st, int ch, int& stays) {
+                                           const QStage& st, int ch, int& stays,
+                                           int phase = 0) {
   const GridArgs& g = a.g;
   const Tc* coef = static_cast<const Tc*>(a.coef);
   const int lane = threadIdx.x & 31, k = lane & 3;
@@ -309,9 +379,73 @@ __device__ __forceinline__ void quad_chunk(const StagedArgs& a, const QGeo<CT>& 
   const float t[3] = {rt.x, rt.y, rt.z};
   const int64_t p = a.perm ? a.perm[st.cb + r] : (int64_t)(st.cb + r);
   float v[16][3];
+  if constexpr (MODE == 4) {
+    if (phase == 2) {
+      // the later field's stencil, from its halo staged in the same buffer;
+      // the convective term and u were left in the round's x records
+      quad_fetch<Tc, CT>(v, inh, l, cell, k, st.halo, st.scl, geo, g,
+                         static_cast<const Tc*>(a.coef2), a.scale2);
+      float w[4][3];
+      quad_sum<false>(v, t, k, w);
+      if (valid) {
+        if (k < 3) {
+          const float* part = reinterpret_cast<const float*>(st.x) + 6 * slot;
+          const float acc = __fmaf_rn(__fsub_rn(sel3(w[0], k), part[3 + k]), (float)a.dt,
+                                      part[k]);
+          a.grad[(int64_t)k * np + p] = ok ? acc : nanf_;
+        }
+      }
+      return;
+    }
+  }
   quad_fetch<Tc, CT>(v, inh, l, cell, k, st.halo, st.scl, geo, g, coef, a.scale);
+  if constexpr (MODE == 3) {
+    // second derivatives -> hess [3][6][np] (a.grad), scaled by n_a/L_a n_b/L_b
+    float h[6][3];
+    quad_sum_hess(v, t, k, h);
+    if (valid) {
+      if (k < 3) {
+        const float hx = g.inv_hf[0], hy = g.inv_hf[1], hz = g.inv_hf[2];
+        const float sc[6] = {__fmul_rn(hx, hx), __fmul_rn(hy, hy), __fmul_rn(hz, hz),
+                             __fmul_rn(hx, hy), __fmul_rn(hx, hz), __fmul_rn(hy, hz)};
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+          a.grad[((int64_t)k * 6 + e) * np + p] = ok ? __fmul_rn(sel3(h[e], k), sc[e]) : nanf_;
+      } else if (!ok) {
+        flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+      }
+    }
+    return;
+  }
   float u1[4][3];
-  quad_sum<MODE == 1>(v, t, k, u1);
+  quad_sum<MODE == 1 || MODE == 4>(v, t, k, u1);
+  if constexpr (MODE == 4) {
+    // Lagrangian acceleration a = (u . grad) u + du/dt -> a.grad [3][np]: u
+    // and its gradient from coef; with a later field (coef2) du/dt =
+    // (u(coef2) - u) / dt_field (a.dt = 1 / dt_field), gathered in a second
+    // phase (the convective term and u wait in the round's x records)
+    if (valid) {
+      if (k < 3) {
+        const float gx = __fmul_rn(sel3(u1[1], k), g.inv_hf[0]);
+        const float gy = __fmul_rn(sel3(u1[2], k), g.inv_hf[1]);
+        const float gz = __fmul_rn(sel3(u1[3], k), g.inv_hf[2]);
+        float conv = __fmul_rn(gx, u1[0][0]);
+        conv = __fmaf_rn(gy, u1[0][1], conv);
+        conv = __fmaf_rn(gz, u1[0][2], conv);
+        if (a.coef2) {
+          float* part = reinterpret_cast<float*>(const_cast<double*>(st.x)) + 6 * slot;
+          part[k] = conv;
+          part[3 + k] = sel3(u1[0], k);
+        } else {
+          a.grad[(int64_t)k * np + p] = ok ? conv : nanf_;
+        }
+        if (a.vel) a.vel[(int64_t)k * np + p] = ok ? sel3(u1[0], k) : nanf_;
+      } else if (!ok) {
+        flag_status(a.status, PS_DEV_NONFINITE_POS, p);
+      }
+    }
+    return;
+  }
   if constexpr (MODE <= 1) {
     if (valid) {
       if (k < 3) a.vel[(int64_t)k * np + p] = ok ? sel3(u1[0], k) : nanf_;
@@ -416,6 +550,38 @@ __device__ __forceinline__ void quad_chunk(const StagedArgs& a, const QGeo<CT>& 
 }
 
 // ---------------------------------------------------- one block per brick --
+// The brick's halo of a.coef by plain loads, in the layout the gathers read
+// (float4 nodes, or raw 16-bit nodes with their rows' scales).  No barrier.
+template <typename Tc, int CT>
+__device__ __forceinline__ void quad_stage_loads(const StagedArgs& a, const QGeo<CT>& geo,
+                                                 const QStage& st, float4* halo) {
+  const Tc* coef = static_cast<const Tc*>(a.coef);
+  const int tid = threadIdx.x;
+  if constexpr (IsNode16<Tc>::value) {
+    const GridArgs& g = a.g;
+    const int nrow = geo.Sy * geo.Sz;
+    Tc* h16 = reinterpret_cast<Tc*>(halo);
+    for (int it = tid; it < nrow * geo.Sx; it += blockDim.x) {
+      const int r = it / geo.Sx, x = it - r * geo.Sx;
+      const int lz = r / geo.Sy, ly = r - lz * geo.Sy;
+      const int64_t row = (int64_t)wrap_row(st.P0[2] + lz, g.n[2]) * g.m[1] +
+                          wrap_row(st.P0[1] + ly, g.n[1]);
+      h16[lz * geo.PS + ly * geo.SX + x] = coef[row * g.rx + wrap_row(st.P0[0] + x, g.n[0])];
+    }
+    float4* sc = const_cast<float4*>(st.scl);
+    for (int r = tid; r < nrow; r += blockDim.x) {
+      const int lz = r / geo.Sy, ly = r - lz * geo.Sy;
+      const int64_t row = (int64_t)wrap_row(st.P0[2] + lz, g.n[2]) * g.m[1] +
+                          wrap_row(st.P0[1] + ly, g.n[1]);
+      sc[r] = __ldg(reinterpret_cast<const float4*>(a.scale) + row);
+    }
+  } else if (a.vec) {
+    stage_halo_vec<Tc, 3>(a, coef, st.P0, halo, false);
+  } else {
+    stage_halo<Tc, 3>(a, coef, st.P0, halo, false);
+  }
+}
+
 // The brick's halo by a tensor copy (node coefficients) or plain loads; its
 // particles in rounds of kQT: phase A by all threads, a block barrier, phase
 // B by the warps in turn.
@@ -470,35 +636,11 @@ __device__ __forceinline__ void quad_brick(const StagedArgs& a, float4* smem) {
       }
     }
   }
-  if (staged && !tma) {
-    if constexpr (IsNode16<Tc>::value) {
-      // the tensor copy's layout by plain loads: raw nodes, rows' scales
-      const GridArgs& g = a.g;
-      const int nrow = geo.Sy * geo.Sz;
-      Tc* h16 = reinterpret_cast<Tc*>(halo);
-      for (int it = tid; it < nrow * geo.Sx; it += blockDim.x) {
-        const int r = it / geo.Sx, x = it - r * geo.Sx;
-        const int lz = r / geo.Sy, ly = r - lz * geo.Sy;
-        const int64_t row = (int64_t)wrap_row(st.P0[2] + lz, g.n[2]) * g.m[1] +
-                            wrap_row(st.P0[1] + ly, g.n[1]);
-        h16[lz * geo.PS + ly * geo.SX + x] = coef[row * g.rx + wrap_row(st.P0[0] + x, g.n[0])];
-      }
-      float4* sc = const_cast<float4*>(st.scl);
-      for (int r = tid; r < nrow; r += blockDim.x) {
-        const int lz = r / geo.Sy, ly = r - lz * geo.Sy;
-        const int64_t row = (int64_t)wrap_row(st.P0[2] + lz, g.n[2]) * g.m[1] +
-                            wrap_row(st.P0[1] + ly, g.n[1]);
-        sc[r] = __ldg(reinterpret_cast<const float4*>(a.scale) + row);
-      }
-    } else if (a.vec) {
-      stage_halo_vec<Tc, 3>(a, coef, st.P0, halo, false);
-    } else {
-      stage_halo<Tc, 3>(a, coef, st.P0, halo, false);
-    }
-  }
+  if (staged && !tma) quad_stage_loads<Tc, CT>(a, geo, st, halo);
   __syncthreads();  // counters, barrier initialisation, staged halo
 
-  bool copied = staged;  // the halo holds the brick's nodes
+  bool copied = staged;  // the tensor copy of the halo completed (or there is none)
+  bool halo_ok = staged; // the halo buffer holds the nodes the next gathers read
   int stays = 0;
   int round = 0;
   for (int cb = beg; cb < end; cb += kQT, ++round) {
@@ -525,6 +667,7 @@ __device__ __forceinline__ void quad_brick(const StagedArgs& a, float4* smem) {
       if (done && a.wait_probe > 0) done = tma_wait(&mbar[1], 0, a.wait_probe);
       if (!done) {
         copied = false;
+        halo_ok = false;
         if (lane == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
       }
     }
@@ -532,13 +675,63 @@ __device__ __forceinline__ void quad_brick(const StagedArgs& a, float4* smem) {
     st.no = cnt[round & 1][1];
     st.cb = cb;
     st.m = mr;
-    st.staged = copied;
+    st.staged = halo_ok;
     if (tid == 0 && cb + kQT < end) {
       // the next round's counters (last read in the previous round)
       cnt[(round + 1) & 1][0] = 0;
       cnt[(round + 1) & 1][1] = 0;
     }
     for (int ch = warp; 8 * ch < mr; ch += nwarps) quad_chunk<Tc, MODE, CT>(a, geo, st, ch, stays);
+    if constexpr (MODE == 4) {
+      if (a.coef2) {
+        // the later field's halo replaces this one (plain loads), then the
+        // second gathers; a tensor copy that had not landed must first (its
+        // bounded wait again), else the second field is read from global
+        // memory (one decision for the block: the staging is shared)
+        __syncthreads();
+        bool can = staged;
+        if (tma && !copied) {
+          copied = tma_wait(&mbar[0], 0);
+          can = can && copied;
+        }
+        can = __syncthreads_and(can);
+        bool by_copy = false;
+        if constexpr (IsNode4<Tc>::value && !IsNode16<Tc>::value) {
+          // tmap2 holds the later field's node map (tma == 2): one more
+          // tensor copy into the same buffer, the barrier's next phase
+          if (can && tma && a.tma == 2 && round == 0) {
+            by_copy = true;
+            if (tid == 0) {
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              tma_copy_halo(&a.tmap2, halo, &mbar[0], st.P0,
+                            (unsigned)(sizeof(float4) * geo.SX * geo.Sy * geo.Sz));
+            }
+            const bool done2 = tma_wait(&mbar[0], 1);
+            can = __syncthreads_and(done2);
+            if (!done2) {
+              copied = tma_wait(&mbar[0], 1);  // must land before the block ends
+              if (lane == 0) flag_status(a.status, PS_DEV_TIMEOUT, beg);
+            }
+          }
+        }
+        if (can && !by_copy) {
+          StagedArgs a2 = a;
+          a2.coef = a.coef2;
+          a2.scale = a.scale2;
+          quad_stage_loads<Tc, CT>(a2, geo, st, halo);
+        }
+        st.staged = can;
+        __syncthreads();
+        for (int ch = warp; 8 * ch < mr; ch += nwarps)
+          quad_chunk<Tc, MODE, CT>(a, geo, st, ch, stays, 2);
+        if (cb + kQT < end) {
+          // the next round's first phase reads the first field's halo again
+          __syncthreads();
+          if (can) quad_stage_loads<Tc, CT>(a, geo, st, halo);
+          halo_ok = can;
+        }
+      }
+    }
     if (cb + kQT < end) __syncthreads();  // the records are refilled
   }
   if (MODE == 2 && a.next_counts && lane == 0 && stays) atomicAdd(&a.next_counts[bin], stays);
@@ -586,6 +779,17 @@ ps_status launch_quad_t(const StagedArgs& a0, cudaStream_t st, bool* done) {
   a.tma = 0;
   if constexpr (NodeDtype<Tc>::v >= 0)
     if (a0.tma && SX <= 256) a.tma = encode_node_halo_map(&a, (ps_dtype)NodeDtype<Tc>::v) ? 1 : 0;
+  if constexpr (MODE == 4 && std::is_same<Tc, float4>::value) {
+    // the later field's node map in tmap2 (tma = 2)
+    if (a.tma == 1 && a.coef2) {
+      StagedArgs t = a;
+      t.coef = a.coef2;
+      if (encode_node_halo_map(&t, PS_F32X4)) {
+        a.tmap2 = t.tmap;
+        a.tma = 2;
+      }
+    }
+  }
   const size_t smem = (size_t)halo_f4<Tc>(a.S[2], a.S[1], a.PS) * sizeof(float4) + qrec_bytes();
   if (smem > 227 * 1024) return PS_OK;
   if (a.b.nbins > 0x7fffffff) return fail(PS_ERR_UNSUPPORTED, "too many bins");
@@ -618,9 +822,13 @@ ps_status launch_quad(const StagedArgs& a, ps_dtype coef_t, int mode, cudaStream
   *done = false;
   auto go = [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
-    if (mode == 0) return launch_quad_t<Tc, 0>(a, st, done);
-    if (mode == 1) return launch_quad_t<Tc, 1>(a, st, done);
-    return launch_quad_t<Tc, 2>(a, st, done);
+    switch (mode) {
+      case 0: return launch_quad_t<Tc, 0>(a, st, done);
+      case 1: return launch_quad_t<Tc, 1>(a, st, done);
+      case 2: return launch_quad_t<Tc, 2>(a, st, done);
+      case 3: return launch_quad_t<Tc, 3>(a, st, done);
+      default: return launch_quad_t<Tc, 4>(a, st, done);
+    }
   };
   switch (coef_t) {
     case PS_F32X4: return go(float4{});

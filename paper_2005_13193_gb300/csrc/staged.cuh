@@ -57,8 +57,9 @@ struct StagedArgs {
 bool encode_node_halo_map(StagedArgs* a, ps_dtype coef_t);
 
 // The quad-per-particle brick kernel (quad.cu) for three components; mode 0
-// velocities, 1 with the gradient tensor, 2 fused Heun step.  Leaves *done
-// false where it does not apply.
+// velocities, 1 with the gradient tensor, 2 fused Heun step, 3 second
+// derivatives (into a.grad), 4 Lagrangian acceleration (into a.grad; a.dt
+// holds 1 / dt_field).  Leaves *done false where it does not apply.
 ps_status launch_quad(const StagedArgs& a, ps_dtype coef_t, int mode, cudaStream_t st,
                       bool* done);
 

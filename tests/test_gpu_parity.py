@@ -624,7 +624,11 @@ def test_hessian_matches_oracle(n, L):
     cmax = np.abs(cref).max()
     f = torch.from_numpy(field).to(DEV)
     pg = torch.from_numpy(pos).to(DEV)
-    out = {}
+    # binned: through the permutation, and physically sorted
+    bins, sorted_pos = ps.bin_particles(n, (8, 8, 8), pg, want_sorted=True, L=L)
+    sbins = ps.Bins(bins.brick, bins.offsets, bins.bin_of, None)
+    perm = bins.perm.cpu().numpy()
+    out, outb = {}, {}
     for dt, bar in ((torch.float32, 4e-5), (torch.float64, 1e-9), (ps.F32X4, 4e-5),
                     (torch.bfloat16, 4 * 2.0 ** -8), (ps.BF16X4, 4 * 2.0 ** -8)):
         sf = ps.SplineField.from_field(f, dt, L=L)
@@ -632,10 +636,20 @@ def test_hessian_matches_oracle(n, L):
         h = sf.hessian(pg, status=st).cpu().numpy()
         assert ps.ps_status_read(st)[0] == 0
         # plus the rounding of the FP32 output itself
-        assert np.all(np.abs(h - ref) <= bar * scale * cmax + 2.0 ** -23 * np.abs(ref)), dt
+        tol = bar * scale * cmax + 2.0 ** -23 * np.abs(ref)
+        assert np.all(np.abs(h - ref) <= tol), dt
         out[dt] = h
+        # from each brick's staged halo
+        hb = sf.hessian(pg, status=st, bins=bins).cpu().numpy()
+        hs = sf.hessian(sorted_pos, status=st, bins=sbins).cpu().numpy()
+        assert ps.ps_status_read(st)[0] == 0
+        assert np.all(np.abs(hb - ref) <= tol), dt
+        assert np.all(np.abs(hs - ref[:, :, perm]) <= tol[:, :, perm]), dt
+        outb[dt] = hb
     np.testing.assert_array_equal(out[ps.F32X4], out[torch.float32])
     np.testing.assert_array_equal(out[ps.BF16X4], out[torch.bfloat16])
+    np.testing.assert_array_equal(outb[ps.F32X4], outb[torch.float32])
+    np.testing.assert_array_equal(outb[ps.BF16X4], outb[torch.bfloat16])
 
 
 def test_hessian_nonfinite_flagged():
@@ -644,13 +658,20 @@ def test_hessian_nonfinite_flagged():
     pos[1, 5] = np.nan
     sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
     st = torch.zeros(4, dtype=torch.int32, device=DEV)
-    h = sf.hessian(torch.from_numpy(pos).to(DEV), status=st).cpu().numpy()
+    pg = torch.from_numpy(pos).to(DEV)
+    h = sf.hessian(pg, status=st).cpu().numpy()
+    assert np.isnan(h[:, :, 5]).all() and np.isfinite(np.delete(h, 5, axis=2)).all()
+    assert ps.ps_status_read(st)[0] == 1
+    st.zero_()
+    bins = ps.bin_particles(n, (8, 8, 8), pg)
+    h = sf.hessian(pg, status=st, bins=bins).cpu().numpy()
     assert np.isnan(h[:, :, 5]).all() and np.isfinite(np.delete(h, 5, axis=2)).all()
     assert ps.ps_status_read(st)[0] == 1
 
 
+@pytest.mark.parametrize("binned", [False, True])
 @pytest.mark.parametrize("two_fields", [False, True])
-def test_lagrangian_accel_matches_oracle(two_fields):
+def test_lagrangian_accel_matches_oracle(two_fields, binned):
     n = (24, 20, 28)
     field, pos, cref = _case(n, 6000, seed=175, spread=1.2)
     f2 = synth.random_field(n, ncomp=3, seed=176).astype(np.float32)
@@ -658,10 +679,19 @@ def test_lagrangian_accel_matches_oracle(two_fields):
     dt = 0.05
     ref = oracle.lagrangian_accel(cref, pos, cref2 if two_fields else None, dt)
     u, G = oracle.interp(cref, pos, grad=True)
+    pg = torch.from_numpy(pos).to(DEV)
+    bins = ps.bin_particles(n, (8, 8, 8), pg) if binned else None
     sf = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), torch.float32)
     sf2 = ps.SplineField.from_field(torch.from_numpy(f2).to(DEV), torch.float32)
-    a = sf.acceleration(torch.from_numpy(pos).to(DEV), later=sf2 if two_fields else None,
-                        dt_field=dt).cpu().numpy()
+    a = sf.acceleration(pg, later=sf2 if two_fields else None, dt_field=dt,
+                        bins=bins).cpu().numpy()
+    if binned:
+        # node storage holds the same values: the same bits
+        n4 = ps.SplineField.from_field(torch.from_numpy(field).to(DEV), ps.F32X4)
+        n42 = ps.SplineField.from_field(torch.from_numpy(f2).to(DEV), ps.F32X4)
+        a4 = n4.acceleration(pg, later=n42 if two_fields else None, dt_field=dt,
+                             bins=bins).cpu().numpy()
+        np.testing.assert_array_equal(a4, a)
     # sum over three axes of (gradient bar 1e-5 * 3 * n/L * max|c|) * |u|
     # + |grad u| * (velocity bar 1e-5 rms), plus both fields' velocity bars
     # over dt
