@@ -565,8 +565,10 @@ def precision_extras(ps, torch, dev):
 def batch_extras(ps, torch, dev):
     """The many-fields workload: 48 fields with edges uniform over {64, 96,
     128, 192, 256}, 10k..2M particles per field (log-uniform), 20 Heun steps
-    (dt 1e-3).  Batched plan (autotuned brick, steps replayed from a CUDA
-    graph) against a loop of single-field Tracker steps on the same GPU."""
+    (dt 1e-3).  Batched plan (autotuned brick; the 48 solves and the 20 steps
+    replayed from one CUDA graph, the steps as one persistent launch or as a
+    launch per phase and step) against a loop of single-field Tracker steps
+    on the same GPU."""
     from paper_2005_13193_gb300 import autotune, synth
     sizes, nps = synth.batch_sizes(48, seed=3000)
     nsteps, dt = 20, 1e-3
@@ -581,9 +583,24 @@ def batch_extras(ps, torch, dev):
     plan = ps.BatchPlan(grids, nps, coef_dtype=ps.F32X4, brick=best)
     pos = pos0.clone()
     ids = torch.arange(plan.np_total, dtype=torch.int64, device=dev)
-    plan.run(flds, pos, nsteps, dt, solve=False, ids=ids, use_graph=True)  # capture
-    t_graph = _event_ms(torch, lambda: plan.run(flds, pos, nsteps, dt, solve=False, ids=ids,
-                                                use_graph=True), 3, warmup=1)
+    # the 48 solves and the 20 steps in one graph: the steps as one cooperative
+    # persistent launch (default), and as a launch per phase and step
+    timings = {}
+    old = ps.ps_tune_get("batch_persistent")
+    try:
+        for name, pers in (("persistent", 1), ("launch_per_step", 0)):
+            ps.ps_tune_set("batch_persistent", pers)
+            plan.run(flds, pos, nsteps, dt, solve=True, ids=ids, use_graph=True)  # capture
+            timings[name] = _event_ms(torch, lambda: plan.run(flds, pos, nsteps, dt, solve=True,
+                                                              ids=ids, use_graph=True), 3,
+                                      warmup=1)
+        ps.ps_tune_set("batch_persistent", 1)
+        plan.run(flds, pos, nsteps, dt, solve=False, ids=ids, use_graph=True)
+        t_steps = _event_ms(torch, lambda: plan.run(flds, pos, nsteps, dt, solve=False, ids=ids,
+                                                    use_graph=True), 3, warmup=1)
+    finally:
+        ps.ps_tune_set("batch_persistent", old)
+    t_graph = timings["persistent"]
     trackers = []
     for f, (n, v) in enumerate(zip(sizes, nps)):
         b = plan.base[f]
@@ -600,8 +617,13 @@ def batch_extras(ps, torch, dev):
             "coef_storage": "f32x4 nodes",
             "autotuned_brick": list(best),
             "autotune_ms_per_step": {"x".join(map(str, k)): v for k, v in table.items()},
+            "graph": "48 solves + 20 Heun steps",
             "batched_graph_ms": t_graph, "batched_particles_per_s": units / (t_graph * 1e-3),
-            "per_field_loop_ms": t_loop, "loop_particles_per_s": units / (t_loop * 1e-3)}
+            "launch_per_step_graph_ms": timings["launch_per_step"],
+            "steps_only_persistent_ms": t_steps,
+            "steps_only_particles_per_s": units / (t_steps * 1e-3),
+            "per_field_loop_ms": t_loop, "loop_particles_per_s": units / (t_loop * 1e-3),
+            "loop_note": "per-field Tracker steps without the solves"}
 
 
 def e2e_measure(ps, torch, dev, field, pos_host, coef, ws_solve, n3, K, ws_, pg):

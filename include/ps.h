@@ -130,6 +130,8 @@ int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
  *  "node_tma" 0 or 1 (default 1): halos of node coefficients by tensor copy.
  *  "solve_xw" 0, 8, 16 or 32 (0 = default 16): x extent of a block of the
  *     strided spline passes.
+ *  "batch_persistent" 0 or 1 (default 1): ps_batch_run runs all steps in one
+ *     cooperative persistent launch (1) or a launch per phase and step (0).
  *  "wait_probe" in [0, 2^30] (default 0), a test knob: > 0 makes every
  *     staged brick wait, after its halo copy has landed, on a barrier that
  *     nothing completes, for that many clocks; the wait gives up, the status
@@ -379,14 +381,19 @@ ps_status ps_rk2_sort(const ps_grid* grid, const int32_t brick[3], int64_t np,
 /* spline coefficients (solve = 1; ps_spline_coeffs per field), then takes  */
 /* nsteps Heun steps of every particle (frozen fields): each step is one    */
 /* bin sort over all particles (global bin = first bin of the field + bin   */
-/* in the field) and one brick-kernel launch over the bricks of all fields. */
+/* in the field) and one pass over the bricks of all fields, all steps in   */
+/* one cooperative persistent launch whose phases meet at grid-wide         */
+/* barriers (tune "batch_persistent" 0: a launch per phase and step).  A    */
+/* barrier wait that runs out (about 2^31 clocks) stops every block and     */
+/* sets PS_DEV_TIMEOUT in *status; positions are then unspecified.          */
 /* Particles end in bin order per field, as with ps_rk2_step(rebin=1); ids  */
 /* (optional, int64 [np_total]) and vel_out (optional, [3][np_total] = u at */
 /* the start of the last step) follow them.  use_graph = 1 captures the     */
-/* nsteps steps in a CUDA graph on the first run and replays it while the   */
-/* pointers, nsteps and dt stay the same (the capture uses a stream owned   */
-/* by the plan; the graph is launched on `stream`).  The plan holds host    */
-/* metadata, that stream and the graph; device scratch comes from ws        */
+/* solves and the steps in a CUDA graph on the first run and replays it     */
+/* while the pointers, nsteps, dt and solve stay the same (the capture uses */
+/* a stream owned by the plan; the graph is launched on `stream`).  The     */
+/* plan holds host metadata, that stream and the graph; device scratch      */
+/* comes from ws                                                            */
 /* (ps_batch_workspace_size).  tune_cache: optional text file whose line    */
 /* "brick <bx> <by> <bz>" overrides `brick` (written by the autotuner).     */
 /* Coefficients: PS_F32, PS_BF16, PS_F16 or their node forms (PS_F32X4,    */

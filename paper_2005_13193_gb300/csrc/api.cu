@@ -133,6 +133,11 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
     tuning().node_tma = (int)value;
     return PS_OK;
   }
+  if (!strcmp(key, "batch_persistent")) {
+    if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "batch_persistent is 0 or 1");
+    tuning().batch_persistent = (int)value;
+    return PS_OK;
+  }
   if (!strcmp(key, "wait_probe")) {
     if (value < 0 || value > (1 << 30)) return fail(PS_ERR_INVALID_ARG, "wait_probe in [0, 2^30]");
     tuning().wait_probe = (int)value;
@@ -148,6 +153,7 @@ extern "C" int64_t ps_tune_get(const char* key) {
   if (!strcmp(key, "node_tma")) return tuning().node_tma;
   if (!strcmp(key, "solve_xw")) return tuning().solve_xw;
   if (!strcmp(key, "wait_probe")) return tuning().wait_probe;
+  if (!strcmp(key, "batch_persistent")) return tuning().batch_persistent;
   return -1;
 }
 

@@ -1,9 +1,12 @@
 // Many periodic fields of uneven sizes and their particle sets advanced
 // together: one bin sort over the concatenated particles of all fields (global
-// bin = first bin of the field + bin in the field), one brick-kernel launch
-// over the bricks of all fields per Heun step, and the sequence of steps
-// captured once in a CUDA graph and replayed.  Not part of the paper's method:
-// a way of running many of its problems at once on one device.
+// bin = first bin of the field + bin in the field) and one pass over the
+// bricks of all fields per Heun step.  By default all steps run in one
+// cooperative persistent launch (the sort's phases and the brick pass
+// separated by grid-wide barriers); otherwise a launch per phase and step.
+// With use_graph the solves of all fields and the steps are captured once in a
+// CUDA graph and replayed.  Not part of the paper's method: a way of running
+// many of its problems at once on one device.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -30,7 +33,7 @@ struct ps_plan {
   // workspace layout: byte offsets
   size_t off_args = 0, off_bintab = 0, off_binbase = 0, off_counts = 0, off_offsets = 0,
          off_scan = 0, off_binof = 0, off_rank = 0, off_pos = 0, off_ids = 0, off_quant = 0,
-         ws_bytes = 0;
+         off_sync = 0, ws_bytes = 0;
   std::vector<unsigned char> h_args;
   std::vector<BinField> h_bintab;
   // captured step sequence and what it was captured for
@@ -77,6 +80,7 @@ void layout(ps_plan* p) {
   p->off_rank = take(np * sizeof(int32_t));
   p->off_pos = take(3 * np * sizeof(double));
   p->off_ids = take(np * sizeof(int64_t));
+  p->off_sync = take(8 * sizeof(unsigned));
   size_t quant = 0;
   if (ps_spline_coeffs_workspace_size(&p->grids[0], 3, p->coef_t) > 0)
     for (int f = 0; f < p->nfields; ++f)
@@ -225,6 +229,27 @@ ps_status upload_tables(ps_plan* p, void* ws, cudaStream_t st) {
   return rc;
 }
 
+// All nsteps Heun steps in one cooperative launch (its counters and barrier
+// words cleared first, on the same stream).
+ps_status enqueue_persistent(ps_plan* p, double* pos, int64_t* ids, int nsteps, void* ws,
+                             int32_t* status, cudaStream_t st) {
+  if (p->np_total == 0 || nsteps == 0) return PS_OK;
+  ps_status rc = check_cuda(cudaMemsetAsync(at<int32_t>(ws, p->off_counts), 0,
+                                            sizeof(int32_t) * (p->total_bins + 1), st),
+                            "batch counts memset");
+  if (!rc)
+    rc = check_cuda(cudaMemsetAsync(at<unsigned>(ws, p->off_sync), 0, 8 * sizeof(unsigned), st),
+                    "batch barrier memset");
+  if (rc) return rc;
+  return staged_batch_persistent(
+      p->coef_t, at<char>(ws, p->off_args), at<int32_t>(ws, p->off_binbase),
+      at<BinField>(ws, p->off_bintab), p->nfields, p->total_bins, p->np_total, nsteps, pos, ids,
+      at<double>(ws, p->off_pos), ids ? at<int64_t>(ws, p->off_ids) : nullptr,
+      at<int32_t>(ws, p->off_binof), at<int32_t>(ws, p->off_rank),
+      at<int32_t>(ws, p->off_counts), at<int32_t>(ws, p->off_offsets),
+      at<int32_t>(ws, p->off_scan), status, at<unsigned>(ws, p->off_sync), p->smem, st);
+}
+
 // One Heun step of every particle of every field: bin sort (positions and
 // labels copied into bin order in the workspace), then the brick kernel,
 // which writes the updated positions back in that order.
@@ -263,65 +288,80 @@ extern "C" ps_status ps_batch_run(ps_plan* p, const ps_batch_field* fields, int 
   }
   cudaStream_t st = as_stream(stream);
   ps_status rc;
-  if (solve) {
+  const bool persistent = tuning().batch_persistent != 0;
+  // the solves of all fields (into the workspace's quantisation area when the
+  // storage needs an intermediate)
+  auto enqueue_solves = [&](cudaStream_t s) -> ps_status {
     const size_t qbytes = p->ws_bytes - p->off_quant;
     for (int f = 0; f < p->nfields; ++f) {
       const bool inter = ps_spline_coeffs_workspace_size(&p->grids[f], 3, p->coef_t) > 0;
-      rc = ps_spline_coeffs(&p->grids[f], 3, PS_F32, fields[f].field, p->coef_t, fields[f].coef,
-                            fields[f].scale, inter ? at<char>(ws, p->off_quant) : nullptr,
-                            inter ? qbytes : 0, stream);
-      if (rc) return rc;
+      ps_status r = ps_spline_coeffs(&p->grids[f], 3, PS_F32, fields[f].field, p->coef_t,
+                                     fields[f].coef, fields[f].scale,
+                                     inter ? at<char>(ws, p->off_quant) : nullptr,
+                                     inter ? qbytes : 0, s);
+      if (r) return r;
     }
+    return PS_OK;
+  };
+  auto enqueue_steps = [&](cudaStream_t s) -> ps_status {
+    if (persistent) return enqueue_persistent(p, pos, ids, nsteps, ws, status, s);
+    for (int k = 0; k < nsteps; ++k) {
+      ps_status r = enqueue_step(p, pos, ids, ws, status, s);
+      if (r) return r;
+    }
+    return PS_OK;
+  };
+  const bool steps = nsteps > 0 && p->np_total > 0;
+  if (!use_graph) {
+    if (solve && (rc = enqueue_solves(st))) return rc;
+    if (!steps) return PS_OK;
+    if ((rc = build_tables(p, fields, pos, ids, vel_out, dt, ws, status))) return rc;
+    if ((rc = upload_tables(p, ws, st))) return rc;
+    return enqueue_steps(st);
   }
-  if (nsteps == 0 || p->np_total == 0) return PS_OK;
+  if (!solve && !steps) return PS_OK;
 
   std::vector<uintptr_t> key = {(uintptr_t)pos, (uintptr_t)ids, (uintptr_t)vel_out,
-                                (uintptr_t)ws, (uintptr_t)status, (uintptr_t)nsteps};
+                                (uintptr_t)ws, (uintptr_t)status, (uintptr_t)nsteps,
+                                (uintptr_t)(solve ? 1 : 0), (uintptr_t)(persistent ? 1 : 0)};
   uint64_t dtbits;
   memcpy(&dtbits, &dt, sizeof(dt));
   key.push_back((uintptr_t)dtbits);
   for (int f = 0; f < p->nfields; ++f) {
     key.push_back((uintptr_t)fields[f].coef);
     key.push_back((uintptr_t)fields[f].scale);
+    key.push_back((uintptr_t)(solve ? fields[f].field : nullptr));
   }
-  const bool fresh = !(use_graph && p->exec && key == p->key);
-  if (fresh) {
+  if (p->exec && key == p->key) return check_cuda(cudaGraphLaunch(p->exec, st), "graph launch");
+  if (steps) {
     if ((rc = build_tables(p, fields, pos, ids, vel_out, dt, ws, status))) return rc;
     if ((rc = upload_tables(p, ws, st))) return rc;
   }
-  if (!use_graph) {
-    for (int s = 0; s < nsteps; ++s)
-      if ((rc = enqueue_step(p, pos, ids, ws, status, st))) return rc;
-    return PS_OK;
+  if (p->exec) {
+    cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
   }
-  if (fresh) {
-    if (p->exec) {
-      cudaGraphExecDestroy(p->exec);
-      p->exec = nullptr;
-    }
-    if (!p->cap &&
-        (rc = check_cuda(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking),
-                         "capture stream")))
-      return rc;
-    if ((rc = staged_batch_launch(p->coef_t, nullptr, nullptr, 0, 0, p->smem, true, p->cap)))
-      return rc;
-    if ((rc = check_cuda(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal),
-                         "begin capture")))
-      return rc;
-    ps_status step_rc = PS_OK;
-    for (int s = 0; s < nsteps && !step_rc; ++s)
-      step_rc = enqueue_step(p, pos, ids, ws, status, p->cap);
-    cudaGraph_t graph = nullptr;
-    rc = check_cuda(cudaStreamEndCapture(p->cap, &graph), "end capture");
-    if (step_rc || rc) {
-      if (graph) cudaGraphDestroy(graph);
-      return step_rc ? step_rc : rc;
-    }
-    rc = check_cuda(cudaGraphInstantiate(&p->exec, graph, 0), "graph instantiate");
-    cudaGraphDestroy(graph);
-    if (rc) return rc;
-    p->key = key;
+  if (!p->cap &&
+      (rc = check_cuda(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking),
+                       "capture stream")))
+    return rc;
+  if ((rc = staged_batch_launch(p->coef_t, nullptr, nullptr, 0, 0, p->smem, true, p->cap)))
+    return rc;
+  if ((rc = check_cuda(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal),
+                       "begin capture")))
+    return rc;
+  ps_status cap_rc = solve ? enqueue_solves(p->cap) : PS_OK;
+  if (!cap_rc && steps) cap_rc = enqueue_steps(p->cap);
+  cudaGraph_t graph = nullptr;
+  rc = check_cuda(cudaStreamEndCapture(p->cap, &graph), "end capture");
+  if (cap_rc || rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return cap_rc ? cap_rc : rc;
   }
+  rc = check_cuda(cudaGraphInstantiate(&p->exec, graph, 0), "graph instantiate");
+  cudaGraphDestroy(graph);
+  if (rc) return rc;
+  p->key = key;
   return check_cuda(cudaGraphLaunch(p->exec, st), "graph launch");
 }
 

@@ -11,22 +11,10 @@
 // then starts at the scan, and the scatter takes ranks from the counters.
 #include <mutex>
 
-#include "ps_internal.cuh"
+#include "bin_device.cuh"
 
 namespace ps {
 namespace {
-
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
-__device__ __forceinline__ int bin_of_position(const GridArgs& g, const BrickArgs& b,
-                                               double x, double y, double z, bool& ok) {
-  const int key = bin_of_coords(b, brick_coord(g, b, x, 0), brick_coord(g, b, y, 1),
-                                brick_coord(g, b, z, 2));
-  ok = key >= 0;
-  return ok ? key : 0;
-}
 
 // Ranks inside runs of equal keys in consecutive lanes: the run's first lane,
 // the lane's offset in the run and the run's length.  Particles stored in the
@@ -43,9 +31,9 @@ __device__ __forceinline__ void run_ranks(int key, int lane, int& first, int& wi
   len = (after ? __ffs(after) - 1 : 32) - first;
 }
 
-// Each warp takes kCountUnroll consecutive groups of 32 particles per trip and
-// issues all their position loads before any index arithmetic.
-constexpr int kCountUnroll = 4;
+// (bin_count_kernel: each warp takes kCountUnroll consecutive groups of 32
+// particles per trip and issues all their position loads before any index
+// arithmetic.)
 
 __global__ void bin_count_kernel(GridArgs g, BrickArgs b, int64_t np,
                                  const double* __restrict__ pos, int32_t* __restrict__ bin_of,
@@ -95,58 +83,13 @@ __global__ void bin_count_kernel(GridArgs g, BrickArgs b, int64_t np,
 __global__ void scan_tile_sums(const int32_t* __restrict__ in, int64_t n,
                                int32_t* __restrict__ tile_sums) {
   __shared__ int32_t red[kScanThreads / 32];
-  const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
-  int32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t idx = tile0 + (int64_t)i * kScanThreads + threadIdx.x;
-    if (idx < n) s += in[idx];
-  }
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int32_t t = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
-    tile_sums[blockIdx.x] = t;
-  }
-}
-
-// Block-wide exclusive scan of one value per thread; returns the block total.
-__device__ int32_t block_exclusive_scan(int32_t v, int32_t& excl) {
-  __shared__ int32_t warp_tot[kScanThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int32_t incl = v;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += o;
-  }
-  if (lane == 31) warp_tot[warp] = incl;
-  __syncthreads();
-  int32_t woff = 0, total = 0;
-  for (int w = 0; w < kScanThreads / 32; ++w) {
-    const int32_t t = warp_tot[w];
-    if (w < warp) woff += t;
-    total += t;
-  }
-  __syncthreads();
-  excl = woff + incl - v;
-  return total;
+  scan_tile_sum<kScanThreads>(in, n, blockIdx.x, tile_sums, red);
 }
 
 // Phase 2: one block scans the tile sums in place (any count, running carry).
 __global__ void scan_tile_offsets(int32_t* tile_sums, int64_t ntiles) {
-  int32_t carry = 0;
-  for (int64_t base = 0; base < ntiles; base += kScanThreads) {
-    const int64_t idx = base + threadIdx.x;
-    const int32_t v = idx < ntiles ? tile_sums[idx] : 0;
-    int32_t excl;
-    const int32_t tot = block_exclusive_scan(v, excl);
-    if (idx < ntiles) tile_sums[idx] = carry + excl;
-    carry += tot;
-  }
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  scan_tile_offsets_block<kScanThreads>(tile_sums, ntiles, warp_tot);
 }
 
 // Phase 3: scan inside each tile, add the tile offset; out has n+1 entries.
@@ -156,29 +99,8 @@ __global__ void scan_tile_offsets(int32_t* tile_sums, int64_t ntiles) {
 __global__ void scan_tiles(const int32_t* __restrict__ in, int64_t n,
                            const int32_t* __restrict__ tile_off, int32_t* __restrict__ out,
                            int64_t clamp) {
-  const int64_t tile0 = (int64_t)blockIdx.x * kScanTile;
-  // each thread takes kScanItems consecutive elements
-  int32_t v[kScanItems];
-  int32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t idx = tile0 + (int64_t)threadIdx.x * kScanItems + i;
-    v[i] = idx < n ? in[idx] : 0;
-    s += v[i];
-  }
-  int32_t excl;
-  const int32_t tot = block_exclusive_scan(s, excl);
-  int32_t run = tile_off[blockIdx.x] + excl;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t idx = tile0 + (int64_t)threadIdx.x * kScanItems + i;
-    if (idx < n) out[idx] = clamp < 0 ? run : (int32_t)min(max((int64_t)run, (int64_t)0), clamp);
-    run += v[i];
-  }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-    const int32_t last = tile_off[blockIdx.x] + tot;
-    out[n] = clamp < 0 ? last : (int32_t)min(max((int64_t)last, (int64_t)0), clamp);
-  }
+  __shared__ int32_t warp_tot[kScanThreads / 32];
+  scan_tile<kScanThreads>(in, n, tile_off, out, clamp, blockIdx.x, gridDim.x, warp_tot);
 }
 
 __global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
@@ -189,30 +111,8 @@ __global__ void bin_scatter_kernel(int64_t np, const double* __restrict__ pos,
                                    double* __restrict__ pos_sorted,
                                    const int64_t* __restrict__ ids,
                                    int64_t* __restrict__ ids_sorted) {
-  // kCountUnroll particles per thread and trip: the dependent loads (bin,
-  // offset, then the payload) of several particles are in flight together
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < np;
-       p0 += stride * kCountUnroll) {
-    int64_t slot[kCountUnroll];
-#pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
-      const int64_t p = p0 + u * stride;
-      slot[u] = p < np ? (int64_t)offsets[bin_of[p]] + rank[p] : -1;
-    }
-#pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
-      const int64_t p = p0 + u * stride;
-      if (slot[u] < 0) continue;
-      if (perm) perm[slot[u]] = p;
-      if (pos_sorted) {
-        pos_sorted[slot[u]] = pos[p];
-        pos_sorted[np + slot[u]] = pos[np + p];
-        pos_sorted[2 * np + slot[u]] = pos[2 * np + p];
-      }
-      if (ids_sorted) ids_sorted[slot[u]] = ids[p];
-    }
-  }
+  scatter_range(np, pos, bin_of, rank, offsets, perm, pos_sorted, ids, ids_sorted,
+                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Scatter for bins counted by an earlier kernel (bin_run's `counted`), which
@@ -301,42 +201,10 @@ __global__ void bin_count_batch_kernel(const BinField* __restrict__ tab, int nfi
                                        int64_t np, const double* __restrict__ pos,
                                        int32_t* __restrict__ bin_of, int32_t* __restrict__ rank,
                                        int32_t* __restrict__ counts, int32_t* status) {
-  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t warp_start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane;
-  for (int64_t base = warp_start; base < np; base += stride) {
-    const int64_t p = base + lane;
-    const bool valid = p < np;
-    int key = -1 - lane;
-    if (valid) {
-      int lo = 0, hi = nfields;
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (tab[mid].pbase <= p) lo = mid;
-        else hi = mid;
-      }
-      if (tab[lo].chunk > 0) {
-        // a sparse field: runs of particles in storage order
-        key = tab[lo].bin_base + (int)((p - tab[lo].pbase) / tab[lo].chunk);
-      } else {
-        bool ok;
-        key = tab[lo].bin_base +
-              bin_of_position(tab[lo].g, tab[lo].b, pos[p], pos[np + p], pos[2 * np + p], ok);
-        if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
-      }
-    }
-    const unsigned peers = __match_any_sync(FULL, key);
-    const int leader = __ffs(peers) - 1;
-    const int within = __popc(peers & ((1u << lane) - 1));
-    int basev = 0;
-    if (valid && lane == leader) basev = atomicAdd(&counts[key], __popc(peers));
-    basev = __shfl_sync(peers, basev, leader);
-    if (valid) {
-      bin_of[p] = key;
-      rank[p] = basev + within;
-    }
-  }
+  batch_count_range(tab, nfields, np, pos, bin_of, rank, counts, status,
+                    (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane,
+                    (int64_t)gridDim.x * blockDim.x);
 }
 
 // Grid of a grid-stride kernel: enough blocks for the work, at most a full

@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "bin_device.cuh"
 #include "staged.cuh"
 
 namespace ps {
@@ -872,15 +873,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == 2 ? 6 : 7)
   brick_phased<Tc, NC, MODE, true>(a, blockIdx.x, smem_a128, &a);
 }
 
-// Many fields in one launch: block b handles global brick b; the field is the
-// last f with bin_base[f] <= b, and its parameters are copied to shared memory.
+// Global brick b of a many-field batch: the field is the last f with
+// bin_base[f] <= b; its arguments are copied to shared memory (sa), its tensor
+// map stays in the global table.  Empty bins return at once.  Every thread of
+// the block calls.
 template <typename Tc, int NC, int MODE>
-__global__ void __launch_bounds__(kThreads, 5)
-    interp_staged_batch(const StagedArgs* __restrict__ tab, const int* __restrict__ bin_base,
-                        int nfields) {
-  extern __shared__ __align__(128) float4 smem_b128[];
-  __shared__ StagedArgs sa;
-  const int b = blockIdx.x;
+__device__ __forceinline__ void batch_brick(const StagedArgs* __restrict__ tab,
+                                            const int* __restrict__ bin_base, int nfields,
+                                            int b, float4* smem, StagedArgs& sa) {
   // field 0's offsets are the global offsets: empty bins leave at once
   const int32_t* goffs = tab[0].offs;
   if (goffs[b] >= goffs[b + 1]) return;
@@ -906,7 +906,141 @@ __global__ void __launch_bounds__(kThreads, 5)
                    : "memory");
   }
   __syncthreads();
-  brick_phased<Tc, NC, MODE, true>(sa, b - bin_base[lo], smem_b128, tab + lo);
+  brick_phased<Tc, NC, MODE, true>(sa, b - bin_base[lo], smem, tab + lo);
+}
+
+// Many fields in one launch: block b handles global brick b.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(kThreads, 5)
+    interp_staged_batch(const StagedArgs* __restrict__ tab, const int* __restrict__ bin_base,
+                        int nfields) {
+  extern __shared__ __align__(128) float4 smem_b128[];
+  __shared__ StagedArgs sa;
+  batch_brick<Tc, NC, MODE>(tab, bin_base, nfields, blockIdx.x, smem_b128, sa);
+}
+
+// ----------------------------------------------------- persistent batch ----
+// All Heun steps of a many-field batch in one cooperative launch: per step
+// the counting pass, the three scan phases, the scatter into bin order (and
+// the counters cleared for the next step), then the bricks of all fields;
+// the phases are separated by grid-wide barriers.  Each barrier is an arrival
+// counter and a generation word; a wait gives up after about 2^31 clocks,
+// sets the block-stop word and PS_DEV_TIMEOUT, and every block leaves at its
+// next barrier.  sync[3] is a word nothing sets: with wait_probe > 0 (a test
+// knob) every block waits on it after the first barrier, for that many
+// clocks, so that the give-up path runs.  sync[4] is the brick pass's claim
+// counter: blocks take kClaim consecutive global bins at a time.
+struct BatchRun {
+  const StagedArgs* tab;   // per-field brick-kernel arguments
+  const int* bin_base;     // nfields + 1
+  const BinField* bintab;  // per-field binning table
+  int nfields;
+  int nsteps;
+  int64_t total_bins, np;
+  double* pos;             // the caller's positions (bin order after a step)
+  int64_t* ids;
+  double* pos_s;           // copies in bin order (workspace)
+  int64_t* ids_s;
+  int32_t* bin_of;
+  int32_t* rank;
+  int32_t* counts;         // total_bins + 1, zero at launch
+  int32_t* offsets;        // total_bins + 1
+  int32_t* scan_tmp;
+  int32_t* status;
+  unsigned* sync;          // arrivals, generation, stop, never set, claims; zero at launch
+  int wait_probe;
+};
+
+__device__ __forceinline__ bool grid_barrier(const BatchRun& r, int& nbar) {
+  __shared__ int go;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vs = r.sync;
+    bool ok = vs[2] == 0;
+    if (ok) {
+      const unsigned gen = vs[1];
+      __threadfence();
+      if (atomicAdd(&r.sync[0], 1u) + 1u == gridDim.x) {
+        atomicExch(&r.sync[0], 0u);
+        __threadfence();
+        atomicAdd(&r.sync[1], 1u);
+      } else {
+        const long long t0 = clock64();
+        while (vs[1] == gen) {
+          if (vs[2]) {
+            ok = false;
+            break;
+          }
+          if (clock64() - t0 > (1ll << 31)) {
+            if (atomicExch(&r.sync[2], 1u) == 0u) flag_status(r.status, PS_DEV_TIMEOUT, nbar);
+            ok = false;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      __threadfence();
+      if (ok && r.wait_probe > 0 && nbar == 0) {
+        const long long t0 = clock64();
+        while (vs[3] == 0 && clock64() - t0 <= r.wait_probe) __nanosleep(100);
+        if (vs[3] == 0) {
+          if (atomicExch(&r.sync[2], 1u) == 0u) flag_status(r.status, PS_DEV_TIMEOUT, nbar);
+          ok = false;
+        }
+      }
+    }
+    go = ok ? 1 : 0;
+  }
+  __syncthreads();
+  ++nbar;
+  return go != 0;
+}
+
+constexpr int kClaim = 4;  // global bins per claim of the persistent brick pass
+
+template <typename Tc>
+__global__ void __launch_bounds__(kThreads, 5) batch_persistent(const __grid_constant__ BatchRun r) {
+  extern __shared__ __align__(128) float4 smem_bp[];
+  __shared__ StagedArgs sa;
+  __shared__ int32_t scan_sh[kThreads / 32];
+  __shared__ int64_t claim;
+  int nbar = 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  const int64_t ntiles = (r.total_bins + kScanTile - 1) / kScanTile;
+  for (int step = 0; step < r.nsteps; ++step) {
+    batch_count_range(r.bintab, r.nfields, r.np, r.pos, r.bin_of, r.rank, r.counts, r.status,
+                      gt - lane, gs);
+    if (!grid_barrier(r, nbar)) return;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+      scan_tile_sum<kThreads>(r.counts, r.total_bins, t, r.scan_tmp, scan_sh);
+    if (!grid_barrier(r, nbar)) return;
+    if (blockIdx.x == 0) scan_tile_offsets_block<kThreads>(r.scan_tmp, ntiles, scan_sh);
+    if (!grid_barrier(r, nbar)) return;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+      scan_tile<kThreads>(r.counts, r.total_bins, r.scan_tmp, r.offsets, -1, t, ntiles,
+                          scan_sh);
+    if (!grid_barrier(r, nbar)) return;
+    scatter_range(r.np, r.pos, r.bin_of, r.rank, r.offsets, nullptr, r.pos_s, r.ids,
+                  r.ids ? r.ids_s : nullptr, gt, gs);
+    for (int64_t i = gt; i <= r.total_bins; i += gs) r.counts[i] = 0;
+    if (gt == 0) atomicExch(&r.sync[4], 0u);
+    if (!grid_barrier(r, nbar)) return;
+    // bricks claimed kClaim at a time (their costs vary with their particles)
+    while (true) {
+      if (threadIdx.x == 0) claim = (int64_t)atomicAdd(&r.sync[4], 1u) * kClaim;
+      __syncthreads();
+      const int64_t b0 = claim;
+      __syncthreads();
+      if (b0 >= r.total_bins) break;
+      for (int64_t b = b0; b < b0 + kClaim && b < r.total_bins; ++b) {
+        batch_brick<Tc, 3, 2>(r.tab, r.bin_base, r.nfields, (int)b, smem_bp, sa);
+        __syncthreads();  // sa and the shared memory are refilled by the next brick
+      }
+    }
+    if (!grid_barrier(r, nbar)) return;
+  }
 }
 
 // ------------------------------------------------- thread per particle ----
@@ -1391,6 +1525,69 @@ ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_b
       kern<<<(unsigned)total_bins, kThreads, smem, st>>>(
           static_cast<const StagedArgs*>(d_tab), d_bin_base, nfields);
       return check_launch("interp_staged_batch");
+    }
+  });
+}
+
+// All nsteps Heun steps of a batch in one cooperative launch (batch_persistent):
+// a grid of every block the device holds at once.  counts and sync must be
+// zero at launch (the caller clears them on the same stream).
+ps_status staged_batch_persistent(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
+                                  const BinField* d_bintab, int nfields, int64_t total_bins,
+                                  int64_t np, int nsteps, double* pos, int64_t* ids,
+                                  double* pos_s, int64_t* ids_s, int32_t* bin_of, int32_t* rank,
+                                  int32_t* counts, int32_t* offsets, int32_t* scan_tmp,
+                                  int32_t* status, unsigned* sync, size_t smem,
+                                  cudaStream_t st) {
+  return with_coef_type(coef_t, [&](auto tag) -> ps_status {
+    using Tc = decltype(tag);
+    if constexpr (std::is_same<Tc, double>::value) {
+      return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
+    } else {
+      auto kern = batch_persistent<Tc>;
+      if (smem > 48 * 1024) {
+        ps_status rc = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "persistent batch smem attribute");
+        if (rc) return rc;
+      }
+      int per_sm = 0;
+      ps_status rc = check_cuda(
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem),
+          "persistent batch occupancy");
+      if (rc) return rc;
+      if (per_sm < 1) return fail(PS_ERR_UNSUPPORTED, "persistent batch kernel does not fit an SM");
+      BatchRun r;
+      r.tab = static_cast<const StagedArgs*>(d_tab);
+      r.bin_base = d_bin_base;
+      r.bintab = d_bintab;
+      r.nfields = nfields;
+      r.nsteps = nsteps;
+      r.total_bins = total_bins;
+      r.np = np;
+      r.pos = pos;
+      r.ids = ids;
+      r.pos_s = pos_s;
+      r.ids_s = ids_s;
+      r.bin_of = bin_of;
+      r.rank = rank;
+      r.counts = counts;
+      r.offsets = offsets;
+      r.scan_tmp = scan_tmp;
+      r.status = status;
+      r.sync = sync;
+      r.wait_probe = tuning().wait_probe;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(per_sm * sm_count()));
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return check_cuda(cudaLaunchKernelEx(&cfg, kern, r), "persistent batch launch");
     }
   });
 }

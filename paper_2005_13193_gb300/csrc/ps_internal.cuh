@@ -76,6 +76,8 @@ struct Tuning {
   int node_tma = 1;           // PS_F32X4 halos by tensor copy
   int solve_xw = 0;           // x extent of a strided-pass block (0: default)
   int wait_probe = 0;         // test knob: clocks of a wait that cannot complete
+  int batch_persistent = 1;   // batched steps: one cooperative launch (1) or a launch
+                              // per phase and step (0)
 };
 Tuning& tuning();
 int sm_count();
@@ -123,6 +125,15 @@ constexpr int kBatchChunk = 128;
 ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
                               int nfields, int64_t total_bins, size_t smem, bool prepare,
                               cudaStream_t st);
+// All nsteps Heun steps of a batch in one cooperative launch (counts and sync,
+// four words, zero at launch).
+ps_status staged_batch_persistent(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
+                                  const BinField* d_bintab, int nfields, int64_t total_bins,
+                                  int64_t np, int nsteps, double* pos, int64_t* ids,
+                                  double* pos_s, int64_t* ids_s, int32_t* bin_of, int32_t* rank,
+                                  int32_t* counts, int32_t* offsets, int32_t* scan_tmp,
+                                  int32_t* status, unsigned* sync, size_t smem,
+                                  cudaStream_t st);
 
 // -------------------------------------------------------------- device ----
 

@@ -81,6 +81,72 @@ def test_batch_equals_per_field_runs(dtype):
         ps.ps_tune_set("brick_kernel", old)
 
 
+def _run_batch(sizes, nps, dtype, seed, nsteps, dt, use_graph, status=None):
+    flds = _fields(sizes, seed, dtype)
+    pos0 = _positions(nps, seed + 100)
+    plan = ps.BatchPlan([(n,) * 3 for n in sizes], nps, coef_dtype=dtype)
+    pos = torch.from_numpy(pos0.copy()).to(DEV)
+    ids = torch.arange(plan.np_total, dtype=torch.int64, device=DEV)
+    vel = torch.empty((3, plan.np_total), dtype=torch.float32, device=DEV)
+    plan.run([(f, sf) for f, sf in flds], pos, nsteps, dt, solve=True, ids=ids, vel=vel,
+             use_graph=use_graph, status=status)
+    return (_by_label(pos.cpu().numpy(), ids.cpu().numpy()),
+            _by_label(vel.cpu().numpy(), ids.cpu().numpy()))
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, ps.F32X4, ps.BF16X4])
+def test_persistent_launch_equals_launch_per_step(dtype):
+    # All steps in one cooperative launch (the default: the sort's phases and
+    # the brick pass separated by grid-wide barriers) give every particle the
+    # bits of a launch per phase and step, eager or replayed from a graph that
+    # also holds the solves.
+    sizes, nps = [16, 24, 32, 48, 32, 64], [1000, 50000, 3000, 20000, 0, 2000]
+    old = ps.ps_tune_get("batch_persistent")
+    try:
+        out = {}
+        for persistent in (1, 0):
+            ps.ps_tune_set("batch_persistent", persistent)
+            for use_graph in (False, True):
+                st = torch.zeros(4, dtype=torch.int32, device=DEV)
+                out[(persistent, use_graph)] = _run_batch(sizes, nps, dtype, 800, 4, 4e-3,
+                                                          use_graph, st)
+                assert ps.ps_status_read(st)[0] == 0
+    finally:
+        ps.ps_tune_set("batch_persistent", old)
+    ref = out[(0, False)]
+    for k, (x, v) in out.items():
+        np.testing.assert_array_equal(x, ref[0])
+        np.testing.assert_array_equal(v, ref[1])
+
+
+def test_persistent_barrier_wait_gives_up():
+    # The test knob "wait_probe" makes every block, after the first grid
+    # barrier, wait on a word that nothing sets, bounded by that many clocks:
+    # the wait gives up, the status word reads PS_DEV_TIMEOUT, every block
+    # leaves at its next barrier and the launch returns.  The device stays
+    # usable: the next run, without the knob, matches a launch per step.
+    sizes, nps = [16, 32, 24], [3000, 20000, 5000]
+    old = ps.ps_tune_get("wait_probe")
+    try:
+        ps.ps_tune_set("wait_probe", 20000)
+        st = torch.zeros(4, dtype=torch.int32, device=DEV)
+        _run_batch(sizes, nps, torch.float32, 900, 3, 4e-3, False, st)
+        code, _, _, count = ps.ps_status_read(st)
+        assert code == ps._abi.PS_DEV_TIMEOUT and count > 0
+    finally:
+        ps.ps_tune_set("wait_probe", old)
+    st = torch.zeros(4, dtype=torch.int32, device=DEV)
+    got = _run_batch(sizes, nps, torch.float32, 900, 3, 4e-3, False, st)
+    assert ps.ps_status_read(st)[0] == 0
+    old_p = ps.ps_tune_get("batch_persistent")
+    try:
+        ps.ps_tune_set("batch_persistent", 0)
+        ref = _run_batch(sizes, nps, torch.float32, 900, 3, 4e-3, False)
+    finally:
+        ps.ps_tune_set("batch_persistent", old_p)
+    np.testing.assert_array_equal(got[0], ref[0])
+
+
 def test_graph_replay_equals_eager_and_is_reused():
     sizes = [32, 64, 48]
     nps = [20000, 100000, 7000]
