@@ -128,6 +128,23 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
     tuning().solve_xw = (int)value;
     return PS_OK;
   }
+  if (!strcmp(key, "solve_stream")) {
+    if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "solve_stream is 0 or 1");
+    tuning().solve_stream = (int)value;
+    return PS_OK;
+  }
+  if (!strcmp(key, "solve_zt")) {
+    if (value != 0 && value != 16 && value != 32 && value != 64 && value != 128 && value != 256)
+      return fail(PS_ERR_INVALID_ARG, "solve_zt is 0, 16, 32, 64, 128 or 256");
+    tuning().solve_zt = (int)value;
+    return PS_OK;
+  }
+  if (!strcmp(key, "solve_stages")) {
+    if (value != 0 && (value < 2 || value > 4))
+      return fail(PS_ERR_INVALID_ARG, "solve_stages is 0, 2, 3 or 4");
+    tuning().solve_stages = (int)value;
+    return PS_OK;
+  }
   if (!strcmp(key, "node_tma")) {
     if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "node_tma is 0 or 1");
     tuning().node_tma = (int)value;
@@ -152,6 +169,9 @@ extern "C" int64_t ps_tune_get(const char* key) {
   if (!strcmp(key, "brick_min_stage")) return tuning().brick_min_stage;
   if (!strcmp(key, "node_tma")) return tuning().node_tma;
   if (!strcmp(key, "solve_xw")) return tuning().solve_xw;
+  if (!strcmp(key, "solve_stream")) return tuning().solve_stream;
+  if (!strcmp(key, "solve_zt")) return tuning().solve_zt;
+  if (!strcmp(key, "solve_stages")) return tuning().solve_stages;
   if (!strcmp(key, "wait_probe")) return tuning().wait_probe;
   if (!strcmp(key, "batch_persistent")) return tuning().batch_persistent;
   return -1;

@@ -81,10 +81,9 @@ void layout(ps_plan* p) {
   p->off_pos = take(3 * np * sizeof(double));
   p->off_ids = take(np * sizeof(int64_t));
   p->off_sync = take(8 * sizeof(unsigned));
-  size_t quant = 0;
-  if (ps_spline_coeffs_workspace_size(&p->grids[0], 3, p->coef_t) > 0)
-    for (int f = 0; f < p->nfields; ++f)
-      quant = std::max(quant, ps_spline_coeffs_workspace_size(&p->grids[f], 3, p->coef_t));
+  size_t quant = 0;  // the largest intermediate a field's solve takes
+  for (int f = 0; f < p->nfields; ++f)
+    quant = std::max(quant, ps_spline_coeffs_workspace_size(&p->grids[f], 3, p->coef_t));
   p->off_quant = take(quant);
   p->ws_bytes = align_up(c.used, 256);
 }

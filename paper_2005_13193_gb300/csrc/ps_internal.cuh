@@ -75,6 +75,9 @@ struct Tuning {
   int brick_min_stage = 8;    // per-brick kernel: fewer particles skip the halo
   int node_tma = 1;           // PS_F32X4 halos by tensor copy
   int solve_xw = 0;           // x extent of a strided-pass block (0: default)
+  int solve_stream = 1;       // FP32 solves in two streamed passes (y-x, then z)
+  int solve_zt = 0;           // columns per block of the streamed z pass (0: default)
+  int solve_stages = 0;       // shared-memory stages of the streamed y-x pass (0: 3)
   int wait_probe = 0;         // test knob: clocks of a wait that cannot complete
   int batch_persistent = 1;   // batched steps: one cooperative launch (1) or a launch
                               // per phase and step (0)

@@ -221,28 +221,13 @@ __device__ __forceinline__ int skew_l(int e, int L, float inv_L) {
 // without bank conflicts; chunk carries move between lanes by shuffles.
 // padded = 0: dst is an unpadded view.  padded = 1: dst is the padded
 // coefficient array; every line is written to all its periodic images.
-// One periodic line of nx values held by a warp in its skewed shared buffer
-// (element e at e + e/L): the causal and anti-causal recursions with their
-// chunk carries, times the gain.  With QUANT the values are divided by the
-// line's power-of-two scale, which is returned.
-template <typename T, int LMAX, bool QUANT>
-__device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z, T gain) {
+// The recursions of one periodic line held by a warp, lane l holding its
+// chunk v[0..len) (the line's values [l L, l L + len)): causal and
+// anti-causal, each with its chunk carries by shuffles; before the gain.
+template <typename T, int LMAX>
+__device__ __forceinline__ void line_recur(T (&v)[LMAX], int len, int lane, T z) {
   const unsigned FULL = 0xffffffffu;
   const T thr = Thr<T>::v;
-  const int s0 = lane * L;
-  int len = nx - s0;
-  len = len < 0 ? 0 : (len > L ? L : len);
-  T* mine = buf + lane * (L + 1);
-  T v[LMAX];
-  if (len == LMAX) {
-#pragma unroll
-    for (int i = 0; i < LMAX; ++i) v[i] = mine[i];
-  } else {
-#pragma unroll
-    for (int i = 0; i < LMAX; ++i)
-      if (i < len) v[i] = mine[i];
-  }
-
   const T y = chunk_causal<T, LMAX>(v, len, z);
   const T a = chunk_zlen<T>(len);
   T carry = T(0), fac = T(1);
@@ -278,6 +263,28 @@ __device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z
   }
   if (wrapped) carry = carry / (T(1) - fac);
   chunk_anticausal_fix<T, LMAX>(v, len, carry, z);
+}
+
+// One periodic line of nx values held by a warp in its skewed shared buffer
+// (element e at e + e/L): the recursions, times the gain.  With QUANT the
+// values are divided by the line's power-of-two scale, which is returned.
+template <typename T, int LMAX, bool QUANT>
+__device__ __forceinline__ float line_solve(T* buf, int nx, int L, int lane, T z, T gain) {
+  const unsigned FULL = 0xffffffffu;
+  const int s0 = lane * L;
+  int len = nx - s0;
+  len = len < 0 ? 0 : (len > L ? L : len);
+  T* mine = buf + lane * (L + 1);
+  T v[LMAX];
+  if (len == LMAX) {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) v[i] = mine[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) v[i] = mine[i];
+  }
+  line_recur<T, LMAX>(v, len, lane, z);
 
   float sc = 1.f;
   if (QUANT) {
@@ -429,6 +436,346 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, NodeT
     }
 }
 
+// ------------------------------------------------------- two-pass solve ----
+// The x and y solves of every (c, z) plane in one pass, the z solve in a
+// second pass that writes the padded layout (planar, or (u, v, w, 0)
+// nodes): the array is read twice and written twice instead of three times
+// (the periodic images, a few faces, are copied after).
+// A thread streams one pencil along the pass's axis in chunks of kSB lines:
+//  * the causal recursion runs in order, from the state that a zero-start
+//    sweep over the pencil's last kSB lines (chunk 0, read first) leaves;
+//  * the anti-causal values of chunk q start from the value at chunk q+1's
+//    first line of an anti-causal sweep entering chunk q+1's end at zero,
+//    sum_i z^i y_i over chunk q+1's causal values y; in chunk q+1's raw
+//    values g and the causal state s entering it that is
+//    s A_len + sum_j g_j W_len[j], formed as the chunk arrives;
+//  * the last chunk enters from the pencil's first line (that value, taken
+//    from chunk 1) and hands its exact start on to the chunk before it.
+// Each truncation drops terms below |z|^kSB = 7.2e-10 of the values beyond
+// it (a geometric tail, at most 1e-9 relative): far below FP32 rounding, as
+// the carry threshold of the chunked passes above.
+// Chunks arrive through a ring of S shared-memory stages filled by 16-byte
+// cp.async copies, S - 1 chunks ahead of the one in use (the wait is
+// cp.async.wait_group's: no spinning); a thread keeps the causal values of
+// the chunk before in registers.
+constexpr int kSB = 16;
+
+// W_len[j] = sum_{i=j}^{len-1} z^(2i-j), A_len = sum_{i<len} z^(2i+1) for
+// len = 1..kSB (FP64 sums of the powers of z on the host).
+__constant__ float c_sb_w[kSB + 1][kSB];
+__constant__ float c_sb_a[kSB + 1];
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Chunk q of a streamed pencil of n >= 2 kSB lines: q = 0 is the warm-up
+// (the last kSB lines), q >= 1 the lines [(q - 1) kSB, min(q kSB, n)).
+__device__ __forceinline__ int sb_start(int q, int n) { return q == 0 ? n - kSB : (q - 1) * kSB; }
+__device__ __forceinline__ int sb_len(int q, int n) {
+  const int r = n - (q - 1) * kSB;
+  return q == 0 ? kSB : (r < kSB ? r : kSB);
+}
+
+// The value entering the end of the chunk before this one: this chunk's raw
+// values g (len of them), the causal state s entering it, a0 the value
+// entering its own end.  Explicitly rounded operations keep every instance
+// bit-identical.
+__device__ __forceinline__ float sb_lookahead(const float (&g)[kSB], int len, float s, float a0) {
+  float a;
+  if (len == kSB) {  // every chunk but a pencil's last: weights by constant index
+    a = __fmul_rn(s, c_sb_a[kSB]);
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) a = __fmaf_rn(g[j], c_sb_w[kSB][j], a);
+    return __fmaf_rn(zpow<float>(kSB), a0, a);
+  }
+  a = __fmul_rn(s, c_sb_a[len]);
+#pragma unroll
+  for (int j = 0; j < kSB; ++j)
+    if (j < len) a = __fmaf_rn(g[j], c_sb_w[len][j], a);
+  return __fmaf_rn(zpow<float>(len), a0, a);
+}
+// The causal recursion over a chunk, in place, from state s (updated).
+__device__ __forceinline__ void sb_causal(float (&g)[kSB], int len, float z, float& s) {
+  float y = s;
+  if (len == kSB) {
+#pragma unroll
+    for (int j = 0; j < kSB; ++j) g[j] = y = __fmaf_rn(z, y, g[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kSB; ++j)
+      if (j < len) g[j] = y = __fmaf_rn(z, y, g[j]);
+  }
+  s = y;
+}
+
+// One pencil per thread, n >= 2 kSB lines, every thread of the block in
+// step: copy(q) issues the block's copies of chunk q into stage q % S,
+// read(q, g) takes this thread's raw values of chunk q from its stage,
+// emit(q, y, len, w) runs the anti-causal recursion over chunk q's causal
+// values from w and writes them, after(q, len) follows every emit (it may
+// hold a block barrier).
+template <int S, typename Copy, typename Read, typename Emit, typename After>
+__device__ __forceinline__ void sb_stream(int n, float z, Copy copy, Read read, Emit emit,
+                                          After after) {
+  const int nq = (n + kSB - 1) / kSB;
+#pragma unroll
+  for (int q = 0; q < S - 1; ++q) {
+    if (q <= nq) copy(q);
+    cp_async_commit();
+  }
+  int next = S - 1;
+  auto fetch = [&](int q, float (&g)[kSB]) {
+    cp_async_wait<S - 2>();
+    __syncthreads();  // chunk q is in; every thread has read chunk q - 1
+    if (next <= nq) copy(next);  // into chunk q - 1's stage
+    cp_async_commit();
+    ++next;
+    read(q, g);
+  };
+  float A[kSB], B[kSB];
+  float s = 0.f;
+  fetch(0, A);
+  sb_causal(A, kSB, z, s);  // the warm-up leaves the state entering line 0
+  fetch(1, B);
+  const float s_wrap = sb_lookahead(B, kSB, s, 0.f);  // the value at line 0
+  sb_causal(B, kSB, z, s);
+  int q = 2;
+  auto step = [&](float (&g)[kSB], float (&yp)[kSB]) {
+    const int len = sb_len(q, n);
+    fetch(q, g);
+    const float a = sb_lookahead(g, len, s, q == nq ? s_wrap : 0.f);
+    emit(q - 1, yp, kSB, a);
+    after(q - 1, kSB);
+    sb_causal(g, len, z, s);
+    if (q == nq) {
+      emit(q, g, len, s_wrap);
+      after(q, len);
+    }
+    ++q;
+  };
+  for (;;) {
+    step(A, B);
+    if (q > nq) break;
+    step(B, A);
+    if (q > nq) break;
+  }
+  cp_async_wait<0>();
+}
+
+// Pass 1: one block per (c, z) plane of an unpadded array, nx = 32 LMAX
+// (LMAX = 4, 8 or 16), one thread per x column, streaming y.  A stage holds
+// kSB rows with x at x + 4 floor(x / 32): the 16-byte copies stay aligned, a
+// lane's chunk of LMAX values is read and written as 16-byte accesses on
+// distinct banks, and a warp's column reads fall on distinct banks.  Each
+// chunk's rows are solved along x in place (a warp per row), then every
+// thread takes its column through the y recursions and stores its outputs,
+// coalesced across the warp.
+template <int LMAX, int S>
+__global__ void __launch_bounds__(32 * LMAX, 1024 / (32 * LMAX)) solve_xy_stream(
+    const float* src, View sv, float* dst, View dv, int ny, int nz, float z, float gain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NX = 32 * LMAX, T = NX, RP = NX + NX / 8;  // padded row
+  constexpr int PR = NX / 4;                                // 16-byte pieces per row
+  float* stage = reinterpret_cast<float*>(smem_raw);       // [S][kSB][RP]
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int c = blockIdx.x / nz, zz = blockIdx.x - c * nz;
+  const float* sp = src + sv.off + c * sv.sc + zz * sv.sz;
+  float* dp = dst + dv.off + c * dv.sc + zz * dv.sz + t;
+  const int xcol = t + 4 * (t >> 5);                        // this thread's column
+  const int xchunk = lane * LMAX + 4 * ((lane * LMAX) >> 5);  // this lane's chunk
+
+  auto copy = [&](int q) {
+    const int len = sb_len(q, ny);
+    const float* g = sp + sb_start(q, ny) * sv.sy;
+    float* st = stage + (q % S) * kSB * RP;
+    const int m = t % PR;
+#pragma unroll
+    for (int j = t / PR; j < kSB; j += T / PR)
+      if (j < len) cp_async16(st + j * RP + 4 * m + 4 * (m >> 3), g + j * sv.sy + 4 * m);
+  };
+  auto read = [&](int q, float (&g)[kSB]) {
+    const int len = sb_len(q, ny);
+    float* st = stage + (q % S) * kSB * RP;
+    // the chunk's rows along x, in place
+    for (int j = warp; j < len; j += T / 32) {
+      float* row = st + j * RP + xchunk;
+      float v[LMAX];
+#pragma unroll
+      for (int e = 0; e < LMAX; e += 4) {  // a chunk never straddles 32 values
+        const float4 f = *reinterpret_cast<const float4*>(row + e);
+        v[e] = f.x;
+        v[e + 1] = f.y;
+        v[e + 2] = f.z;
+        v[e + 3] = f.w;
+      }
+      line_recur<float, LMAX>(v, LMAX, lane, z);
+#pragma unroll
+      for (int e = 0; e < LMAX; e += 4)
+        *reinterpret_cast<float4*>(row + e) =
+            make_float4(__fmul_rn(gain, v[e]), __fmul_rn(gain, v[e + 1]),
+                        __fmul_rn(gain, v[e + 2]), __fmul_rn(gain, v[e + 3]));
+    }
+    __syncthreads();
+    const float* col = st + xcol;
+    if (len == kSB) {
+#pragma unroll
+      for (int j = 0; j < kSB; ++j) g[j] = col[j * RP];
+    } else {
+#pragma unroll
+      for (int j = 0; j < kSB; ++j) g[j] = j < len ? col[j * RP] : 0.f;
+    }
+  };
+  auto emit = [&](int qo, float (&y)[kSB], int len, float w) {
+    float* o = dp + sb_start(qo, ny) * dv.sy;
+    if (len == kSB) {
+#pragma unroll
+      for (int i = kSB - 1; i >= 0; --i) {
+        w = __fmaf_rn(z, w, y[i]);
+        o[i * dv.sy] = __fmul_rn(gain, w);
+      }
+    } else {
+#pragma unroll
+      for (int i = kSB - 1; i >= 0; --i)
+        if (i < len) {
+          w = __fmaf_rn(z, w, y[i]);
+          o[i * dv.sy] = __fmul_rn(gain, w);
+        }
+    }
+  };
+  sb_stream<S>(ny, z, copy, read, emit, [](int, int) {});
+}
+
+// Pass 2 output addressing: element (c, Pz, Py, P) at off + c sc + Pz sz +
+// Py sy + P sx floats (planar: sx = 1; nodes: c is the float in the node,
+// sx = 4).
+struct OutView {
+  int64_t off, sc, sz, sy, sx;
+};
+
+// Pass 2: ZT columns of x at one y per block, one thread per (column,
+// component), streaming z from an unpadded array (nx a multiple of 4, rows
+// 16-byte aligned) into the interior of the padded layout (Pz = z + 1,
+// Py = y + 1, P = x + 1; the periodic images follow in fill_images).
+// LPC = 1: planar, the component from blockIdx.z.  LPC = 4: nodes, four
+// consecutive threads per column hold u, v, w and the zero fourth value (it
+// reads u's values and stores zeros), so a warp stores eight whole nodes
+// (128 bytes) per line.  A stage holds kSB lines of the block's columns per
+// component (component blocks padded by 8 floats: the three components of a
+// column fall on distinct banks).
+template <int LPC, int ZT, int S>
+__global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_z_stream(
+    const float* src, View sv, float* dst, OutView ov, int nx, int ny, int nz, float z,
+    float gain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NCB = LPC == 1 ? 1 : 3;               // components per block
+  constexpr int CS = kSB * ZT + (LPC == 1 ? 0 : 8);   // one component's lines
+  constexpr int T = ZT * LPC, PL = ZT / 4;            // 16-byte pieces per line
+  float* stage = reinterpret_cast<float*>(smem_raw);  // [S][NCB][CS]
+  const int t = threadIdx.x;
+  const int col = t / LPC, x0 = blockIdx.x * ZT, x = x0 + col;
+  const int k = LPC == 1 ? 0 : t % LPC, c0 = LPC == 1 ? (int)blockIdx.z : 0;
+  const bool pad = LPC == 4 && k == 3;
+  const float* sp = src + sv.off + c0 * sv.sc + blockIdx.y * sv.sy + x0;
+  const int sz = (int)ov.sz;  // < 2^31 elements per padded plane
+  float* op = dst + ov.off + (c0 + k) * ov.sc + (blockIdx.y + 1) * ov.sy + (x + 1) * ov.sx + sz;
+  const float og = pad ? 0.f : gain;
+  const bool xin = 4 * (t % PL) < nx - x0;
+
+  // piece p = t + T u of a chunk: line (p / PL) % kSB of component
+  // p / (PL kSB), 16 bytes at 4 (p % PL)
+  auto copy = [&](int q) {
+    const int len = sb_len(q, nz), r0 = sb_start(q, nz);
+    float* st = stage + (q % S) * NCB * CS;
+    if (!xin) return;
+#pragma unroll
+    for (int p = t; p < NCB * kSB * PL; p += T) {
+      const int m = p % PL, j = (p / PL) % kSB, kk = p / (PL * kSB);
+      if (j < len)
+        cp_async16(st + kk * CS + j * ZT + 4 * m, sp + kk * sv.sc + (r0 + j) * sv.sz + 4 * m);
+    }
+  };
+  auto read = [&](int q, float (&g)[kSB]) {
+    const int len = sb_len(q, nz);
+    const float* st = stage + (q % S) * NCB * CS + (pad ? 0 : k) * CS + col;
+    if (len == kSB) {
+#pragma unroll
+      for (int j = 0; j < kSB; ++j) g[j] = st[j * ZT];
+    } else {
+#pragma unroll
+      for (int j = 0; j < kSB; ++j) g[j] = j < len ? st[j * ZT] : 0.f;
+    }
+  };
+  auto emit = [&](int qo, float (&y)[kSB], int len, float w) {
+    if (x >= nx) return;
+    float* rp = op + (int64_t)sb_start(qo, nz) * sz;
+    if (len == kSB) {
+#pragma unroll
+      for (int i = kSB - 1; i >= 0; --i) {
+        w = __fmaf_rn(z, w, y[i]);
+        rp[i * sz] = pad ? 0.f : __fmul_rn(og, w);
+      }
+    } else {
+#pragma unroll
+      for (int i = kSB - 1; i >= 0; --i)
+        if (i < len) {
+          w = __fmaf_rn(z, w, y[i]);
+          rp[i * sz] = pad ? 0.f : __fmul_rn(og, w);
+        }
+    }
+  };
+  sb_stream<S>(nz, z, copy, read, emit, [](int, int) {});
+}
+
+// The periodic images of a padded array whose interior is written: along
+// each axis P = 0, n + 1, n + 2 holds the value at P = n, 1, 2 (node
+// padded_to_node(P) + 1), and the row tail [nx + 3, rx) is zero.  E is
+// float (planar, component blockIdx.y, stride cs) or float4 (nodes).
+// fill_x_images: one thread per interior row, its three x images and tail.
+template <typename E>
+__global__ void fill_x_images(E* a, int64_t cs, int64_t rx, int nx, int ny, int nz) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int64_t)nz * ny) return;
+  const int Pz = 1 + (int)(r / ny), Py = 1 + (int)(r % ny);
+  E* row = a + blockIdx.y * cs + ((int64_t)Pz * (ny + 3) + Py) * rx;
+  const E e0 = row[nx], e1 = row[1], e2 = row[2];
+  row[0] = e0;
+  row[nx + 1] = e1;
+  row[nx + 2] = e2;
+  for (int64_t P = nx + 3; P < rx; ++P) row[P] = E{};
+}
+// fill_yz_images: one block per row with Pz or Py in {0, n + 1, n + 2},
+// copied whole from its interior row (every P mapped to the interior too,
+// so it reads nothing fill_x_images writes).
+template <typename E>
+__global__ void fill_yz_images(E* a, int64_t cs, int64_t rx, int nx, int ny, int nz) {
+  const int b = blockIdx.x, my = ny + 3;
+  int Pz, Py;
+  if (b < 3 * my) {
+    const int gi = b / my;
+    Pz = gi == 0 ? 0 : nz + gi;
+    Py = b % my;
+  } else {
+    const int b2 = b - 3 * my, gi = b2 % 3;
+    Pz = 1 + b2 / 3;
+    Py = gi == 0 ? 0 : ny + gi;
+  }
+  const int sz_ = padded_to_node(Pz, nz) + 1, sy_ = padded_to_node(Py, ny) + 1;
+  E* base = a + blockIdx.y * cs;
+  E* row = base + ((int64_t)Pz * my + Py) * rx;
+  const E* srow = base + ((int64_t)sz_ * my + sy_) * rx;
+  for (int64_t P = threadIdx.x; P < rx; P += blockDim.x)
+    row[P] = P < nx + 3 ? srow[padded_to_node((int)P, nx) + 1] : E{};
+}
+
 // ------------------------------------------------------------------ host ----
 
 struct StridedCfg {
@@ -562,6 +909,106 @@ ps_status launch_x_node4(const float* src, View sv, NodeT* dst, float* scale4, i
   return launch_x_node4_l<64>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
 }
 
+// Two-pass solve: applies to FP32 fields and FP32 coefficients (planar or
+// nodes) when a row is 128, 256 or 512 values (a warp's chunks of 4, 8 or
+// 16) and every streamed pencil holds two chunks (tune "solve_stream" 0
+// keeps the three passes).  It needs the unpadded FP32 intermediate in the
+// workspace.
+bool stream_grid(const ps_grid* g) {
+  const int nx = g->n[0];
+  return (nx == 128 || nx == 256 || nx == 512) && g->n[1] >= 2 * kSB && g->n[2] >= 2 * kSB;
+}
+bool stream_solve_ok(const ps_grid* g) {
+  return tuning().solve_stream && stream_grid(g);
+}
+
+template <int LMAX, int S>
+ps_status launch_xy_stream_s(const float* src, View sv, float* dst, View dv, int ny, int nz,
+                             int ncomp, float z, float gain, cudaStream_t st) {
+  constexpr int NX = 32 * LMAX;
+  const size_t smem = (size_t)S * kSB * (NX + NX / 8) * sizeof(float);
+  auto kern = solve_xy_stream<LMAX, S>;
+  if (smem > 48 * 1024) {
+    ps_status rc = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "solve_xy_stream smem attribute");
+    if (rc) return rc;
+  }
+  kern<<<(unsigned)(ncomp * nz), NX, smem, st>>>(src, sv, dst, dv, ny, nz, z, gain);
+  return check_launch("solve_xy_stream");
+}
+
+template <int LMAX>
+ps_status launch_xy_stream_l(const float* src, View sv, float* dst, View dv, int ny, int nz,
+                             int ncomp, float z, float gain, cudaStream_t st) {
+  const int S = tuning().solve_stages > 0 ? tuning().solve_stages : 3;
+  if (S == 2) return launch_xy_stream_s<LMAX, 2>(src, sv, dst, dv, ny, nz, ncomp, z, gain, st);
+  if (S == 4) return launch_xy_stream_s<LMAX, 4>(src, sv, dst, dv, ny, nz, ncomp, z, gain, st);
+  return launch_xy_stream_s<LMAX, 3>(src, sv, dst, dv, ny, nz, ncomp, z, gain, st);
+}
+
+// nx = 128, 256 or 512 (stream_grid)
+ps_status launch_xy_stream(const float* src, View sv, float* dst, View dv, int nx, int ny,
+                           int nz, int ncomp, float z, float gain, cudaStream_t st) {
+  if (nx == 128) return launch_xy_stream_l<4>(src, sv, dst, dv, ny, nz, ncomp, z, gain, st);
+  if (nx == 256) return launch_xy_stream_l<8>(src, sv, dst, dv, ny, nz, ncomp, z, gain, st);
+  return launch_xy_stream_l<16>(src, sv, dst, dv, ny, nz, ncomp, z, gain, st);
+}
+
+template <int LPC, int ZT>
+ps_status launch_z_stream_t(const float* src, View sv, float* dst, OutView ov, int nx, int ny,
+                            int nz, int cblocks, float z, float gain, cudaStream_t st) {
+  constexpr int S = 4;
+  const size_t smem = (size_t)S * (LPC == 1 ? 1 : 3) * (kSB * ZT + (LPC == 1 ? 0 : 8)) * 4;
+  auto kern = solve_z_stream<LPC, ZT, S>;
+  if (smem > 48 * 1024) {
+    ps_status rc = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "solve_z_stream smem attribute");
+    if (rc) return rc;
+  }
+  dim3 grid((unsigned)((nx + ZT - 1) / ZT), (unsigned)ny, (unsigned)cblocks);
+  kern<<<grid, ZT * LPC, smem, st>>>(src, sv, dst, ov, nx, ny, nz, z, gain);
+  return check_launch("solve_z_stream");
+}
+
+// cblocks: components (planar, LPC = 1) or 1 (nodes, LPC = 4).
+template <int LPC>
+ps_status launch_z_stream(const float* src, View sv, float* dst, OutView ov, int nx, int ny,
+                          int nz, int cblocks, float z, float gain, cudaStream_t st) {
+  // measured at 512^3: planar 256 columns per block, nodes 64 (256 threads)
+  const int zt = tuning().solve_zt > 0 ? tuning().solve_zt : (LPC == 1 ? 256 : 64);
+  if (LPC == 1) {
+    if (zt <= 32)
+      return launch_z_stream_t<1, 32>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+    if (zt <= 64)
+      return launch_z_stream_t<1, 64>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+    if (zt <= 128)
+      return launch_z_stream_t<1, 128>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+    return launch_z_stream_t<1, 256>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+  }
+  if (zt <= 16)
+    return launch_z_stream_t<4, 16>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+  if (zt <= 32)
+    return launch_z_stream_t<4, 32>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+  return launch_z_stream_t<4, 64>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+}
+
+// The periodic images and row tails of a padded array whose interior is
+// written; ncomp arrays cs elements apart.
+template <typename E>
+ps_status launch_fill_images(E* a, int64_t cs, int64_t rx, int nx, int ny, int nz, int ncomp,
+                             cudaStream_t st) {
+  const int64_t rows = (int64_t)nz * ny;
+  fill_x_images<E><<<dim3((unsigned)((rows + 255) / 256), (unsigned)ncomp), 256, 0, st>>>(
+      a, cs, rx, nx, ny, nz);
+  ps_status rc = check_launch("fill_x_images");
+  if (rc) return rc;
+  fill_yz_images<E><<<dim3((unsigned)(3 * (ny + 3) + 3 * nz), (unsigned)ncomp), 128, 0, st>>>(
+      a, cs, rx, nx, ny, nz);
+  return check_launch("fill_yz_images");
+}
+
 // Fill the constant tables of z^k once per device (the host's FP64 z).
 ps_status upload_zpow(double zd) {
   static std::mutex mu;
@@ -579,6 +1026,21 @@ ps_status upload_zpow(double zd) {
   for (int k = 0; k <= 64; ++k) pf[k] = (float)pd[k];
   if ((rc = check_cuda(cudaMemcpyToSymbol(c_zpow_d, pd, sizeof(pd)), "z powers (FP64)"))) return rc;
   if ((rc = check_cuda(cudaMemcpyToSymbol(c_zpow_f, pf, sizeof(pf)), "z powers (FP32)"))) return rc;
+  // the streamed passes' look-ahead weights (index 0 unused)
+  float w[kSB + 1][kSB] = {}, a[kSB + 1] = {};
+  for (int len = 1; len <= kSB; ++len) {
+    double sa = 0.0;
+    for (int i = 0; i < len; ++i) sa += pd[2 * i + 1];
+    a[len] = (float)sa;
+    for (int j = 0; j < len; ++j) {
+      double sw = 0.0;
+      for (int i = j; i < len; ++i) sw += pd[2 * i - j];
+      w[len][j] = (float)sw;
+    }
+  }
+  if ((rc = check_cuda(cudaMemcpyToSymbol(c_sb_w, w, sizeof(w)), "look-ahead weights"))) return rc;
+  if ((rc = check_cuda(cudaMemcpyToSymbol(c_sb_a, a, sizeof(a)), "look-ahead state weights")))
+    return rc;
   done[dev] = true;
   return PS_OK;
 }
@@ -596,6 +1058,44 @@ View interior_view(const ps_grid* g, int64_t rx) {
   View v = padded_view(g, rx);
   v.off = v.sz + v.sy + 1;
   return v;
+}
+
+// FP32 field -> padded planar FP32 coefficients: the x-y pass into the
+// unpadded workspace, the z pass into the padded layout's interior, then its
+// periodic images.
+ps_status run_solve_stream_planar(const ps_grid* g, int ncomp, const float* field, float* inter,
+                                  float* coef, int64_t rx, cudaStream_t st) {
+  const double zd = sqrt(3.0) - 2.0;
+  if (ps_status zrc = upload_zpow(zd)) return zrc;
+  const float z = (float)zd, gain = (float)(-6.0 * zd);
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  View fv = unpadded_view(g), pv = padded_view(g, rx);
+  ps_status rc = launch_xy_stream(field, fv, inter, fv, nx, ny, nz, ncomp, z, gain, st);
+  if (rc) return rc;
+  OutView ov{pv.off, pv.sc, pv.sz, pv.sy, 1};
+  rc = launch_z_stream<1>(inter, fv, coef, ov, nx, ny, nz, ncomp, z, gain, st);
+  if (rc) return rc;
+  return launch_fill_images<float>(coef, pv.sc, rx, nx, ny, nz, ncomp, st);
+}
+
+// FP32 field -> FP32 nodes: the x-y pass into the unpadded workspace, the z
+// pass over the three components writing (u, v, w, 0) nodes, then the
+// periodic images.
+ps_status run_solve_stream_node4(const ps_grid* g, const float* field, float* inter,
+                                 float4* out, int64_t rx, cudaStream_t st) {
+  const double zd = sqrt(3.0) - 2.0;
+  if (ps_status zrc = upload_zpow(zd)) return zrc;
+  const float z = (float)zd, gain = (float)(-6.0 * zd);
+  const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  View fv = unpadded_view(g);
+  ps_status rc = launch_xy_stream(field, fv, inter, fv, nx, ny, nz, 3, z, gain, st);
+  if (rc) return rc;
+  const int64_t my = ny + 3;
+  OutView ov{0, 1, my * rx * 4, rx * 4, 4};
+  rc = launch_z_stream<4>(inter, fv, reinterpret_cast<float*>(out), ov, nx, ny, nz, 1, z, gain,
+                          st);
+  if (rc) return rc;
+  return launch_fill_images<float4>(out, 0, rx, nx, ny, nz, 1, st);
 }
 
 // y pass (src -> dst), z pass (in place on dst), x pass (dst -> out).
@@ -650,7 +1150,7 @@ extern "C" size_t ps_spline_coeffs_workspace_size(const ps_grid* grid, int ncomp
                                                   ps_dtype coef_t) {
   if (!grid || ncomp < 1) return 0;
   if (coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_F32X4 || coef_t == PS_BF16X4 ||
-      coef_t == PS_F16X4)
+      coef_t == PS_F16X4 || (coef_t == PS_F32 && validate_grid(grid) == PS_OK && stream_grid(grid)))
     return align_up((size_t)ncomp * (size_t)grid_volume(grid) * sizeof(float), 256) + 256;
   return 0;
 }
@@ -682,8 +1182,15 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
   const float* ff = static_cast<const float*>(field);
   const double* fd = static_cast<const double*>(field);
 
+  const bool aligned16 = (reinterpret_cast<uintptr_t>(field) & 15) == 0;
   if (coef_t == PS_F32) {
     float* c = static_cast<float*>(coef);
+    // the two-pass solve when the workspace holds its intermediate, else
+    // the three passes in place
+    const size_t inter_bytes = (size_t)ncomp * (size_t)grid_volume(grid) * sizeof(float);
+    if (field_t == PS_F32 && stream_solve_ok(grid) && aligned16 && ws && ws_bytes >= inter_bytes &&
+        (reinterpret_cast<uintptr_t>(ws) & 255) == 0)
+      return run_solve_stream_planar(grid, ncomp, ff, static_cast<float*>(ws), c, rx, st);
     return field_t == PS_F32
                ? run_solve<float, float, float, false>(grid, ncomp, ff, fv, c, iv, c, pv,
                                                        nullptr, 1, st)
@@ -705,6 +1212,8 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
   float* inter = static_cast<float*>(ws);
   if (coef_t == PS_F32X4) {
     float4* c = static_cast<float4*>(coef);
+    if (field_t == PS_F32 && stream_solve_ok(grid) && aligned16)
+      return run_solve_stream_node4(grid, ff, inter, c, rx, st);
     return field_t == PS_F32 ? run_solve_node4<float>(grid, ff, fv, inter, c, nullptr, rx, st)
                              : run_solve_node4<double>(grid, fd, fv, inter, c, nullptr, rx, st);
   }

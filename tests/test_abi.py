@@ -48,7 +48,11 @@ def test_workspace_queries_on_host():
     ws_rk = lib.ps_rk2_workspace_size(ctypes.byref(g), brick, np_)
     assert ws_rk >= 24 * np_ + 8 * np_
     assert lib.ps_rk2_workspace_size(ctypes.byref(g), None, np_) == 0
-    assert lib.ps_spline_coeffs_workspace_size(ctypes.byref(g), 3, _abi.PS_F32) == 0
+    # planar FP32: the two-pass solve's unpadded intermediate where it applies
+    # (optional: without it the three passes run in place)
+    assert lib.ps_spline_coeffs_workspace_size(ctypes.byref(g), 3, _abi.PS_F32) >= 3 * 4 * 512 ** 3
+    g_odd = make_grid((37, 20, 9))
+    assert lib.ps_spline_coeffs_workspace_size(ctypes.byref(g_odd), 3, _abi.PS_F32) == 0
     assert lib.ps_spline_coeffs_workspace_size(ctypes.byref(g), 3, _abi.PS_BF16) >= 3 * 4 * 512 ** 3
 
 

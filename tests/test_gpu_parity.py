@@ -75,6 +75,43 @@ def test_spline_coeffs_long_pencils(n):
         assert np.abs(got - ref).max() <= coef_tol(field), shape
 
 
+@pytest.mark.parametrize("n", [(128, 40, 50), (256, 33, 47), (128, 32, 700), (512, 48, 32),
+                               (128, 700, 34)])
+def test_streamed_solve_matches_oracle(n):
+    # The two-pass solve (x-y pass, then the z pass into the padded layout's
+    # interior, then its periodic images) streams y and z in 16-line chunks:
+    # ragged last chunks, every row width it takes (128, 256, 512), long
+    # pencils.  It meets the bar against the oracle, planar and node storage
+    # hold the same bits, and the z pass's columns per block and the x-y
+    # pass's stages change no bit.
+    field = synth.random_field(n, ncomp=3, seed=sum(n) + 7)
+    ref32 = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
+    f = torch.from_numpy(field.astype(np.float32)).to(DEV)
+    keys = ("solve_stream", "solve_zt", "solve_stages")
+    old = {k: ps.ps_tune_get(k) for k in keys}
+    try:
+        ps.ps_tune_set("solve_stream", 1)
+        s32 = ps.SplineField.from_field(f, torch.float32)
+        p32 = s32.padded()
+        assert np.abs(p32.cpu().numpy() - ref32).max() <= coef_tol(field)
+        assert torch.count_nonzero(s32.coef[..., n[0] + 3:]) == 0  # the row tail
+        p4 = ps.SplineField.from_field(f, ps.F32X4)
+        assert torch.equal(p4.padded(), p32)
+        assert torch.count_nonzero(p4.coef[..., 3]) == 0
+        for zt, stages in ((16, 2), (64, 4), (256, 3)):
+            ps.ps_tune_set("solve_zt", zt)
+            ps.ps_tune_set("solve_stages", stages)
+            assert torch.equal(ps.SplineField.from_field(f, torch.float32).padded(), p32)
+            assert torch.equal(ps.SplineField.from_field(f, ps.F32X4).padded(), p32)
+        # the three-pass solve agrees within the rounding bar
+        ps.ps_tune_set("solve_stream", 0)
+        p3 = ps.SplineField.from_field(f, torch.float32).padded()
+        assert (p3 - p32).abs().max().item() <= coef_tol(field)
+    finally:
+        for k, v in old.items():
+            ps.ps_tune_set(k, v)
+
+
 # ---------------------------------------------------------------- binning ----
 
 @pytest.mark.parametrize("n,brick", [((32, 32, 32), (8, 8, 8)), ((37, 20, 9), (8, 4, 5)),
