@@ -130,6 +130,12 @@ int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
  *  "node_tma" 0 or 1 (default 1): halos of node coefficients by tensor copy.
  *  "solve_xw" 0, 8, 16 or 32 (0 = default 16): x extent of a block of the
  *     strided spline passes.
+ *  "solve_stream" 0 or 1 (default 1): FP32 solves in two streamed passes
+ *     where they apply (ps_spline_coeffs).
+ *  "solve_zt" 0, 16, 32, 64, 128 or 256 (0 = default: 256 planar, 64
+ *     nodes): x columns per block of the streamed z pass.
+ *  "solve_stages" 0, 2, 3 or 4 (0 = default 3): chunks in flight + 1 in the
+ *     streamed x-y pass.
  *  "batch_persistent" 0 or 1 (default 1): ps_batch_run runs all steps in one
  *     cooperative persistent launch (1) or a launch per phase and step (0).
  *  "wait_probe" in [0, 2^30] (default 0), a test knob: > 0 makes every
@@ -160,6 +166,14 @@ ps_status ps_status_read(const int32_t* status, int32_t* host_out, void* stream)
 /*   Arithmetic is FP64 when coef_t is PS_F64, else FP32.                   */
 /*   scale: required for BF16/F16 (per x-line power-of-two scale), else     */
 /*   ignored.  field and coef must not overlap.  ncomp in [1, 16].          */
+/*   ws: ps_spline_coeffs_workspace_size bytes, 256-byte aligned; required  */
+/*   for the 16-bit and node forms.  For PS_F32 it is nonzero when nx is    */
+/*   128, 256 or 512 and ny, nz >= 32: given it (and a 16-byte aligned F32  */
+/*   field) the solve takes two streamed passes (x and y of every plane,    */
+/*   then z), which truncate each periodic recursion's look-ahead at 16     */
+/*   lines (terms below 7.2e-10 of the values skipped, under FP32           */
+/*   rounding); without it the three passes run in place.  PS_F32X4 takes   */
+/*   the two passes on the same grids.                                      */
 /* ------------------------------------------------------------------------ */
 size_t ps_spline_coeffs_workspace_size(const ps_grid* grid, int ncomp,
                                        ps_dtype coef_t);

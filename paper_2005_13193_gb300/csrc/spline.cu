@@ -18,10 +18,12 @@
 // 1e-12 (FP32) or 1e-24 (FP64) after a chunk or two, where the sum stops, so
 // every pencil is read once and written once.
 //
-// Passes: y, then z (strided: threads along x read coalesced rows), then x
-// (one warp per row, staged through shared memory), which writes the padded
-// N+3 layout with periodic ghosts and, for BF16/FP16, a power-of-two scale per
-// x-line.
+// FP32 coefficients of FP32 fields on rows of 128, 256 or 512 values take two
+// streamed passes (x and y of every plane, then z; see below).  Otherwise
+// three passes: y, then z (strided: threads along x read coalesced rows),
+// then x (one warp per row, staged through shared memory), which writes the
+// padded N+3 layout with periodic ghosts and, for BF16/FP16, a power-of-two
+// scale per x-line.
 #include <mutex>
 
 #include "ps_internal.cuh"
