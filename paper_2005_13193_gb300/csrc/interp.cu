@@ -510,21 +510,39 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
     const int lx = (signed char)(w & 0xff), ly = (signed char)((w >> 8) & 0xff),
               lz = (signed char)((w >> 16) & 0xff);
     const float4* hp = halo + (lz + kh) * PS + ly * Sx + lx + q;
+    if constexpr (NC == 3 && !GRAD) {
+      // u and v as one packed pair (two FP32 FMAs per instruction, each
+      // rounded as fmaf), w alone
+      float2 auv = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
+      for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 v = hp[2 * kk * PS + j * Sx];
-        const float vv[3] = {v.x, v.y, v.z};
-        const float w = f4get(by, j) * bz[kk];
+        for (int j = 0; j < 4; ++j) {
+          const float4 v = hp[2 * kk * PS + j * Sx];
+          const float w = f4get(by, j) * bz[kk];
+          auv = __ffma2_rn(make_float2(w, w), make_float2(v.x, v.y), auv);
+          acc[2] = fmaf(w, v.z, acc[2]);
+        }
+      }
+      acc[0] = auv.x;
+      acc[1] = auv.y;
+    } else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
-        if (GRAD) {
-          const float wy = f4get(dby, j) * bz[kk], wz = f4get(by, j) * dbz[kk];
+      for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            accy[c] = fmaf(wy, vv[c], accy[c]);
-            accz[c] = fmaf(wz, vv[c], accz[c]);
+        for (int j = 0; j < 4; ++j) {
+          const float4 v = hp[2 * kk * PS + j * Sx];
+          const float vv[3] = {v.x, v.y, v.z};
+          const float w = f4get(by, j) * bz[kk];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
+          if (GRAD) {
+            const float wy = f4get(dby, j) * bz[kk], wz = f4get(by, j) * dbz[kk];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              accy[c] = fmaf(wy, vv[c], accy[c]);
+              accz[c] = fmaf(wz, vv[c], accz[c]);
+            }
           }
         }
       }
@@ -548,8 +566,17 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
       }
     }
   }
+  if constexpr (NC == 3) {
+    // the butterfly over the group with u and v packed (each sum rounded as
+    // the scalar one)
+    const float2 uv = group_sum2<8>(__fmul2_rn(make_float2(bxq, bxq), make_float2(acc[0], acc[1])));
+    out[0] = uv.x;
+    out[1] = uv.y;
+    out[2] = group_sum<8>(bxq * acc[2]);
+  } else {
 #pragma unroll
-  for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
+    for (int c = 0; c < NC; ++c) out[c] = group_sum<8>(bxq * acc[c]);
+  }
   if (GRAD) {
     const float dbxq = reinterpret_cast<const float*>(R.db(0))[4 * i + q];
 #pragma unroll

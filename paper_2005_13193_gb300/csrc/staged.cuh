@@ -83,6 +83,15 @@ __device__ __forceinline__ T group_sum(T v) {
   for (int d = 1; d < G; d <<= 1) v += __shfl_xor_sync(FULL, v, d);
   return v;
 }
+// The same butterfly on a packed pair: two shuffles and one packed add per
+// level, each component rounded as group_sum's.
+template <int G>
+__device__ __forceinline__ float2 group_sum2(float2 v) {
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1)
+    v = __fadd2_rn(v, make_float2(__shfl_xor_sync(FULL, v.x, d), __shfl_xor_sync(FULL, v.y, d)));
+  return v;
+}
 
 template <typename Tc>
 __device__ __forceinline__ typename AccOf<Tc>::type load_coef(const Tc* coef,
