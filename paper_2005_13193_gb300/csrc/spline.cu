@@ -25,6 +25,7 @@
 // padded N+3 layout with periodic ghosts and, for BF16/FP16, a power-of-two
 // scale per x-line.
 #include <mutex>
+#include <type_traits>
 
 #include "ps_internal.cuh"
 
@@ -656,27 +657,28 @@ __global__ void __launch_bounds__(32 * LMAX, 1024 / (32 * LMAX)) solve_xy_stream
   sb_stream<S>(ny, z, copy, read, emit, [](int, int) {});
 }
 
-// Pass 2 output addressing: element (c, Pz, Py, P) at off + c sc + Pz sz +
-// Py sy + P sx floats (planar: sx = 1; nodes: c is the float in the node,
-// sx = 4).
+// Output addressing of a line stream: element (c, line, other, x) at off +
+// c sc + line sz + other sy + x sx floats (planar: sx = 1; nodes: c is the
+// float in the node, sx = 4; into a padded layout, off points at its
+// interior).
 struct OutView {
   int64_t off, sc, sz, sy, sx;
 };
 
-// Pass 2: ZT columns of x at one y per block, one thread per (column,
-// component), streaming z from an unpadded array (nx a multiple of 4, rows
-// 16-byte aligned) into the interior of the padded layout (Pz = z + 1,
-// Py = y + 1, P = x + 1; the periodic images follow in fill_images).
-// LPC = 1: planar, the component from blockIdx.z.  LPC = 4: nodes, four
-// consecutive threads per column hold u, v, w and the zero fourth value (it
-// reads u's values and stores zeros), so a warp stores eight whole nodes
-// (128 bytes) per line.  A stage holds kSB lines of the block's columns per
-// component (component blocks padded by 8 floats: the three components of a
-// column fall on distinct banks).
+// Lines along one axis of an unpadded array (nx a multiple of 4, rows
+// 16-byte aligned): the source's line stride sv.sz, blockIdx.y the other
+// axis at stride sv.sy; ZT columns of x per block, one thread per (column,
+// component), streaming the nl lines.  It may write in place (a thread
+// reads all of its pencil's lines before it writes them).  LPC = 1: one
+// component, from blockIdx.z.  LPC = 4: nodes, four consecutive threads per
+// column hold u, v, w and the zero fourth value (it reads u's values and
+// stores zeros), so a warp stores eight whole nodes (128 bytes) per line.  A
+// stage holds kSB lines of the block's columns per component (component
+// blocks padded by 8 floats: the three components of a column fall on
+// distinct banks).
 template <int LPC, int ZT, int S>
-__global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_z_stream(
-    const float* src, View sv, float* dst, OutView ov, int nx, int ny, int nz, float z,
-    float gain) {
+__global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_line_stream(
+    const float* src, View sv, float* dst, OutView ov, int nx, int nl, float z, float gain) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NCB = LPC == 1 ? 1 : 3;               // components per block
   constexpr int CS = kSB * ZT + (LPC == 1 ? 0 : 8);   // one component's lines
@@ -687,15 +689,15 @@ __global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_z_stream(
   const int k = LPC == 1 ? 0 : t % LPC, c0 = LPC == 1 ? (int)blockIdx.z : 0;
   const bool pad = LPC == 4 && k == 3;
   const float* sp = src + sv.off + c0 * sv.sc + blockIdx.y * sv.sy + x0;
-  const int sz = (int)ov.sz;  // < 2^31 elements per padded plane
-  float* op = dst + ov.off + (c0 + k) * ov.sc + (blockIdx.y + 1) * ov.sy + (x + 1) * ov.sx + sz;
+  const int sz = (int)ov.sz;  // < 2^31 elements per plane
+  float* op = dst + ov.off + (c0 + k) * ov.sc + blockIdx.y * ov.sy + x * ov.sx;
   const float og = pad ? 0.f : gain;
   const bool xin = 4 * (t % PL) < nx - x0;
 
   // piece p = t + T u of a chunk: line (p / PL) % kSB of component
   // p / (PL kSB), 16 bytes at 4 (p % PL)
   auto copy = [&](int q) {
-    const int len = sb_len(q, nz), r0 = sb_start(q, nz);
+    const int len = sb_len(q, nl), r0 = sb_start(q, nl);
     float* st = stage + (q % S) * NCB * CS;
     if (!xin) return;
 #pragma unroll
@@ -706,7 +708,7 @@ __global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_z_stream(
     }
   };
   auto read = [&](int q, float (&g)[kSB]) {
-    const int len = sb_len(q, nz);
+    const int len = sb_len(q, nl);
     const float* st = stage + (q % S) * NCB * CS + (pad ? 0 : k) * CS + col;
     if (len == kSB) {
 #pragma unroll
@@ -718,7 +720,7 @@ __global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_z_stream(
   };
   auto emit = [&](int qo, float (&y)[kSB], int len, float w) {
     if (x >= nx) return;
-    float* rp = op + (int64_t)sb_start(qo, nz) * sz;
+    float* rp = op + (int64_t)sb_start(qo, nl) * sz;
     if (len == kSB) {
 #pragma unroll
       for (int i = kSB - 1; i >= 0; --i) {
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(ZT * LPC, 1024 / (ZT * LPC)) solve_z_stream(
         }
     }
   };
-  sb_stream<S>(nz, z, copy, read, emit, [](int, int) {});
+  sb_stream<S>(nl, z, copy, read, emit, [](int, int) {});
 }
 
 // The periodic images of a padded array whose interior is written: along
@@ -958,42 +960,43 @@ ps_status launch_xy_stream(const float* src, View sv, float* dst, View dv, int n
 }
 
 template <int LPC, int ZT>
-ps_status launch_z_stream_t(const float* src, View sv, float* dst, OutView ov, int nx, int ny,
-                            int nz, int cblocks, float z, float gain, cudaStream_t st) {
+ps_status launch_line_stream_t(const float* src, View sv, float* dst, OutView ov, int nx,
+                               int nother, int nl, int cblocks, float z, float gain,
+                               cudaStream_t st) {
   constexpr int S = 4;
   const size_t smem = (size_t)S * (LPC == 1 ? 1 : 3) * (kSB * ZT + (LPC == 1 ? 0 : 8)) * 4;
-  auto kern = solve_z_stream<LPC, ZT, S>;
+  auto kern = solve_line_stream<LPC, ZT, S>;
   if (smem > 48 * 1024) {
     ps_status rc = check_cuda(
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-        "solve_z_stream smem attribute");
+        "solve_line_stream smem attribute");
     if (rc) return rc;
   }
-  dim3 grid((unsigned)((nx + ZT - 1) / ZT), (unsigned)ny, (unsigned)cblocks);
-  kern<<<grid, ZT * LPC, smem, st>>>(src, sv, dst, ov, nx, ny, nz, z, gain);
-  return check_launch("solve_z_stream");
+  dim3 grid((unsigned)((nx + ZT - 1) / ZT), (unsigned)nother, (unsigned)cblocks);
+  kern<<<grid, ZT * LPC, smem, st>>>(src, sv, dst, ov, nx, nl, z, gain);
+  return check_launch("solve_line_stream");
 }
 
-// cblocks: components (planar, LPC = 1) or 1 (nodes, LPC = 4).
+// nother lines of nl values (the other axis at blockIdx.y); cblocks:
+// components (LPC = 1) or 1 (nodes, LPC = 4).
 template <int LPC>
-ps_status launch_z_stream(const float* src, View sv, float* dst, OutView ov, int nx, int ny,
-                          int nz, int cblocks, float z, float gain, cudaStream_t st) {
-  // measured at 512^3: planar 256 columns per block, nodes 64 (256 threads)
+ps_status launch_line_stream(const float* src, View sv, float* dst, OutView ov, int nx,
+                             int nother, int nl, int cblocks, float z, float gain,
+                             cudaStream_t st) {
+  // measured at 512^3: one component 256 columns per block, nodes 64 (256 threads)
   const int zt = tuning().solve_zt > 0 ? tuning().solve_zt : (LPC == 1 ? 256 : 64);
+#define PS_LS(L, Z) \
+  return launch_line_stream_t<L, Z>(src, sv, dst, ov, nx, nother, nl, cblocks, z, gain, st)
   if (LPC == 1) {
-    if (zt <= 32)
-      return launch_z_stream_t<1, 32>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
-    if (zt <= 64)
-      return launch_z_stream_t<1, 64>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
-    if (zt <= 128)
-      return launch_z_stream_t<1, 128>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
-    return launch_z_stream_t<1, 256>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+    if (zt <= 32) PS_LS(1, 32);
+    if (zt <= 64) PS_LS(1, 64);
+    if (zt <= 128) PS_LS(1, 128);
+    PS_LS(1, 256);
   }
-  if (zt <= 16)
-    return launch_z_stream_t<4, 16>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
-  if (zt <= 32)
-    return launch_z_stream_t<4, 32>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
-  return launch_z_stream_t<4, 64>(src, sv, dst, ov, nx, ny, nz, cblocks, z, gain, st);
+  if (zt <= 16) PS_LS(4, 16);
+  if (zt <= 32) PS_LS(4, 32);
+  PS_LS(4, 64);
+#undef PS_LS
 }
 
 // The periodic images and row tails of a padded array whose interior is
@@ -1074,8 +1077,8 @@ ps_status run_solve_stream_planar(const ps_grid* g, int ncomp, const float* fiel
   View fv = unpadded_view(g), pv = padded_view(g, rx);
   ps_status rc = launch_xy_stream(field, fv, inter, fv, nx, ny, nz, ncomp, z, gain, st);
   if (rc) return rc;
-  OutView ov{pv.off, pv.sc, pv.sz, pv.sy, 1};
-  rc = launch_z_stream<1>(inter, fv, coef, ov, nx, ny, nz, ncomp, z, gain, st);
+  OutView ov{pv.off + pv.sz + pv.sy + 1, pv.sc, pv.sz, pv.sy, 1};  // the interior
+  rc = launch_line_stream<1>(inter, fv, coef, ov, nx, ny, nz, ncomp, z, gain, st);
   if (rc) return rc;
   return launch_fill_images<float>(coef, pv.sc, rx, nx, ny, nz, ncomp, st);
 }
@@ -1093,14 +1096,37 @@ ps_status run_solve_stream_node4(const ps_grid* g, const float* field, float* in
   ps_status rc = launch_xy_stream(field, fv, inter, fv, nx, ny, nz, 3, z, gain, st);
   if (rc) return rc;
   const int64_t my = ny + 3;
-  OutView ov{0, 1, my * rx * 4, rx * 4, 4};
-  rc = launch_z_stream<4>(inter, fv, reinterpret_cast<float*>(out), ov, nx, ny, nz, 1, z, gain,
-                          st);
+  OutView ov{(my * rx + rx + 1) * 4, 1, my * rx * 4, rx * 4, 4};  // the interior
+  rc = launch_line_stream<4>(inter, fv, reinterpret_cast<float*>(out), ov, nx, ny, nz, 1, z,
+                             gain, st);
   if (rc) return rc;
   return launch_fill_images<float4>(out, 0, rx, nx, ny, nz, 1, st);
 }
 
-// y pass (src -> dst), z pass (in place on dst), x pass (dst -> out).
+// The y and z passes of the three-pass solve as line streams (FP32, an
+// unpadded intermediate with 16-byte rows, ny and nz >= 32): y from the
+// field into the intermediate (or in place), then z in place.
+bool stream3_grid(const ps_grid* g) {
+  return g->n[0] % 4 == 0 && g->n[1] >= 2 * kSB && g->n[2] >= 2 * kSB;
+}
+ps_status run_yz_streams(const ps_grid* g, int ncomp, const float* field, float* inter,
+                         float z, float gain, cudaStream_t st) {
+  const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const int64_t cs = nx * ny * nz;
+  const View yv{0, cs, nx, nx * ny};  // lines along y, the other axis z
+  const OutView yo{0, cs, nx, nx * ny, 1};
+  ps_status rc = launch_line_stream<1>(field, yv, inter, yo, (int)nx, (int)nz, (int)ny, ncomp,
+                                       z, gain, st);
+  if (rc) return rc;
+  const View zv{0, cs, nx * ny, nx};  // lines along z, the other axis y
+  const OutView zo{0, cs, nx * ny, nx, 1};
+  return launch_line_stream<1>(inter, zv, inter, zo, (int)nx, (int)ny, (int)nz, ncomp, z, gain,
+                               st);
+}
+
+// y pass (src -> dst), z pass (in place on dst), x pass (dst -> out).  With
+// FP32 throughout, an unpadded intermediate and the grid stream3_grid takes,
+// the y and z passes are line streams.
 template <typename Tin, typename T, typename Tout, bool QUANT>
 ps_status run_solve(const ps_grid* g, int ncomp, const Tin* field, View fv, T* inter,
                     View iv, Tout* out, View ov, float* scale, int padded,
@@ -1109,11 +1135,24 @@ ps_status run_solve(const ps_grid* g, int ncomp, const Tin* field, View fv, T* i
   if (ps_status zrc = upload_zpow(zd)) return zrc;
   const T z = (T)zd, gain = (T)(-6.0 * zd);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  ps_status rc = launch_strided<Tin, T>(field, fv, fv.sz, fv.sy, inter, iv, iv.sz, iv.sy,
-                                        nx, ny, nz, ncomp, z, gain, st);
-  if (rc) return rc;
-  rc = launch_strided<T, T>(inter, iv, iv.sy, iv.sz, inter, iv, iv.sy, iv.sz, nx, nz, ny,
-                            ncomp, z, gain, st);
+  ps_status rc = PS_OK;
+  bool streamed = false;
+  if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
+    const bool unpadded = iv.off == 0 && iv.sy == nx && iv.sz == (int64_t)nx * ny;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(field) | reinterpret_cast<uintptr_t>(inter)) &
+                          15) == 0;
+    if (tuning().solve_stream && stream3_grid(g) && unpadded && aligned) {
+      rc = run_yz_streams(g, ncomp, field, inter, z, gain, st);
+      streamed = true;
+    }
+  }
+  if (!streamed) {
+    rc = launch_strided<Tin, T>(field, fv, fv.sz, fv.sy, inter, iv, iv.sz, iv.sy, nx, ny, nz,
+                                ncomp, z, gain, st);
+    if (rc) return rc;
+    rc = launch_strided<T, T>(inter, iv, iv.sy, iv.sz, inter, iv, iv.sy, iv.sz, nx, nz, ny,
+                              ncomp, z, gain, st);
+  }
   if (rc) return rc;
   return launch_x<T, Tout, QUANT>(inter, iv, out, ov, scale, nx, ny, nz, ncomp, padded, z,
                                   gain, st);
@@ -1127,11 +1166,22 @@ ps_status run_solve_node4(const ps_grid* g, const Tin* field, View fv, float* in
   if (ps_status zrc = upload_zpow(zd)) return zrc;
   const float z = (float)zd, gain = (float)(-6.0 * zd);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
-  ps_status rc = launch_strided<Tin, float>(field, fv, fv.sz, fv.sy, inter, fv, fv.sz, fv.sy,
-                                            nx, ny, nz, 3, z, gain, st);
-  if (rc) return rc;
-  rc = launch_strided<float, float>(inter, fv, fv.sy, fv.sz, inter, fv, fv.sy, fv.sz, nx, nz, ny,
+  ps_status rc = PS_OK;
+  bool streamed = false;
+  if constexpr (std::is_same<Tin, float>::value) {
+    if (tuning().solve_stream && stream3_grid(g) &&
+        ((reinterpret_cast<uintptr_t>(field) | reinterpret_cast<uintptr_t>(inter)) & 15) == 0) {
+      rc = run_yz_streams(g, 3, field, inter, z, gain, st);
+      streamed = true;
+    }
+  }
+  if (!streamed) {
+    rc = launch_strided<Tin, float>(field, fv, fv.sz, fv.sy, inter, fv, fv.sz, fv.sy, nx, ny, nz,
                                     3, z, gain, st);
+    if (rc) return rc;
+    rc = launch_strided<float, float>(inter, fv, fv.sy, fv.sz, inter, fv, fv.sy, fv.sz, nx, nz,
+                                      ny, 3, z, gain, st);
+  }
   if (rc) return rc;
   return launch_x_node4(inter, fv, out, scale4, rx, nx, ny, nz, z, gain, st);
 }
@@ -1152,7 +1202,8 @@ extern "C" size_t ps_spline_coeffs_workspace_size(const ps_grid* grid, int ncomp
                                                   ps_dtype coef_t) {
   if (!grid || ncomp < 1) return 0;
   if (coef_t == PS_BF16 || coef_t == PS_F16 || coef_t == PS_F32X4 || coef_t == PS_BF16X4 ||
-      coef_t == PS_F16X4 || (coef_t == PS_F32 && validate_grid(grid) == PS_OK && stream_grid(grid)))
+      coef_t == PS_F16X4 ||
+      (coef_t == PS_F32 && validate_grid(grid) == PS_OK && (stream_grid(grid) || stream3_grid(grid))))
     return align_up((size_t)ncomp * (size_t)grid_volume(grid) * sizeof(float), 256) + 256;
   return 0;
 }
@@ -1190,9 +1241,12 @@ extern "C" ps_status ps_spline_coeffs(const ps_grid* grid, int ncomp, ps_dtype f
     // the two-pass solve when the workspace holds its intermediate, else
     // the three passes in place
     const size_t inter_bytes = (size_t)ncomp * (size_t)grid_volume(grid) * sizeof(float);
-    if (field_t == PS_F32 && stream_solve_ok(grid) && aligned16 && ws && ws_bytes >= inter_bytes &&
-        (reinterpret_cast<uintptr_t>(ws) & 255) == 0)
+    const bool have_ws = ws && ws_bytes >= inter_bytes && (reinterpret_cast<uintptr_t>(ws) & 255) == 0;
+    if (field_t == PS_F32 && stream_solve_ok(grid) && aligned16 && have_ws)
       return run_solve_stream_planar(grid, ncomp, ff, static_cast<float*>(ws), c, rx, st);
+    if (field_t == PS_F32 && tuning().solve_stream && stream3_grid(grid) && aligned16 && have_ws)
+      return run_solve<float, float, float, false>(grid, ncomp, ff, fv, static_cast<float*>(ws),
+                                                   fv, c, pv, nullptr, 1, st);
     return field_t == PS_F32
                ? run_solve<float, float, float, false>(grid, ncomp, ff, fv, c, iv, c, pv,
                                                        nullptr, 1, st)

@@ -76,14 +76,15 @@ def test_spline_coeffs_long_pencils(n):
 
 
 @pytest.mark.parametrize("n", [(128, 40, 50), (256, 33, 47), (128, 32, 700), (512, 48, 32),
-                               (128, 700, 34)])
+                               (128, 700, 34), (36, 40, 50), (100, 36, 33), (1028, 32, 33)])
 def test_streamed_solve_matches_oracle(n):
     # The two-pass solve (x-y pass, then the z pass into the padded layout's
     # interior, then its periodic images) streams y and z in 16-line chunks:
     # ragged last chunks, every row width it takes (128, 256, 512), long
-    # pencils.  It meets the bar against the oracle, planar and node storage
-    # hold the same bits, and the z pass's columns per block and the x-y
-    # pass's stages change no bit.
+    # pencils; other row widths (a multiple of 4) stream y and z and keep
+    # the x pass.  It meets the bar against the oracle, planar and node
+    # storage hold the same bits, and the line streams' columns per block and
+    # the x-y pass's stages change no bit.
     field = synth.random_field(n, ncomp=3, seed=sum(n) + 7)
     ref32 = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
     f = torch.from_numpy(field.astype(np.float32)).to(DEV)
@@ -103,10 +104,11 @@ def test_streamed_solve_matches_oracle(n):
             ps.ps_tune_set("solve_stages", stages)
             assert torch.equal(ps.SplineField.from_field(f, torch.float32).padded(), p32)
             assert torch.equal(ps.SplineField.from_field(f, ps.F32X4).padded(), p32)
-        # the three-pass solve agrees within the rounding bar
+        # the strided three-pass solve agrees: each is within the bar of the
+        # oracle, so the two are within twice it
         ps.ps_tune_set("solve_stream", 0)
         p3 = ps.SplineField.from_field(f, torch.float32).padded()
-        assert (p3 - p32).abs().max().item() <= coef_tol(field)
+        assert (p3 - p32).abs().max().item() <= 2 * coef_tol(field)
     finally:
         for k, v in old.items():
             ps.ps_tune_set(k, v)
