@@ -439,6 +439,206 @@ __global__ void __launch_bounds__(96) solve_x_node4(const T* src, View sv, NodeT
     }
 }
 
+// ------------------------------------------------------------- wide lines ----
+// x lines longer than a warp takes at 16 values a lane (nx > 512, FP32): W
+// warps hold one line, 32 W lanes with chunks of L <= 16 values, the line in
+// one skewed buffer (element e at e + e / L).  The chunk carries go through
+// shared memory (cy, ca: one value per lane) with block barriers instead of
+// shuffles; with QUANT the line's maximum is taken across its W warps
+// (red[W]).  Every thread of the block calls it; returns the line's scale.
+template <bool QUANT>
+__device__ float line_solve_wide(float* buf, int nx, int L, int vl, int nvl, float z, float gain,
+                                 float* cy, float* ca, float* red) {
+  constexpr int LMAX = 16;
+  const float thr = Thr<float>::v;
+  int len = nx - vl * L;
+  len = len < 0 ? 0 : (len > L ? L : len);
+  float* mine = buf + vl * (L + 1);
+  float v[LMAX];
+  if (len == LMAX) {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) v[i] = mine[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) v[i] = mine[i];
+  }
+  const float y = chunk_causal<float, LMAX>(v, len, z);
+  const float a = chunk_zlen<float>(len);
+  cy[vl] = y;
+  ca[vl] = a;
+  __syncthreads();
+  float carry = 0.f, fac = 1.f;
+  bool wrapped = true;
+  for (int j = 1; j <= nvl; ++j) {
+    int sl = vl - j;
+    if (sl < 0) sl += nvl;
+    carry += fac * cy[sl];
+    fac *= ca[sl];
+    if (fabsf(fac) < thr) {
+      wrapped = false;
+      break;
+    }
+  }
+  if (wrapped) carry = carry / (1.f - fac);
+  chunk_causal_fix<float, LMAX>(v, len, carry);
+  const float w = chunk_anticausal<float, LMAX>(v, len, z);
+  __syncthreads();  // every lane has read the causal end states
+  cy[vl] = w;
+  __syncthreads();
+  carry = 0.f;
+  fac = 1.f;
+  wrapped = true;
+  for (int j = 1; j <= nvl; ++j) {
+    int sl = vl + j;
+    if (sl >= nvl) sl -= nvl;
+    carry += fac * cy[sl];
+    fac *= ca[sl];
+    if (fabsf(fac) < thr) {
+      wrapped = false;
+      break;
+    }
+  }
+  if (wrapped) carry = carry / (1.f - fac);
+  chunk_anticausal_fix<float, LMAX>(v, len, carry, z);
+  float sc = 1.f;
+  if (QUANT) {
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+      if (i < len) mx = fmaxf(mx, fabsf(gain * v[i]));
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+    if ((vl & 31) == 0) red[vl >> 5] = mx;
+    __syncthreads();
+    mx = 0.f;
+    for (int k = 0; k < nvl / 32; ++k) mx = fmaxf(mx, red[k]);
+    sc = pow2_at_least(mx);
+  }
+  const float inv_sc = 1.f / sc;  // exact: sc is a power of two
+#pragma unroll
+  for (int i = 0; i < LMAX; ++i)
+    if (i < len) mine[i] = gain * v[i] * inv_sc;
+  return sc;
+}
+
+// The planar x pass on wide lines: one (c, z, y) line per block of 32 W
+// threads; writes as solve_x.  (e + 1/2) / L stays 1/(2L) from an integer,
+// far above the FP32 rounding of the product for lines of 2^20 values, so
+// skew() is exact here too.
+template <typename Tout, bool QUANT>
+__global__ void __launch_bounds__(512) solve_x_wide(const float* src, View sv, Tout* dst,
+                                                    View dv, float* scale, int nx, int ny, int nz,
+                                                    int L, int padded, float z, float gain) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x, nvl = blockDim.x;
+  float* buf = reinterpret_cast<float*>(smem_raw);  // nvl (L + 1)
+  float* cy = buf + nvl * (L + 1);
+  float* ca = cy + nvl;
+  float* red = ca + nvl;
+  const int row = blockIdx.x;  // c * nz * ny + z * ny + y
+  const int yy = row % ny, r2 = row / ny, zz = r2 % nz, c = r2 / nz;
+  const float inv_L = 1.f / (float)L;
+  const float* sp = src + sv.off + c * sv.sc + zz * sv.sz + yy * sv.sy;
+  for (int e = t; e < nx; e += nvl) buf[skew(e, inv_L)] = sp[e];
+  __syncthreads();
+  const float sc = line_solve_wide<QUANT>(buf, nx, L, t, nvl, z, gain, cy, ca, red);
+  __syncthreads();
+  if (!padded) {
+    Tout* orow = dst + dv.off + c * dv.sc + zz * dv.sz + yy * dv.sy;
+    for (int e = t; e < nx; e += nvl) orow[e] = (Tout)buf[skew(e, inv_L)];
+    return;
+  }
+  int Py[2], Pz[2];
+  int npy = 1, npz = 1;
+  Py[0] = yy + 1;
+  if (yy == ny - 1) Py[npy++] = 0;
+  else if (yy == 0) Py[npy++] = ny + 1;
+  else if (yy == 1) Py[npy++] = ny + 2;
+  Pz[0] = zz + 1;
+  if (zz == nz - 1) Pz[npz++] = 0;
+  else if (zz == 0) Pz[npz++] = nz + 1;
+  else if (zz == 1) Pz[npz++] = nz + 2;
+  for (int iz = 0; iz < npz; ++iz)
+    for (int iy = 0; iy < npy; ++iy) {
+      Tout* orow = dst + dv.off + c * dv.sc + Pz[iz] * dv.sz + Py[iy] * dv.sy;
+      for (int P = t; P < dv.sy; P += nvl) {
+        const float val = P < nx + 3 ? buf[skew(padded_to_node(P, nx), inv_L)] : 0.f;
+        orow[P] = cvt_out<Tout>(val);
+      }
+      if (QUANT && t == 0) scale[((int64_t)c * (nz + 3) + Pz[iz]) * (ny + 3) + Py[iy]] = sc;
+    }
+}
+
+// The node x pass on wide lines: one (z, y) row per block, W warps per
+// component (96 W threads); writes as solve_x_node4.
+template <typename NodeT>
+__global__ void __launch_bounds__(768) solve_x_node4_wide(const float* src, View sv, NodeT* dst,
+                                                          float* scale4, int64_t rx, int nx,
+                                                          int ny, int nz, int L, float z,
+                                                          float gain) {
+  constexpr bool Q = IsNode16<NodeT>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float line_scale[3];
+  const int nvl = blockDim.x / 3, comp = threadIdx.x / nvl, vl = threadIdx.x - comp * nvl;
+  const int LB = nvl * (L + 1);
+  float* base = reinterpret_cast<float*>(smem_raw);
+  float* buf = base + comp * LB;                       // 3 lines
+  float* cy = base + 3 * LB + comp * 2 * nvl;          // 3 x (cy, ca)
+  float* ca = cy + nvl;
+  float* red = base + 3 * LB + 6 * nvl + comp * (nvl / 32);
+  const int yy = blockIdx.x, zz = blockIdx.y;
+  const float inv_L = 1.f / (float)L;
+  const float* sp = src + sv.off + comp * sv.sc + zz * sv.sz + yy * sv.sy;
+  for (int e = vl; e < nx; e += nvl) buf[skew(e, inv_L)] = sp[e];
+  __syncthreads();
+  const float sc = line_solve_wide<Q>(buf, nx, L, vl, nvl, z, gain, cy, ca, red);
+  if (vl == 0) line_scale[comp] = sc;
+  __syncthreads();
+  const float* b0 = base;
+  const float* b1 = b0 + LB;
+  const float* b2 = b1 + LB;
+  int Py[2], Pz[2];
+  int npy = 1, npz = 1;
+  Py[0] = yy + 1;
+  if (yy == ny - 1) Py[npy++] = 0;
+  else if (yy == 0) Py[npy++] = ny + 1;
+  else if (yy == 1) Py[npy++] = ny + 2;
+  Pz[0] = zz + 1;
+  if (zz == nz - 1) Pz[npz++] = 0;
+  else if (zz == 0) Pz[npz++] = nz + 1;
+  else if (zz == 1) Pz[npz++] = nz + 2;
+  for (int iz = 0; iz < npz; ++iz)
+    for (int iy = 0; iy < npy; ++iy) {
+      const int64_t r = (int64_t)Pz[iz] * (ny + 3) + Py[iy];
+      NodeT* orow = dst + r * rx;
+      for (int P = threadIdx.x; P < rx; P += blockDim.x) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        if (P < nx + 3) {
+          const int e = skew(padded_to_node(P, nx), inv_L);
+          a = b0[e];
+          b = b1[e];
+          c = b2[e];
+        }
+        orow[P] = NodeOut<NodeT>::make(a, b, c);
+      }
+      if (Q && threadIdx.x < 4)
+        scale4[r * 4 + threadIdx.x] = threadIdx.x < 3 ? line_scale[threadIdx.x] : 1.f;
+    }
+}
+
+// Wide-line geometry: W warps of chunks L (even, <= 16) for nx > 512.
+struct WideGeo {
+  int W, L;
+};
+WideGeo wide_geo(int nx) {
+  WideGeo g;
+  g.W = (nx + 511) / 512;
+  const int L = (nx + 32 * g.W - 1) / (32 * g.W);
+  g.L = L + (L & 1);
+  return g;
+}
+
 // ------------------------------------------------------- two-pass solve ----
 // The x and y solves of every (c, z) plane in one pass, the z solve in a
 // second pass that writes the padded layout (planar, or (u, v, w, 0)
@@ -862,6 +1062,24 @@ template <typename T, typename Tout, bool QUANT>
 ps_status launch_x(const T* src, View sv, Tout* dst, View dv, float* scale, int nx,
                    int ny, int nz, int ncomp, int padded, T z, T gain, cudaStream_t st) {
   const int L = x_chunk(nx);
+  if constexpr (sizeof(T) == 4) {
+    if (L > 16) {  // wide lines: W warps per line
+      const WideGeo wg = wide_geo(nx);
+      const int nvl = 32 * wg.W;
+      const size_t smem = ((size_t)nvl * (wg.L + 1) + 2 * nvl + wg.W) * sizeof(float);
+      auto kern = solve_x_wide<Tout, QUANT>;
+      if (smem > 48 * 1024) {
+        ps_status rc = check_cuda(
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "solve_x_wide smem attribute");
+        if (rc) return rc;
+      }
+      const int64_t rows = (int64_t)ncomp * nz * ny;
+      kern<<<(unsigned)rows, nvl, smem, st>>>(src, sv, dst, dv, scale, nx, ny, nz, wg.L, padded,
+                                              z, gain);
+      return check_launch("solve_x_wide");
+    }
+  }
   if (L <= 2)
     return launch_x_l<T, Tout, QUANT, 2>(src, sv, dst, dv, scale, nx, ny, nz, ncomp, L,
                                           padded, z, gain, st);
@@ -874,12 +1092,11 @@ ps_status launch_x(const T* src, View sv, Tout* dst, View dv, float* scale, int 
   if (L <= 16)
     return launch_x_l<T, Tout, QUANT, 16>(src, sv, dst, dv, scale, nx, ny, nz, ncomp, L,
                                            padded, z, gain, st);
-  if (L <= 32)
-    return launch_x_l<T, Tout, QUANT, 32>(src, sv, dst, dv, scale, nx, ny, nz, ncomp, L,
-                                           padded, z, gain, st);
-  if constexpr (sizeof(T) == 4)
-    return launch_x_l<T, Tout, QUANT, 64>(src, sv, dst, dv, scale, nx, ny, nz, ncomp, L,
-                                           padded, z, gain, st);
+  if constexpr (sizeof(T) == 8) {
+    if (L <= 32)
+      return launch_x_l<T, Tout, QUANT, 32>(src, sv, dst, dv, scale, nx, ny, nz, ncomp, L,
+                                             padded, z, gain, st);
+  }
   return fail(PS_ERR_UNSUPPORTED, "FP64 solve supports n <= 1024");
 }
 
@@ -908,9 +1125,20 @@ ps_status launch_x_node4(const float* src, View sv, NodeT* dst, float* scale4, i
   if (L <= 8) return launch_x_node4_l<8>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
   if (L <= 16)
     return launch_x_node4_l<16>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
-  if (L <= 32)
-    return launch_x_node4_l<32>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
-  return launch_x_node4_l<64>(src, sv, dst, scale4, rx, nx, ny, nz, L, z, gain, st);
+  // wide lines: W warps per component
+  const WideGeo wg = wide_geo(nx);
+  const int nvl = 32 * wg.W;
+  const size_t smem = ((size_t)3 * nvl * (wg.L + 1) + 6 * nvl + 3 * wg.W) * sizeof(float);
+  auto kern = solve_x_node4_wide<NodeT>;
+  if (smem > 48 * 1024) {
+    ps_status rc = check_cuda(
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "solve_x_node4_wide smem attribute");
+    if (rc) return rc;
+  }
+  kern<<<dim3((unsigned)ny, (unsigned)nz), 3 * nvl, smem, st>>>(src, sv, dst, scale4, rx, nx, ny,
+                                                                  nz, wg.L, z, gain);
+  return check_launch("solve_x_node4_wide");
 }
 
 // Two-pass solve: applies to FP32 fields and FP32 coefficients (planar or
