@@ -330,6 +330,48 @@ def test_low_precision_coefficients(dtype, bound):
     assert rel_err(sf.interp(pg, bins=bins).cpu().numpy(), ref) <= bound
 
 
+@pytest.mark.parametrize("dtype,ulp", [(torch.bfloat16, 2.0 ** -8), (torch.float16, 2.0 ** -11)])
+@pytest.mark.parametrize("n", [(1100, 6, 5), (1028, 32, 33)])
+def test_low_precision_wide_rows(dtype, ulp, n):
+    # rows over 512 values take W warps per x-line (carries and the line's
+    # maximum through shared memory); (1028, 32, 33) also streams y and z.
+    # Each stored value is its FP32 coefficient rounded to 16 bits after
+    # division by the line's power-of-two scale: within half an ulp of the
+    # scaled value, plus the FP32 solve's bar.
+    field = synth.random_field(n, ncomp=3, seed=sum(n) + 9)
+    ref = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
+    f = torch.from_numpy(field.astype(np.float32)).to(DEV)
+    sf = ps.SplineField.from_field(f, dtype)
+    sc = sf.scale.cpu().numpy()  # [ncomp][nz+3][ny+3]
+    assert np.all(np.log2(sc) == np.round(np.log2(sc)))
+    got = sf.padded().float().cpu().numpy() * sc[..., None]
+    # a line's scale is at least its largest value: the rounding is at most
+    # half an ulp of the scale
+    tol = 0.5 * ulp * sc[..., None] + coef_tol(field)
+    assert np.all(np.abs(got - ref) <= tol)
+    # the per-line scale is the least power of two at or above the line's
+    # largest coefficient
+    mx = np.abs(ref[..., : n[0] + 3]).max(axis=-1)
+    assert np.all(sc >= mx * (1 - 1e-6)) and np.all(sc < 2 * mx * (1 + 1e-6))
+
+
+def test_planar_solve_without_workspace_matches():
+    # planar FP32 without a workspace runs the three passes in place; with one
+    # it streams; each is within the bar of the oracle, so within twice it of
+    # the other
+    n = (96, 40, 36)
+    field = synth.random_field(n, ncomp=3, seed=191)
+    f = torch.from_numpy(field.astype(np.float32)).to(DEV)
+    with_ws = ps.SplineField.from_field(f, torch.float32).padded()
+    coef = torch.empty_like(ps.SplineField.from_field(f, torch.float32).coef)
+    ps.ps_spline_coeffs(f, coef, None, None)
+    no_ws = coef[..., : n[0] + 3]
+    ref = oracle.spline_coeffs(field.astype(np.float32).astype(np.float64))
+    assert np.abs(no_ws.cpu().numpy() - ref).max() <= coef_tol(field)
+    assert np.abs(with_ws.cpu().numpy() - ref).max() <= coef_tol(field)
+    assert (no_ws - with_ws).abs().max().item() <= 2 * coef_tol(field)
+
+
 def test_nonfinite_position_flagged():
     n = (16, 16, 16)
     field, pos, cref = _case(n, 100, seed=81)
