@@ -129,7 +129,9 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
     p->pbase[f + 1] = p->pbase[f] + nps[f];
     // a field so sparse that its bricks would hold fewer particles on average
     // than the staging threshold gathers from global memory anyway: bin it in
-    // runs of particles, a block per run instead of a block per brick
+    // runs of particles, a block per run instead of a block per brick (the
+    // runs cut the bricks' order into equal spans, so a run's particles are
+    // neighbours and their gathers share cache lines)
     const double cells = (double)grids[f].n[0] * grids[f].n[1] * grids[f].n[2];
     const double per_brick =
         (double)nps[f] * p->brick[0] * p->brick[1] * p->brick[2] / cells;
@@ -205,6 +207,7 @@ ps_status build_tables(ps_plan* p, const ps_batch_field* fields, double* pos, in
     bf.pbase = p->pbase[f];
     bf.bin_base = p->bin_base[f];
     bf.chunk = p->chunk[f];
+    bf.nruns = p->bin_base[f + 1] - p->bin_base[f];
   }
   return PS_OK;
 }

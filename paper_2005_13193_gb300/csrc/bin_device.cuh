@@ -64,14 +64,12 @@ __device__ __forceinline__ void batch_count_range(const BinField* __restrict__ t
           if (tab[mid].pbase <= p) lo = mid;
           else hi = mid;
         }
-        if (tab[lo].chunk > 0) {
-          // a sparse field: runs of particles in storage order
-          key = tab[lo].bin_base + (int)((p - tab[lo].pbase) / tab[lo].chunk);
-        } else {
-          bool ok;
-          key = tab[lo].bin_base + bin_of_position(tab[lo].g, tab[lo].b, x[u], y[u], z[u], ok);
-          if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
-        }
+        bool ok;
+        const int b = bin_of_position(tab[lo].g, tab[lo].b, x[u], y[u], z[u], ok);
+        if (!ok) flag_status(status, PS_DEV_NONFINITE_POS, p);
+        // a sparse field: runs, each an equal span of the bricks' order
+        key = tab[lo].bin_base +
+              (tab[lo].chunk > 0 ? (int)((int64_t)b * tab[lo].nruns / tab[lo].b.nbins) : b);
       }
       const unsigned peers = __match_any_sync(FULL, key);
       const int leader = __ffs(peers) - 1;

@@ -108,7 +108,8 @@ struct BinField {
   BrickArgs b;
   int64_t pbase;     // first particle of the field in the concatenated arrays
   int32_t bin_base;  // first global bin of the field
-  int32_t chunk;     // > 0: bins are runs of `chunk` particles, not bricks
+  int32_t chunk;     // > 0: bins are runs of about `chunk` particles, not bricks
+  int32_t nruns;     // runs of a field with chunk > 0
 };
 ps_status bin_run_batch(const BinField* d_tab, int nfields, int64_t total_bins, int64_t np,
                         const double* pos, int32_t* bin_of, int32_t* bin_offsets,
