@@ -136,6 +136,9 @@ int64_t ps_coef_row_pitch(int nx, ps_dtype coef_t);
  *     nodes): x columns per block of the streamed z pass.
  *  "solve_stages" 0, 2, 3 or 4 (0 = default 3): chunks in flight + 1 in the
  *     streamed x-y pass.
+ *  "batch_run_below" in [0, 2^20] (default 16): ps_batch_plan bins a field
+ *     whose bricks would hold fewer particles on average in runs of about
+ *     128 neighbouring particles (stencils from global memory), not bricks.
  *  "batch_persistent" 0 or 1 (default 1): ps_batch_run runs all steps in one
  *     cooperative persistent launch (1) or a launch per phase and step (0).
  *  "wait_probe" in [0, 2^30] (default 0), a test knob: > 0 makes every

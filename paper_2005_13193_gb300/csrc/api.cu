@@ -150,6 +150,11 @@ extern "C" ps_status ps_tune_set(const char* key, int64_t value) {
     tuning().node_tma = (int)value;
     return PS_OK;
   }
+  if (!strcmp(key, "batch_run_below")) {
+    if (value < 0 || value > (1 << 20)) return fail(PS_ERR_INVALID_ARG, "batch_run_below in [0, 2^20]");
+    tuning().batch_run_below = (int)value;
+    return PS_OK;
+  }
   if (!strcmp(key, "batch_persistent")) {
     if (value < 0 || value > 1) return fail(PS_ERR_INVALID_ARG, "batch_persistent is 0 or 1");
     tuning().batch_persistent = (int)value;
@@ -174,6 +179,7 @@ extern "C" int64_t ps_tune_get(const char* key) {
   if (!strcmp(key, "solve_stages")) return tuning().solve_stages;
   if (!strcmp(key, "wait_probe")) return tuning().wait_probe;
   if (!strcmp(key, "batch_persistent")) return tuning().batch_persistent;
+  if (!strcmp(key, "batch_run_below")) return tuning().batch_run_below;
   return -1;
 }
 

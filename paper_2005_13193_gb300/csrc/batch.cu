@@ -135,7 +135,7 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
     const double cells = (double)grids[f].n[0] * grids[f].n[1] * grids[f].n[2];
     const double per_brick =
         (double)nps[f] * p->brick[0] * p->brick[1] * p->brick[2] / cells;
-    if (per_brick < tuning().brick_min_stage) p->chunk[f] = kBatchChunk;
+    if (per_brick < tuning().batch_run_below) p->chunk[f] = kBatchChunk;
     bins += p->chunk[f] ? (nps[f] + kBatchChunk - 1) / kBatchChunk : p->bricks[f].nbins;
     if (bins >= ((int64_t)1 << 31)) {
       delete p;

@@ -79,6 +79,8 @@ struct Tuning {
   int solve_zt = 0;           // columns per block of the streamed z pass (0: default)
   int solve_stages = 0;       // shared-memory stages of the streamed y-x pass (0: 3)
   int wait_probe = 0;         // test knob: clocks of a wait that cannot complete
+  int batch_run_below = 16;   // batched fields with fewer particles per brick on
+                              // average are binned in runs, not bricks
   int batch_persistent = 1;   // batched steps: one cooperative launch (1) or a launch
                               // per phase and step (0)
 };
