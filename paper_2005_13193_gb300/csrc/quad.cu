@@ -256,24 +256,43 @@ __device__ __forceinline__ void quad_sum(const float v[16][3], const float t[3],
     dbz = pick4(d4, k);
   }
   float A[3] = {0.f, 0.f, 0.f}, Bx[3] = {0.f, 0.f, 0.f}, By[3] = {0.f, 0.f, 0.f};
+  // u and v as packed pairs (two FP32 operations per instruction, each
+  // rounded as its scalar form), w alone
+  float2 A2 = make_float2(0.f, 0.f), Bx2 = A2, By2 = A2;
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < 4; ++j) {
+    float2 vr[4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float sx = __fmul_rn(bx[0], v[4 * j][c]);
-      sx = __fmaf_rn(bx[1], v[4 * j + 1][c], sx);
-      sx = __fmaf_rn(bx[2], v[4 * j + 2][c], sx);
-      sx = __fmaf_rn(bx[3], v[4 * j + 3][c], sx);
-      A[c] = __fmaf_rn(by[j], sx, A[c]);
-      if (GRAD) {
-        float dx = __fmul_rn(dbx[0], v[4 * j][c]);
-        dx = __fmaf_rn(dbx[1], v[4 * j + 1][c], dx);
-        dx = __fmaf_rn(dbx[2], v[4 * j + 2][c], dx);
-        dx = __fmaf_rn(dbx[3], v[4 * j + 3][c], dx);
-        Bx[c] = __fmaf_rn(by[j], dx, Bx[c]);
-        By[c] = __fmaf_rn(dby[j], sx, By[c]);
-      }
+    for (int i = 0; i < 4; ++i) vr[i] = make_float2(v[4 * j + i][0], v[4 * j + i][1]);
+    float2 sx2 = __fmul2_rn(make_float2(bx[0], bx[0]), vr[0]);
+#pragma unroll
+    for (int i = 1; i < 4; ++i) sx2 = __ffma2_rn(make_float2(bx[i], bx[i]), vr[i], sx2);
+    A2 = __ffma2_rn(make_float2(by[j], by[j]), sx2, A2);
+    float sx = __fmul_rn(bx[0], v[4 * j][2]);
+    sx = __fmaf_rn(bx[1], v[4 * j + 1][2], sx);
+    sx = __fmaf_rn(bx[2], v[4 * j + 2][2], sx);
+    sx = __fmaf_rn(bx[3], v[4 * j + 3][2], sx);
+    A[2] = __fmaf_rn(by[j], sx, A[2]);
+    if (GRAD) {
+      float2 dx2 = __fmul2_rn(make_float2(dbx[0], dbx[0]), vr[0]);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) dx2 = __ffma2_rn(make_float2(dbx[i], dbx[i]), vr[i], dx2);
+      Bx2 = __ffma2_rn(make_float2(by[j], by[j]), dx2, Bx2);
+      By2 = __ffma2_rn(make_float2(dby[j], dby[j]), sx2, By2);
+      float dx = __fmul_rn(dbx[0], v[4 * j][2]);
+      dx = __fmaf_rn(dbx[1], v[4 * j + 1][2], dx);
+      dx = __fmaf_rn(dbx[2], v[4 * j + 2][2], dx);
+      dx = __fmaf_rn(dbx[3], v[4 * j + 3][2], dx);
+      Bx[2] = __fmaf_rn(by[j], dx, Bx[2]);
+      By[2] = __fmaf_rn(dby[j], sx, By[2]);
     }
+  }
+  A[0] = A2.x;
+  A[1] = A2.y;
+  Bx[0] = Bx2.x;
+  Bx[1] = Bx2.y;
+  By[0] = By2.x;
+  By[1] = By2.y;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     out[0][c] = __fmul_rn(bz, A[c]);
