@@ -159,7 +159,8 @@ extern "C" ps_status ps_batch_plan(int nfields, const ps_grid* grids, const int6
     size_t s = 0;
     ps_status rc = staged_fill_rk2(&grids[f], coef_t, p->brick, nullptr, nullptr, 0, nullptr,
                                    nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
-                                   p->chunk[f] ? 1 : 0, probe.data(), &s);
+                                   p->chunk[f] ? 1 : 0, nullptr, nullptr, 0, 0, probe.data(),
+                                   &s);
     if (rc) {
       delete p;
       return rc;
@@ -193,12 +194,18 @@ ps_status build_tables(ps_plan* p, const ps_batch_field* fields, double* pos, in
   int32_t* offsets = at<int32_t>(ws, p->off_offsets);
   double* pos_s = at<double>(ws, p->off_pos);
   int64_t* ids_s = at<int64_t>(ws, p->off_ids);
+  int32_t* counts = at<int32_t>(ws, p->off_counts);
+  int32_t* bin_of = at<int32_t>(ws, p->off_binof);
   for (int f = 0; f < p->nfields; ++f) {
     size_t s = 0;
+    // the step kernel counts the next step's bins (global keys: the field's
+    // first bin plus its bin; runs for fields binned in runs)
+    const int nruns = p->chunk[f] ? p->bin_base[f + 1] - p->bin_base[f] : 0;
     ps_status rc = staged_fill_rk2(&p->grids[f], p->coef_t, p->brick, fields[f].coef,
                                    fields[f].scale, p->np_total, pos_s, pos,
                                    offsets + p->bin_base[f], vel, ids ? ids_s : nullptr, ids,
-                                   dt, status, p->chunk[f] ? 1 : 0,
+                                   dt, status, p->chunk[f] ? 1 : 0, counts + p->bin_base[f],
+                                   bin_of, p->bin_base[f], nruns,
                                    p->h_args.data() + (size_t)f * p->args_size, &s);
     if (rc) return rc;
     BinField& bf = p->h_bintab[f];
@@ -254,16 +261,30 @@ ps_status enqueue_persistent(ps_plan* p, double* pos, int64_t* ids, int nsteps, 
 
 // One Heun step of every particle of every field: bin sort (positions and
 // labels copied into bin order in the workspace), then the brick kernel,
-// which writes the updated positions back in that order.
+// which writes the updated positions back in that order and counts their
+// bins for the next step's sort.  The first step of a run counts from the
+// positions (and clears the counters before the brick kernel); the others
+// start at the scan of the counts the previous step took.
 ps_status enqueue_step(ps_plan* p, double* pos, int64_t* ids, void* ws, int32_t* status,
-                       cudaStream_t st) {
+                       bool first, cudaStream_t st) {
   if (p->np_total == 0) return PS_OK;
-  ps_status rc = bin_run_batch(at<BinField>(ws, p->off_bintab), p->nfields, p->total_bins,
-                               p->np_total, pos, at<int32_t>(ws, p->off_binof),
-                               at<int32_t>(ws, p->off_offsets), at<double>(ws, p->off_pos),
-                               ids, ids ? at<int64_t>(ws, p->off_ids) : nullptr,
-                               at<int32_t>(ws, p->off_counts), at<int32_t>(ws, p->off_rank),
-                               at<int32_t>(ws, p->off_scan), status, st);
+  int32_t* counts = at<int32_t>(ws, p->off_counts);
+  ps_status rc;
+  if (first) {
+    rc = bin_run_batch(at<BinField>(ws, p->off_bintab), p->nfields, p->total_bins, p->np_total,
+                       pos, at<int32_t>(ws, p->off_binof), at<int32_t>(ws, p->off_offsets),
+                       at<double>(ws, p->off_pos), ids,
+                       ids ? at<int64_t>(ws, p->off_ids) : nullptr, counts,
+                       at<int32_t>(ws, p->off_rank), at<int32_t>(ws, p->off_scan), status, st);
+    if (!rc)
+      rc = check_cuda(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (p->total_bins + 1), st),
+                      "batch counts clear");
+  } else {
+    rc = bin_rescan_counted(p->total_bins, p->np_total, pos, at<int32_t>(ws, p->off_binof),
+                            at<int32_t>(ws, p->off_offsets), at<double>(ws, p->off_pos), ids,
+                            ids ? at<int64_t>(ws, p->off_ids) : nullptr, counts,
+                            at<int32_t>(ws, p->off_scan), status, st);
+  }
   if (rc) return rc;
   return staged_batch_launch(p->coef_t, at<char>(ws, p->off_args),
                              at<int32_t>(ws, p->off_binbase), p->nfields, p->total_bins,
@@ -308,7 +329,7 @@ extern "C" ps_status ps_batch_run(ps_plan* p, const ps_batch_field* fields, int 
   auto enqueue_steps = [&](cudaStream_t s) -> ps_status {
     if (persistent) return enqueue_persistent(p, pos, ids, nsteps, ws, status, s);
     for (int k = 0; k < nsteps; ++k) {
-      ps_status r = enqueue_step(p, pos, ids, ws, status, s);
+      ps_status r = enqueue_step(p, pos, ids, ws, status, k == 0, s);
       if (r) return r;
     }
     return PS_OK;

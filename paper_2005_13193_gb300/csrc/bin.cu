@@ -130,68 +130,10 @@ __global__ void bin_scatter_counted(int64_t np, const double* __restrict__ pos,
                                     const int64_t* __restrict__ ids,
                                     int64_t* __restrict__ ids_sorted, int64_t nbins,
                                     int32_t* status) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && offsets[nbins] != np)
-    flag_status(status, PS_DEV_BAD_BINS, offsets[nbins]);
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  for (int64_t base = wid * 32 * kCountUnroll; base < np; base += warps * 32 * kCountUnroll) {
-    int key[kCountUnroll];
-    double x[kCountUnroll], y[kCountUnroll], z[kCountUnroll];
-    int64_t id[kCountUnroll];
-    // bins and payloads of all groups first
-#pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
-      const int64_t p = base + u * 32 + lane;
-      key[u] = -1 - lane;  // unique per lane when invalid
-      x[u] = y[u] = z[u] = 0.0;
-      id[u] = 0;
-      if (p < np) {
-        const int bn = bin_of[p];
-        if ((uint64_t)(int64_t)bn < (uint64_t)nbins) key[u] = bn;
-        else flag_status(status, PS_DEV_BAD_BINS, p);
-        if (pos_sorted) {
-          x[u] = pos[p];
-          y[u] = pos[np + p];
-          z[u] = pos[2 * np + p];
-        }
-        if (ids_sorted) id[u] = ids[p];
-      }
-    }
-    // one atomic per run of equal bins, all groups' atomics in flight together
-    unsigned peers[kCountUnroll];
-    int old[kCountUnroll];
-#pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
-      peers[u] = __match_any_sync(FULL, key[u]);
-      old[u] = 0;
-      if (key[u] >= 0 && lane == __ffs(peers[u]) - 1)
-        old[u] = atomicSub(&counts[key[u]], __popc(peers[u]));
-    }
-#pragma unroll
-    for (int u = 0; u < kCountUnroll; ++u) {
-      const int leader = __ffs(peers[u]) - 1;
-      const int top = __shfl_sync(FULL, old[u], leader);
-      if (key[u] < 0) continue;
-      const int64_t p = base + u * 32 + lane;
-      const int len = __popc(peers[u]);
-      const int r = top - len + __popc(peers[u] & ((1u << lane) - 1u));
-      const int64_t lo = offsets[key[u]], hi = offsets[key[u] + 1];
-      if (top - len < 0 || (int64_t)top > hi - lo) {
-        flag_status(status, PS_DEV_BAD_BINS, p);
-        continue;
-      }
-      const int64_t slot = lo + r;
-      if (perm) perm[slot] = p;
-      if (pos_sorted) {
-        pos_sorted[slot] = x[u];
-        pos_sorted[np + slot] = y[u];
-        pos_sorted[2 * np + slot] = z[u];
-      }
-      if (ids_sorted) ids_sorted[slot] = id[u];
-    }
-  }
+  scatter_counted_range(np, pos, bin_of, counts, offsets, perm, pos_sorted, ids, ids_sorted,
+                        nbins, status,
+                        ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                        ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 // Counting pass over the concatenated particles of many fields: particle p of
@@ -265,6 +207,28 @@ ps_status bin_run(const GridArgs& ga, const BrickArgs& ba, int64_t np, const dou
       bin_scatter_kernel<<<persistent_blocks(np, 256), 256, 0, st>>>(
           np, pos, bin_of, rank, bin_offsets, perm, pos_sorted, ids, ids_sorted);
     if ((rc = check_launch("bin_scatter"))) return rc;
+  }
+  return PS_OK;
+}
+
+ps_status bin_rescan_counted(int64_t total_bins, int64_t np, const double* pos,
+                             const int32_t* bin_of, int32_t* bin_offsets, double* pos_sorted,
+                             const int64_t* ids, int64_t* ids_sorted, int32_t* counts,
+                             int32_t* scan_tmp, int32_t* status, cudaStream_t st) {
+  const int64_t ntiles = (int64_t)scan_tmp_elems(total_bins);
+  scan_tile_sums<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, total_bins, scan_tmp);
+  ps_status rc = check_launch("scan_tile_sums");
+  if (rc) return rc;
+  scan_tile_offsets<<<1, kScanThreads, 0, st>>>(scan_tmp, ntiles);
+  if ((rc = check_launch("scan_tile_offsets"))) return rc;
+  scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, st>>>(counts, total_bins, scan_tmp,
+                                                        bin_offsets, -1);
+  if ((rc = check_launch("scan_tiles"))) return rc;
+  if (np > 0) {
+    bin_scatter_counted<<<persistent_blocks(np, 256), 256, 0, st>>>(
+        np, pos, bin_of, counts, bin_offsets, nullptr, pos_sorted, ids, ids_sorted, total_bins,
+        status);
+    if ((rc = check_launch("bin_scatter_counted"))) return rc;
   }
   return PS_OK;
 }

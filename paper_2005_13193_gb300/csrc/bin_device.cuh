@@ -187,6 +187,84 @@ __device__ __forceinline__ void scan_tile(const int32_t* __restrict__ in, int64_
 // offset, then the payload) of several in flight together.
 constexpr int kCountUnroll = 4;
 
+// Scatter into bin order from counts the step kernels took (the counted
+// re-binning): bins in bin_of, bounds in offsets; each run of equal bins in a
+// warp takes its slots with one atomicSub on the bin's counter, so the
+// counters end at zero.  Slots outside a bin's range are not written and are
+// reported (PS_DEV_BAD_BINS).  Warp wid of `warps` covers groups of
+// kCountUnroll x 32 particles; every lane of the warp calls.
+__device__ __forceinline__ void scatter_counted_range(int64_t np, const double* __restrict__ pos,
+                                    const int32_t* __restrict__ bin_of,
+                                    int32_t* __restrict__ counts,
+                                    const int32_t* __restrict__ offsets,
+                                    int64_t* __restrict__ perm,
+                                    double* __restrict__ pos_sorted,
+                                    const int64_t* __restrict__ ids,
+                                    int64_t* __restrict__ ids_sorted, int64_t nbins,
+                                    int32_t* status, int64_t wid, int64_t warps) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  if (wid == 0 && lane == 0 && offsets[nbins] != np)
+    flag_status(status, PS_DEV_BAD_BINS, offsets[nbins]);
+  for (int64_t base = wid * 32 * kCountUnroll; base < np; base += warps * 32 * kCountUnroll) {
+    int key[kCountUnroll];
+    double x[kCountUnroll], y[kCountUnroll], z[kCountUnroll];
+    int64_t id[kCountUnroll];
+    // bins and payloads of all groups first
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int64_t p = base + u * 32 + lane;
+      key[u] = -1 - lane;  // unique per lane when invalid
+      x[u] = y[u] = z[u] = 0.0;
+      id[u] = 0;
+      if (p < np) {
+        const int bn = bin_of[p];
+        if ((uint64_t)(int64_t)bn < (uint64_t)nbins) key[u] = bn;
+        else flag_status(status, PS_DEV_BAD_BINS, p);
+        if (pos_sorted) {
+          x[u] = pos[p];
+          y[u] = pos[np + p];
+          z[u] = pos[2 * np + p];
+        }
+        if (ids_sorted) id[u] = ids[p];
+      }
+    }
+    // one atomic per run of equal bins, all groups' atomics in flight together
+    unsigned peers[kCountUnroll];
+    int old[kCountUnroll];
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      peers[u] = __match_any_sync(FULL, key[u]);
+      old[u] = 0;
+      if (key[u] >= 0 && lane == __ffs(peers[u]) - 1)
+        old[u] = atomicSub(&counts[key[u]], __popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const int leader = __ffs(peers[u]) - 1;
+      const int top = __shfl_sync(FULL, old[u], leader);
+      if (key[u] < 0) continue;
+      const int64_t p = base + u * 32 + lane;
+      const int len = __popc(peers[u]);
+      const int r = top - len + __popc(peers[u] & ((1u << lane) - 1u));
+      const int64_t lo = offsets[key[u]], hi = offsets[key[u] + 1];
+      if (top - len < 0 || (int64_t)top > hi - lo) {
+        flag_status(status, PS_DEV_BAD_BINS, p);
+        continue;
+      }
+      const int64_t slot = lo + r;
+      if (perm) perm[slot] = p;
+      if (pos_sorted) {
+        pos_sorted[slot] = x[u];
+        pos_sorted[np + slot] = y[u];
+        pos_sorted[2 * np + slot] = z[u];
+      }
+      if (ids_sorted) ids_sorted[slot] = id[u];
+    }
+  }
+}
+
+
 // Scatter into bin order: slot = offsets[bin_of[p]] + rank[p]; the calling
 // thread starts at particle `first` and steps by `stride`.
 __device__ __forceinline__ void scatter_range(int64_t np, const double* __restrict__ pos,

@@ -812,8 +812,9 @@ __device__ __forceinline__ void process_brick(const StagedArgs& a, int beg, int 
       const int i = tid - (nwarps - kCountWarps) * 32;
       const bool vi = i < m;
       const int64_t pp = vi ? (a.perm ? a.perm[cb + i] : (int64_t)(cb + i)) : 0;
-      const int key = vi ? bin_of_coords(a.b, R.nbc(0)[i], R.nbc(1)[i], R.nbc(2)[i]) : 0;
-      count_into_bin(a.next_counts, a.next_bin, a.status, vi, pp, key);
+      int key = vi ? bin_of_coords(a.b, R.nbc(0)[i], R.nbc(1)[i], R.nbc(2)[i]) : 0;
+      if (a.next_runs > 0 && key >= 0) key = (int)((int64_t)key * a.next_runs / a.b.nbins);
+      count_into_bin(a.next_counts, a.next_bin, a.status, vi, pp, key, a.next_key_base);
     }
     }  // MODE == 2
   }
@@ -948,9 +949,11 @@ __global__ void __launch_bounds__(kThreads, 5)
 
 // ----------------------------------------------------- persistent batch ----
 // All Heun steps of a many-field batch in one cooperative launch: per step
-// the counting pass, the three scan phases, the scatter into bin order (and
-// the counters cleared for the next step), then the bricks of all fields;
-// the phases are separated by grid-wide barriers.  Each barrier is an arrival
+// the three scan phases, the scatter into bin order, then the bricks of all
+// fields, which count the bins of the positions they write for the next
+// step (the first step counts from the positions, scatters by rank and
+// clears the counters; later ones scatter from the counts, which end at
+// zero); the phases are separated by grid-wide barriers.  Each barrier is an arrival
 // counter and a generation word; a wait gives up after about 2^31 clocks,
 // sets the block-stop word and PS_DEV_TIMEOUT, and every block leaves at its
 // next barrier.  sync[3] is a word nothing sets: with wait_probe > 0 (a test
@@ -1037,9 +1040,13 @@ __global__ void __launch_bounds__(kThreads, 5) batch_persistent(const __grid_con
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const int64_t ntiles = (r.total_bins + kScanTile - 1) / kScanTile;
   for (int step = 0; step < r.nsteps; ++step) {
-    batch_count_range(r.bintab, r.nfields, r.np, r.pos, r.bin_of, r.rank, r.counts, r.status,
-                      gt - lane, gs);
-    if (!grid_barrier(r, nbar)) return;
+    // the first step counts from the positions; later ones scan the counts
+    // the previous step's bricks took
+    if (step == 0) {
+      batch_count_range(r.bintab, r.nfields, r.np, r.pos, r.bin_of, r.rank, r.counts, r.status,
+                        gt - lane, gs);
+      if (!grid_barrier(r, nbar)) return;
+    }
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
       scan_tile_sum<kThreads>(r.counts, r.total_bins, t, r.scan_tmp, scan_sh);
     if (!grid_barrier(r, nbar)) return;
@@ -1049,9 +1056,15 @@ __global__ void __launch_bounds__(kThreads, 5) batch_persistent(const __grid_con
       scan_tile<kThreads>(r.counts, r.total_bins, r.scan_tmp, r.offsets, -1, t, ntiles,
                           scan_sh);
     if (!grid_barrier(r, nbar)) return;
-    scatter_range(r.np, r.pos, r.bin_of, r.rank, r.offsets, nullptr, r.pos_s, r.ids,
-                  r.ids ? r.ids_s : nullptr, gt, gs);
-    for (int64_t i = gt; i <= r.total_bins; i += gs) r.counts[i] = 0;
+    if (step == 0) {
+      scatter_range(r.np, r.pos, r.bin_of, r.rank, r.offsets, nullptr, r.pos_s, r.ids,
+                    r.ids ? r.ids_s : nullptr, gt, gs);
+      for (int64_t i = gt; i <= r.total_bins; i += gs) r.counts[i] = 0;
+    } else {  // the counters end at zero, ready for this step's counting
+      scatter_counted_range(r.np, r.pos, r.bin_of, r.counts, r.offsets, nullptr, r.pos_s,
+                            r.ids, r.ids ? r.ids_s : nullptr, r.total_bins, r.status, gt >> 5,
+                            gs >> 5);
+    }
     if (gt == 0) atomicExch(&r.sync[4], 0u);
     if (!grid_barrier(r, nbar)) return;
     // bricks claimed kClaim at a time (their costs vary with their particles)
@@ -1503,7 +1516,8 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
                           const void* coef, const float* scale, int64_t np_total,
                           const double* pos_in, double* pos_out, const int32_t* offs,
                           float* vel, const int64_t* ids_in, int64_t* ids_out, double dt,
-                          int32_t* status, int chunked, void* out, size_t* smem) {
+                          int32_t* status, int chunked, int32_t* next_counts, int32_t* next_bin,
+                          int next_key_base, int next_runs, void* out, size_t* smem) {
   if (coef_t == PS_F64) return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
   StagedArgs a{};
   ps_status rc = fill_staged(grid, coef_t, brick, 0, false, &a, smem);
@@ -1525,6 +1539,10 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
   a.dtih[2] = d.z;
   a.status = status;
   a.chunked = chunked;
+  a.next_counts = next_counts;
+  a.next_bin = next_bin;
+  a.next_key_base = next_key_base;
+  a.next_runs = next_runs;
   memcpy(out, &a, sizeof(a));
   return PS_OK;
 }

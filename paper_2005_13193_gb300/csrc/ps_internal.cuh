@@ -113,6 +113,12 @@ struct BinField {
   int32_t chunk;     // > 0: bins are runs of about `chunk` particles, not bricks
   int32_t nruns;     // runs of a field with chunk > 0
 };
+// Scan of counts the step kernels took, then the counted scatter (the counts
+// end at zero).
+ps_status bin_rescan_counted(int64_t total_bins, int64_t np, const double* pos,
+                             const int32_t* bin_of, int32_t* bin_offsets, double* pos_sorted,
+                             const int64_t* ids, int64_t* ids_sorted, int32_t* counts,
+                             int32_t* scan_tmp, int32_t* status, cudaStream_t st);
 ps_status bin_run_batch(const BinField* d_tab, int nfields, int64_t total_bins, int64_t np,
                         const double* pos, int32_t* bin_of, int32_t* bin_offsets,
                         double* pos_sorted, const int64_t* ids, int64_t* ids_sorted,
@@ -125,7 +131,8 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
                           const void* coef, const float* scale, int64_t np_total,
                           const double* pos_in, double* pos_out, const int32_t* offs,
                           float* vel, const int64_t* ids_in, int64_t* ids_out, double dt,
-                          int32_t* status, int chunked, void* out, size_t* smem);
+                          int32_t* status, int chunked, int32_t* next_counts, int32_t* next_bin,
+                          int next_key_base, int next_runs, void* out, size_t* smem);
 // Particles per bin of a field binned in runs of particles instead of bricks.
 constexpr int kBatchChunk = 128;
 ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
@@ -224,7 +231,7 @@ __device__ __forceinline__ int bin_of_coords(const BrickArgs& b, int bx, int by,
 // 32 lanes must call.
 __device__ __forceinline__ void count_into_bin(int32_t* counts, int32_t* bin_of,
                                                int32_t* status, bool valid, int64_t p,
-                                               int key) {
+                                               int key, int key_base = 0) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   if (valid && key < 0) {
@@ -234,7 +241,7 @@ __device__ __forceinline__ void count_into_bin(int32_t* counts, int32_t* bin_of,
   const int k = valid ? key : -1 - lane;  // unique per lane when invalid
   const unsigned peers = __match_any_sync(FULL, k);
   if (valid && lane == __ffs(peers) - 1) atomicAdd(&counts[k], __popc(peers));
-  if (valid) bin_of[p] = k;
+  if (valid) bin_of[p] = key_base + k;
 }
 
 // FP64 variant for FP64 coefficients: t = s - floor(s) in FP64.

@@ -44,6 +44,8 @@ struct StagedArgs {
   // new bin at its slot in pos_out, bin counters (zeroed beforehand)
   int32_t* next_counts;
   int32_t* next_bin;
+  int32_t next_key_base;  // added to the key stored in next_bin (batched bins)
+  int32_t next_runs;      // > 0: bins are runs, run = brick * next_runs / nbins
   int bshift[3];  // log2 of the brick extent, -1 if not a power of two
   // high word of the double 2^30 L/n per axis: |x| has a smaller high word
   // (sign cleared) only if |x n/L| < 2^30, read without an FP64 operation
