@@ -398,9 +398,11 @@ ps_status ps_rk2_sort(const ps_grid* grid, const int32_t brick[3], int64_t np,
 /* spline coefficients (solve = 1; ps_spline_coeffs per field), then takes  */
 /* nsteps Heun steps of every particle (frozen fields): each step is one    */
 /* bin sort over all particles (global bin = first bin of the field + bin   */
-/* in the field) and one pass over the bricks of all fields, all steps in   */
-/* one cooperative persistent launch whose phases meet at grid-wide         */
-/* barriers (tune "batch_persistent" 0: a launch per phase and step).  A    */
+/* in the field) and one pass over the bricks of all fields, which counts  */
+/* the next step's bins as it writes the positions (the first step counts   */
+/* from the positions), all steps in one cooperative persistent launch      */
+/* whose phases meet at grid-wide barriers (tune "batch_persistent" 0: a    */
+/* launch per phase and step).  A                                           */
 /* barrier wait that runs out (about 2^31 clocks) stops every block and     */
 /* sets PS_DEV_TIMEOUT in *status; positions are then unspecified.          */
 /* Particles end in bin order per field, as with ps_rk2_step(rebin=1); ids  */
