@@ -69,7 +69,7 @@ typedef enum {
   PS_ERR_INVALID_ARG = 1,   /* bad pointer, size, dtype or layout request   */
   PS_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed  */
   PS_ERR_WORKSPACE = 3,     /* ws NULL, misaligned or smaller than needed   */
-  PS_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement  */
+  PS_ERR_UNSUPPORTED = 4,   /* valid request the library does not implement */
   PS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                */
   PS_ERR_DEVICE_STATUS = 6  /* ps_status_read found a device-side anomaly   */
 } ps_status;
