@@ -287,8 +287,8 @@ ps_status enqueue_step(ps_plan* p, double* pos, int64_t* ids, void* ws, int32_t*
   }
   if (rc) return rc;
   return staged_batch_launch(p->coef_t, at<char>(ws, p->off_args),
-                             at<int32_t>(ws, p->off_binbase), p->nfields, p->total_bins,
-                             p->smem, false, st);
+                             at<int32_t>(ws, p->off_binbase), p->h_args.data(), p->bin_base.data(),
+                             p->nfields, p->total_bins, p->smem, false, st);
 }
 
 }  // namespace
@@ -368,7 +368,8 @@ extern "C" ps_status ps_batch_run(ps_plan* p, const ps_batch_field* fields, int 
       (rc = check_cuda(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking),
                        "capture stream")))
     return rc;
-  if ((rc = staged_batch_launch(p->coef_t, nullptr, nullptr, 0, 0, p->smem, true, p->cap)))
+  if ((rc = staged_batch_launch(p->coef_t, nullptr, nullptr, nullptr, nullptr, 0, 0, p->smem, true,
+                                p->cap)))
     return rc;
   if ((rc = check_cuda(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal),
                        "begin capture")))

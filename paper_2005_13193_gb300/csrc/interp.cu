@@ -947,6 +947,36 @@ __global__ void __launch_bounds__(kThreads, 5)
   batch_brick<Tc, NC, MODE>(tab, bin_base, nfields, blockIdx.x, smem_b128, sa);
 }
 
+constexpr int kParamFields = 48;  // 48 x 640 bytes of arguments: within the 32 KB of parameters
+struct BatchParams {
+  StagedArgs a[kParamFields];
+  int bin_base[kParamFields + 1];
+  int nfields;
+};
+static_assert(sizeof(BatchParams) <= 32764, "kernel parameters are limited to 32764 bytes");
+
+// A batch of at most kParamFields fields passes its argument table as one
+// kernel parameter: the brick body then reads each field's arguments from the
+// constant bank, as the single-field kernel does (72 registers, 7 blocks per
+// SM), instead of from a shared-memory copy (96 registers, 5 blocks); the
+// tensor maps are named in parameter space like the single-field kernel's.
+template <typename Tc, int NC, int MODE>
+__global__ void __launch_bounds__(kThreads, sizeof(Tc) == 2 ? 6 : 7)
+    interp_staged_batch_p(const __grid_constant__ BatchParams tab) {
+  extern __shared__ __align__(128) float4 smem_bp128[];
+  const int b = blockIdx.x;
+  // field 0's offsets are the global offsets: empty bins leave at once
+  const int32_t* goffs = tab.a[0].offs;
+  if (goffs[b] >= goffs[b + 1]) return;
+  int lo = 0, hi = tab.nfields;  // bin_base[lo] <= b < bin_base[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tab.bin_base[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  brick_phased<Tc, NC, MODE, true>(tab.a[lo], b - tab.bin_base[lo], smem_bp128, &tab.a[lo]);
+}
+
 // ----------------------------------------------------- persistent batch ----
 // All Heun steps of a many-field batch in one cooperative launch: per step
 // the three scan phases, the scatter into bin order, then the bricks of all
@@ -1551,22 +1581,38 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
 // fields.  Set prepare = true once before any stream capture (it only sets the
 // shared-memory limit of the kernel).
 ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
-                              int nfields, int64_t total_bins, size_t smem, bool prepare,
-                              cudaStream_t st) {
+                              const void* h_tab, const int* h_bin_base, int nfields,
+                              int64_t total_bins, size_t smem, bool prepare, cudaStream_t st) {
   return with_coef_type(coef_t, [&](auto tag) -> ps_status {
     using Tc = decltype(tag);
     if constexpr (std::is_same<Tc, double>::value) {
       return fail(PS_ERR_UNSUPPORTED, "batched RK2 needs F32/BF16/F16");
     } else {
       auto kern = interp_staged_batch<Tc, 3, 2>;
+      auto kern_p = interp_staged_batch_p<Tc, 3, 2>;
       if (prepare) {
-        if (smem > 48 * 1024)
-          return check_cuda(
+        ps_status rc = PS_OK;
+        if (smem > 48 * 1024) {
+          rc = check_cuda(
               cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
               "batch smem attribute");
-        return PS_OK;
+          if (!rc)
+            rc = check_cuda(cudaFuncSetAttribute(
+                                kern_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                            "batch smem attribute");
+        }
+        return rc;
       }
       if (total_bins <= 0) return PS_OK;
+      if (h_tab && h_bin_base && nfields <= kParamFields) {
+        // the table by value (a graph captures it with the launch)
+        BatchParams tab;
+        memcpy(tab.a, h_tab, (size_t)nfields * sizeof(StagedArgs));
+        memcpy(tab.bin_base, h_bin_base, (size_t)(nfields + 1) * sizeof(int));
+        tab.nfields = nfields;
+        kern_p<<<(unsigned)total_bins, kThreads, smem, st>>>(tab);
+        return check_launch("interp_staged_batch_p");
+      }
       kern<<<(unsigned)total_bins, kThreads, smem, st>>>(
           static_cast<const StagedArgs*>(d_tab), d_bin_base, nfields);
       return check_launch("interp_staged_batch");

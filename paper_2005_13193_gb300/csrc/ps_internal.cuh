@@ -135,9 +135,11 @@ ps_status staged_fill_rk2(const ps_grid* grid, ps_dtype coef_t, const int32_t br
                           int next_key_base, int next_runs, void* out, size_t* smem);
 // Particles per bin of a field binned in runs of particles instead of bricks.
 constexpr int kBatchChunk = 128;
+// h_tab, h_bin_base: host copies of the same tables; with at most 48 fields
+// they go by value as a kernel parameter (else pass NULL).
 ps_status staged_batch_launch(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
-                              int nfields, int64_t total_bins, size_t smem, bool prepare,
-                              cudaStream_t st);
+                              const void* h_tab, const int* h_bin_base, int nfields,
+                              int64_t total_bins, size_t smem, bool prepare, cudaStream_t st);
 // All nsteps Heun steps of a batch in one cooperative launch (counts and sync,
 // four words, zero at launch).
 ps_status staged_batch_persistent(ps_dtype coef_t, const void* d_tab, const int* d_bin_base,
