@@ -107,3 +107,39 @@ def test_bad_arguments_rejected_on_host():
         rc = lib.ps_rk2_step(ctypes.byref(g), _abi.PS_F32, P, None, None, None, 10, P, None,
                              None, 1e-3, brick, mode, P, None, 0, None, None)
         assert rc == _abi.PS_ERR_WORKSPACE
+
+
+# every tune key: its documented values are taken and read back, anything
+# else is refused and leaves the value unchanged (host only, no GPU)
+TUNE_KEYS = {
+    "brick_kernel": ([-1, 0, 2, 5], [1, 3, 4, 6, -2]),
+    "brick_min_stage": ([0, 8, 1 << 20], [-1, (1 << 20) + 1]),
+    "node_tma": ([0, 1], [2, -1]),
+    "solve_xw": ([0, 8, 16, 32], [4, 24, 64]),
+    "solve_stream": ([0, 1], [2, -1]),
+    "solve_zt": ([0, 16, 32, 64, 128, 256], [8, 48, 512]),
+    "solve_stages": ([0, 2, 3, 4], [1, 5]),
+    "batch_run_below": ([0, 16, 1 << 20], [-1, (1 << 20) + 1]),
+    "batch_persistent": ([0, 1], [2, -1]),
+    "wait_probe": ([0, 1000, 1 << 30], [-1, (1 << 30) + 1]),
+}
+
+
+@pytest.mark.parametrize("key", sorted(TUNE_KEYS))
+def test_tune_keys_on_host(key):
+    lib = _abi.load()
+    k = key.encode()
+    good, bad = TUNE_KEYS[key]
+    old = lib.ps_tune_get(k)
+    try:
+        for v in good:
+            assert lib.ps_tune_set(k, v) == _abi.PS_OK, (key, v)
+            assert lib.ps_tune_get(k) == v
+        last = lib.ps_tune_get(k)
+        for v in bad:
+            assert lib.ps_tune_set(k, v) == _abi.PS_ERR_INVALID_ARG, (key, v)
+            assert lib.ps_tune_get(k) == last
+    finally:
+        lib.ps_tune_set(k, old)
+    assert lib.ps_tune_set(b"no_such_key", 1) == _abi.PS_ERR_INVALID_ARG
+    assert lib.ps_tune_get(b"no_such_key") == -1
