@@ -554,9 +554,27 @@ __device__ __forceinline__ bool gather8(const float4* __restrict__ halo, int PS,
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float w = f4get(by, j) * bz[kk];
+        // a node's components by one load, the values load_coef would give
+        float nv[3] = {0.f, 0.f, 0.f};
+        if constexpr (IsNode4<Tc>::value && NC == 3) {
+          const int64_t row = (int64_t)(az + kh + 2 * kk) * g.m[1] + ay + j;
+          if constexpr (IsNode16<Tc>::value) {
+            const Tc n = coef[row * g.rx + ax + q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) nv[c] = node16_value(n.v[c]) * __ldg(scale + row * 4 + c);
+          } else {
+            const float4 n = __ldg(reinterpret_cast<const float4*>(coef) + row * g.rx + ax + q);
+            nv[0] = n.x;
+            nv[1] = n.y;
+            nv[2] = n.z;
+          }
+        }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          const float v = load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j, ax + q);
+          const float v = (IsNode4<Tc>::value && NC == 3)
+                              ? nv[c]
+                              : (float)load_coef<Tc>(coef, scale, g, c, az + kh + 2 * kk, ay + j,
+                                                     ax + q);
           acc[c] = fmaf(w, v, acc[c]);
           if (GRAD) {
             accy[c] = fmaf(f4get(dby, j) * bz[kk], v, accy[c]);
